@@ -1,0 +1,1096 @@
+/*
+ * FP64 oracle of the TLMPM cutting substep (BladeMaster, arXiv 2609.27342).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * CPU statement of what one substep computes.  Only the test suite, the
+ * package smoke check and the CPU-baseline leg of the benchmark may build,
+ * link or call it; the GPU library shares no code with it.
+ *
+ * Everything is double precision with plain loops and a scatter-form P2G
+ * that follows Eq. 2 literally.  Build with -ffp-contract=off so the few
+ * decisions that must agree bit-for-bit with the GPU (side labels, Eq. 4/6)
+ * are evaluated with separately rounded multiplies and adds.
+ *
+ * Readings of points the paper leaves open (they are listed again in the
+ * design notes of the repository):
+ *   - stress: compressible neo-Hookean (the workloads ask for it; the paper's
+ *     own model is fixed-corotated, Sec. III-B);
+ *   - shape functions: quadratic B-splines on cell-corner nodes, base node
+ *     floor(X/dx - 1/2) relative to the grid origin (Eq. 1);
+ *   - substep order: contact -> cutting resistance -> reaction wrench ->
+ *     pair contact -> side labels (into the next code) -> stress -> P2G per
+ *     logical grid -> coupling -> grid update -> G2P -> MUSL re-scatter with
+ *     coupling -> F update -> commit codes -> rigid tool update;
+ *   - x update uses the Eq. 9 velocity; F += dt sum_i v*_i (x) grad0 N_ip with
+ *     v* from the coupled MUSL re-scatter;
+ *   - D release: with D^n < 1 the full impulse is applied and D accumulates;
+ *     with D^n = 1 the positive component along d is removed (Eq. 5);
+ *   - friction history transport: project onto the tangent plane and rescale
+ *     to the previous length; slip stores u = -(f_t + c_t v_t)/k_t (Eq. 12);
+ *   - blade = oriented box (half-thickness along n, half-length along e,
+ *     height behind the edge along -d), floor = frictionless half-space;
+ *   - self-contact exclusion: the reference stencils share a node and the
+ *     codes do not conflict (Sec. III-E).
+ *
+ * Parity status per function is stated in the repository's test suite;
+ * whole-run trajectories are parity unpinned beyond the invariants there.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_CUTS 32
+#define OR_MAX_SEG 16
+#define OR_HIST 16
+
+/* error bits (sticky) */
+#define OR_E_INVERTED 1u
+#define OR_E_NONFINITE 2u
+#define OR_E_HIST_OVERFLOW 4u
+
+typedef struct {
+  double E, nu, rho, dx, origin[3], V0, dt, beta, g[3];
+  int floor_on;
+  double floor_z;
+  double s_R, s_n, gamma_k, gamma_c;
+  int pair_on;
+  double pair_mu_s, pair_mu_d;
+  double Gc, zeta, u_min, b_back, b_lead, h;
+  int tool_contact_on;
+  int single_field; /* 1: P2G/G2P ignore codes (the single-field baseline) */
+} or_params;
+
+typedef struct {
+  int n_steps;
+  int cut_id;
+  double v[3], w[3];
+} or_seg;
+
+typedef struct {
+  double edge[3], n[3], e[3], d[3]; /* tool-frame geometry */
+  double half_len, thick, height, mu_s, mu_d;
+  double mass, inertia[9];
+  double x0[3], R0[9];
+  double kv;
+  int rigid_interval;
+  int nseg;
+  or_seg seg[OR_MAX_SEG];
+} or_blade;
+
+/* One logical grid at one node: S_i^c = (m, p, dp) of Eq. 8 plus results. */
+typedef struct {
+  int64_t code;
+  double m, p[3], dp[3];
+  double vold[3], vnew[3];
+  double pstar[3], vstar[3];
+} or_lgrid;
+
+typedef struct {
+  int cnt, cap;
+  or_lgrid *g;
+} or_node;
+
+typedef struct {
+  int64_t partner;
+  double u[3];
+} or_hist;
+
+typedef struct {
+  or_params P;
+  or_blade B;
+  int has_blade;
+  int64_t n;
+  double *X, *x, *v, *F, *D, *ut;
+  unsigned char *digit, *digit_next; /* n * OR_MAX_CUTS ternary digits */
+  double *J;                          /* per-particle total contact+body impulse this step */
+  or_hist *hist, *hist_next;
+  int *hist_cnt, *hist_cnt_next;
+  /* grid */
+  int lo[3], dim[3];
+  or_node *nodes;
+  /* tool state */
+  double xB[3], R[9], vB[3], wB[3];
+  int64_t step;
+  int cur_cut;
+  double accF[3], accT[3];
+  int acc_cnt;
+  double lastF[6];
+  double *wrench_hist;
+  int64_t wrench_cap;
+  double impulse_sum[3]; /* sum of impulses scattered last step (Eq. 18) */
+  unsigned err;
+  double mp, Rp, mu, lam;
+} or_scene;
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                             */
+/* ------------------------------------------------------------------------ */
+
+static double dot3(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+/* y = M x for row-major 3x3 M, summed left to right */
+static void matvec(const double M[9], const double x[3], double y[3]) {
+  for (int i = 0; i < 3; ++i) y[i] = M[3 * i] * x[0] + M[3 * i + 1] * x[1] + M[3 * i + 2] * x[2];
+}
+static void matmul(const double A[9], const double B[9], double C[9]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+static double det3(const double A[9]) {
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+         A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+static int inv3(const double A[9], double B[9]) {
+  double d = det3(A);
+  if (d == 0.0) return 0;
+  B[0] = (A[4] * A[8] - A[5] * A[7]) / d;
+  B[1] = (A[2] * A[7] - A[1] * A[8]) / d;
+  B[2] = (A[1] * A[5] - A[2] * A[4]) / d;
+  B[3] = (A[5] * A[6] - A[3] * A[8]) / d;
+  B[4] = (A[0] * A[8] - A[2] * A[6]) / d;
+  B[5] = (A[2] * A[3] - A[0] * A[5]) / d;
+  B[6] = (A[3] * A[7] - A[4] * A[6]) / d;
+  B[7] = (A[1] * A[6] - A[0] * A[7]) / d;
+  B[8] = (A[0] * A[4] - A[1] * A[3]) / d;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1: reference-configuration quadratic B-spline                         */
+/* ------------------------------------------------------------------------ */
+
+/* xl = (X - origin)/dx.  Returns base node floor(xl - 1/2); w[k], dw[k] are
+ * N and dN/dxl of nodes base+k, k = 0, 1, 2 (divide dw by dx for dN/dX). */
+int or_bspline(double xl, double w[3], double dw[3]) {
+  int base = (int)floor(xl - 0.5);
+  double fx = xl - base; /* in [0.5, 1.5) */
+  w[0] = 0.5 * (1.5 - fx) * (1.5 - fx);
+  w[1] = 0.75 - (fx - 1.0) * (fx - 1.0);
+  w[2] = 0.5 * (fx - 0.5) * (fx - 0.5);
+  dw[0] = fx - 1.5;
+  dw[1] = -2.0 * (fx - 1.0);
+  dw[2] = fx - 0.5;
+  return base;
+}
+
+/* ------------------------------------------------------------------------ */
+/* stress: compressible neo-Hookean                                          */
+/*   psi = mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2                    */
+/*   P   = mu (F - F^{-T}) + lam ln J F^{-T}                                 */
+/* ------------------------------------------------------------------------ */
+
+#define OR_JMIN 1e-6
+
+double or_psi(const double F[9], double mu, double lam) {
+  double J = det3(F);
+  if (J < OR_JMIN) J = OR_JMIN;
+  double tr = 0;
+  for (int k = 0; k < 9; ++k) tr += F[k] * F[k];
+  double lj = log(J);
+  return 0.5 * mu * (tr - 3.0) - mu * lj + 0.5 * lam * lj * lj;
+}
+
+/* returns 1 when J was clamped (inverted or degenerate element) */
+int or_piola(const double F[9], double mu, double lam, double P[9]) {
+  double J = det3(F);
+  int clamped = 0;
+  if (!(J > OR_JMIN)) {
+    J = OR_JMIN;
+    clamped = 1;
+  }
+  /* F^{-T} = cof(F) / J */
+  double c[9];
+  c[0] = F[4] * F[8] - F[5] * F[7];
+  c[1] = F[5] * F[6] - F[3] * F[8];
+  c[2] = F[3] * F[7] - F[4] * F[6];
+  c[3] = F[2] * F[7] - F[1] * F[8];
+  c[4] = F[0] * F[8] - F[2] * F[6];
+  c[5] = F[1] * F[6] - F[0] * F[7];
+  c[6] = F[1] * F[5] - F[2] * F[4];
+  c[7] = F[2] * F[3] - F[0] * F[5];
+  c[8] = F[0] * F[4] - F[1] * F[3];
+  double lj = log(J);
+  for (int k = 0; k < 9; ++k) {
+    double FinvT = c[k] / J;
+    P[k] = mu * (F[k] - FinvT) + lam * lj * FinvT;
+  }
+  return clamped;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 7 and the conflict predicate                                          */
+/* ------------------------------------------------------------------------ */
+
+static int64_t pow3(int k) {
+  int64_t r = 1;
+  while (k-- > 0) r *= 3;
+  return r;
+}
+
+/* c = sum_k d_k 3^k */
+int64_t or_code(const unsigned char *digits, int K) {
+  int64_t c = 0;
+  for (int k = 0; k < K; ++k) c += (int64_t)digits[k] * pow3(k);
+  return c;
+}
+
+/* d_k(c): the k-th ternary digit */
+int or_digit(int64_t c, int k) { return (int)((c / pow3(k)) % 3); }
+
+/* conflict(a, b) <=> exists k with (d_k(a), d_k(b)) in {(1,2), (2,1)} */
+int or_conflict(int64_t a, int64_t b) {
+  for (int k = 0; k < OR_MAX_CUTS; ++k) {
+    int da = or_digit(a, k), db = or_digit(b, k);
+    if ((da == 1 && db == 2) || (da == 2 && db == 1)) return 1;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 8: compatible-state coupling at one node                              */
+/*   S_bar^a = S^a + 1/M sum_{b != a, !conflict(a,b)} (m^a S^b - m^b S^a)    */
+/* S is ns x nc (row a = logical grid a), updated in place.                  */
+/* ------------------------------------------------------------------------ */
+
+void or_couple(int ns, const int64_t *codes, const double *m, int nc, double *S) {
+  double M = 0;
+  for (int a = 0; a < ns; ++a) M += m[a];
+  if (!(M > 0)) return;
+  double *Sbar = (double *)malloc(sizeof(double) * (size_t)ns * (size_t)nc);
+  for (int a = 0; a < ns; ++a) {
+    for (int c = 0; c < nc; ++c) {
+      double acc = 0;
+      for (int b = 0; b < ns; ++b) {
+        if (b == a || or_conflict(codes[a], codes[b])) continue;
+        acc += m[a] * S[b * nc + c] - m[b] * S[a * nc + c];
+      }
+      Sbar[a * nc + c] = S[a * nc + c] + acc / M;
+    }
+  }
+  memcpy(S, Sbar, sizeof(double) * (size_t)ns * (size_t)nc);
+  free(Sbar);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 12: tangential spring-history Coulomb friction                        */
+/* ------------------------------------------------------------------------ */
+
+void or_friction(const double u_hist[3], const double n[3], const double vrel[3], double fn,
+                 double meff, double dt, double gk, double gc, double mus, double mud,
+                 double ft[3], double u_new[3]) {
+  /* transport the stored displacement to the current tangent plane */
+  double un = dot3(u_hist, n), ul = norm3(u_hist);
+  double tu[3] = {u_hist[0] - un * n[0], u_hist[1] - un * n[1], u_hist[2] - un * n[2]};
+  double tl = norm3(tu);
+  double ut[3] = {0, 0, 0};
+  if (tl > 0) {
+    for (int i = 0; i < 3; ++i) ut[i] = tu[i] * (ul / tl);
+  }
+  double vn = dot3(vrel, n);
+  double vt[3] = {vrel[0] - vn * n[0], vrel[1] - vn * n[1], vrel[2] - vn * n[2]};
+  double kt = gk * meff / (dt * dt);
+  double ct = 2.0 * gc * sqrt(meff * kt);
+  double ftr[3];
+  for (int i = 0; i < 3; ++i) ftr[i] = -kt * ut[i] - ct * vt[i];
+  double fl = norm3(ftr);
+  if (fl <= mus * fn) { /* stick: keep the trial force */
+    for (int i = 0; i < 3; ++i) {
+      ft[i] = ftr[i];
+      u_new[i] = ut[i] + dt * vt[i];
+    }
+  } else { /* slip at the dynamic bound; history matches the applied force */
+    for (int i = 0; i < 3; ++i) {
+      ft[i] = mud * fn * ftr[i] / fl;
+      u_new[i] = -(ft[i] + ct * vt[i]) / kt;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* blade box: closest point, outward normal and sphere gap                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double xe[3], n[3], e[3], d[3], ve[3]; /* edge point, axes, edge velocity */
+  double c[3];                           /* box centre */
+  double hext[3];                        /* half extents along n, e, d */
+  double Iinv_w[9];                      /* world inverse inertia */
+} or_frame;
+
+static void or_make_frame(const or_scene *s, or_frame *fr) {
+  const or_blade *B = &s->B;
+  double t[3];
+  matvec(s->R, B->edge, t);
+  for (int i = 0; i < 3; ++i) fr->xe[i] = s->xB[i] + t[i];
+  matvec(s->R, B->n, fr->n);
+  matvec(s->R, B->e, fr->e);
+  matvec(s->R, B->d, fr->d);
+  double r[3] = {fr->xe[0] - s->xB[0], fr->xe[1] - s->xB[1], fr->xe[2] - s->xB[2]};
+  double wr[3];
+  cross3(s->wB, r, wr);
+  for (int i = 0; i < 3; ++i) fr->ve[i] = s->vB[i] + wr[i];
+  for (int i = 0; i < 3; ++i) fr->c[i] = fr->xe[i] - 0.5 * B->height * fr->d[i];
+  fr->hext[0] = 0.5 * B->thick;
+  fr->hext[1] = B->half_len;
+  fr->hext[2] = 0.5 * B->height;
+  memset(fr->Iinv_w, 0, sizeof fr->Iinv_w);
+  if (B->mass > 0) {
+    double Ib_inv[9], RT[9], tmp[9];
+    inv3(B->inertia, Ib_inv);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) RT[3 * i + j] = s->R[3 * j + i];
+    matmul(s->R, Ib_inv, tmp);
+    matmul(tmp, RT, fr->Iinv_w);
+  }
+}
+
+/* closest point x_c, outward normal nB, signed sphere-surface gap phi */
+void or_box_closest(const double c[3], const double ax_n[3], const double ax_e[3],
+                    const double ax_d[3], const double hext[3], const double x[3], double R,
+                    double xc[3], double nB[3], double *phi) {
+  const double *ax[3] = {ax_n, ax_e, ax_d};
+  double r[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
+  double q[3], qc[3], nl[3] = {0, 0, 0};
+  int outside = 0;
+  for (int a = 0; a < 3; ++a) {
+    q[a] = dot3(r, ax[a]);
+    if (fabs(q[a]) > hext[a]) outside = 1;
+  }
+  if (outside) {
+    double diff[3];
+    for (int a = 0; a < 3; ++a) {
+      qc[a] = q[a] < -hext[a] ? -hext[a] : (q[a] > hext[a] ? hext[a] : q[a]);
+      diff[a] = q[a] - qc[a];
+    }
+    double dist = norm3(diff);
+    for (int a = 0; a < 3; ++a) nl[a] = diff[a] / dist;
+    *phi = dist - R;
+  } else {
+    int best = 0;
+    double bd = hext[0] - fabs(q[0]);
+    for (int a = 1; a < 3; ++a) {
+      double dd = hext[a] - fabs(q[a]);
+      if (dd < bd) {
+        bd = dd;
+        best = a;
+      }
+    }
+    for (int a = 0; a < 3; ++a) qc[a] = q[a];
+    double sg = q[best] < 0 ? -1.0 : 1.0;
+    qc[best] = sg * hext[best];
+    nl[best] = sg;
+    *phi = -bd - R;
+  }
+  for (int i = 0; i < 3; ++i) {
+    xc[i] = c[i] + qc[0] * ax[0][i] + qc[1] * ax[1][i] + qc[2] * ax[2][i];
+    nB[i] = nl[0] * ax[0][i] + nl[1] * ax[1][i] + nl[2] * ax[2][i];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 3, 4, 6: blade coordinates, cutting band and side assignment.         */
+/* Evaluated with separately rounded operations in a fixed order.            */
+/* Returns the new digit (1 or 2) or 0 when no assignment happens.           */
+/* ------------------------------------------------------------------------ */
+
+int or_side_label(const double x[3], const double v[3], const double xe[3], const double n[3],
+                  const double e[3], const double d[3], const double ve[3], double h, double L,
+                  double b_back, double b_lead, double dt) {
+  double r0 = x[0] - xe[0], r1 = x[1] - xe[1], r2 = x[2] - xe[2];
+  double s = r0 * n[0] + r1 * n[1] + r2 * n[2];
+  double l = r0 * e[0] + r1 * e[1] + r2 * e[2];
+  double f = r0 * d[0] + r1 * d[1] + r2 * d[2];
+  double uc = (ve[0] - v[0]) * d[0] + (ve[1] - v[1]) * d[1] + (ve[2] - v[2]) * d[2];
+  double ucdt = uc * dt;
+  double lowb = -b_back - (ucdt > 0.0 ? ucdt : 0.0);
+  int band = fabs(s) <= h && fabs(l) <= L && lowb <= f && f <= b_lead;
+  if (!band || !(f <= 0.0)) return 0;
+  return s < 0.0 ? 1 : 2;
+}
+
+/* Eq. 5: one update of the cutting-progress variable */
+double or_cut_progress(double D, double Jc, double uc, double Wth) {
+  double nd = D + Jc * uc / Wth;
+  return nd < 1.0 ? nd : 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* scene                                                                     */
+/* ------------------------------------------------------------------------ */
+
+static void base_of(const or_scene *s, const double X[3], int b[3], double w[3][3],
+                    double dw[3][3]) {
+  for (int a = 0; a < 3; ++a) {
+    double xl = (X[a] - s->P.origin[a]) / s->P.dx;
+    b[a] = or_bspline(xl, w[a], dw[a]);
+    for (int k = 0; k < 3; ++k) dw[a][k] /= s->P.dx;
+  }
+}
+
+static int node_index(const or_scene *s, int i, int j, int k) {
+  int a = i - s->lo[0], b = j - s->lo[1], c = k - s->lo[2];
+  return (c * s->dim[1] + b) * s->dim[0] + a;
+}
+
+static or_lgrid *lgrid_find(or_node *nd, int64_t code, int create) {
+  for (int a = 0; a < nd->cnt; ++a)
+    if (nd->g[a].code == code) return &nd->g[a];
+  if (!create) return NULL;
+  if (nd->cnt == nd->cap) {
+    nd->cap = nd->cap ? 2 * nd->cap : 4;
+    nd->g = (or_lgrid *)realloc(nd->g, sizeof(or_lgrid) * (size_t)nd->cap);
+  }
+  or_lgrid *g = &nd->g[nd->cnt++];
+  memset(g, 0, sizeof *g);
+  g->code = code;
+  return g;
+}
+
+static int64_t pcode(const or_scene *s, int64_t p, const unsigned char *dg) {
+  if (s->P.single_field) return 0;
+  return or_code(dg + p * OR_MAX_CUTS, OR_MAX_CUTS);
+}
+
+or_scene *or_create(const or_params *P, const or_blade *B, int64_t n, const double *X,
+                    int64_t wrench_cap) {
+  or_scene *s = (or_scene *)calloc(1, sizeof(or_scene));
+  s->P = *P;
+  if (s->P.h <= 0) s->P.h = 6.0 * P->dx;           /* h_k = 6 dx, Sec. III-D */
+  if (s->P.b_back <= 0) s->P.b_back = P->dx;
+  if (s->P.b_lead <= 0) s->P.b_lead = P->dx;
+  s->n = n;
+  s->mp = P->rho * P->V0;
+  s->Rp = P->s_R * cbrt(P->V0) / 2.0; /* R_p = s_R (V0)^{1/3} / 2, Sec. III-E */
+  s->mu = P->E / (2.0 * (1.0 + P->nu));
+  s->lam = P->E * P->nu / ((1.0 + P->nu) * (1.0 - 2.0 * P->nu));
+  size_t n3 = (size_t)n * 3;
+  s->X = (double *)malloc(sizeof(double) * n3);
+  s->x = (double *)malloc(sizeof(double) * n3);
+  s->v = (double *)calloc(n3, sizeof(double));
+  s->F = (double *)calloc((size_t)n * 9, sizeof(double));
+  s->D = (double *)calloc((size_t)n, sizeof(double));
+  s->ut = (double *)calloc(n3, sizeof(double));
+  s->J = (double *)calloc(n3, sizeof(double));
+  s->digit = (unsigned char *)calloc((size_t)n * OR_MAX_CUTS, 1);
+  s->digit_next = (unsigned char *)calloc((size_t)n * OR_MAX_CUTS, 1);
+  s->hist = (or_hist *)calloc((size_t)n * OR_HIST, sizeof(or_hist));
+  s->hist_next = (or_hist *)calloc((size_t)n * OR_HIST, sizeof(or_hist));
+  s->hist_cnt = (int *)calloc((size_t)n, sizeof(int));
+  s->hist_cnt_next = (int *)calloc((size_t)n, sizeof(int));
+  memcpy(s->X, X, sizeof(double) * n3);
+  memcpy(s->x, X, sizeof(double) * n3);
+  for (int64_t p = 0; p < n; ++p) s->F[9 * p] = s->F[9 * p + 4] = s->F[9 * p + 8] = 1.0;
+  /* node range covering every particle's stencil */
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, X + 3 * p, b, w, dw);
+    for (int a = 0; a < 3; ++a) {
+      if (b[a] < lo[a]) lo[a] = b[a];
+      if (b[a] + 2 > hi[a]) hi[a] = b[a] + 2;
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    s->lo[a] = n > 0 ? lo[a] : 0;
+    s->dim[a] = n > 0 ? hi[a] - lo[a] + 1 : 1;
+  }
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  s->nodes = (or_node *)calloc(nn, sizeof(or_node));
+  s->cur_cut = -1;
+  s->wrench_cap = wrench_cap;
+  s->wrench_hist = (double *)calloc((size_t)(wrench_cap > 0 ? wrench_cap : 1) * 6, sizeof(double));
+  if (B) {
+    s->B = *B;
+    s->has_blade = 1;
+    if (s->B.rigid_interval < 1) s->B.rigid_interval = 1;
+    if (s->B.kv <= 0) s->B.kv = 1.0 / (10.0 * P->dt);
+    memcpy(s->xB, B->x0, sizeof s->xB);
+    memcpy(s->R, B->R0, sizeof s->R);
+  }
+  return s;
+}
+
+void or_destroy(or_scene *s) {
+  if (!s) return;
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  for (size_t i = 0; i < nn; ++i) free(s->nodes[i].g);
+  free(s->nodes);
+  free(s->X); free(s->x); free(s->v); free(s->F); free(s->D); free(s->ut); free(s->J);
+  free(s->digit); free(s->digit_next);
+  free(s->hist); free(s->hist_next); free(s->hist_cnt); free(s->hist_cnt_next);
+  free(s->wrench_hist);
+  free(s);
+}
+
+/* segment active at substep `step`; NULL when the program has ended */
+static const or_seg *seg_at(const or_scene *s, int64_t step) {
+  int64_t acc = 0;
+  for (int i = 0; i < s->B.nseg; ++i) {
+    acc += s->B.seg[i].n_steps;
+    if (step < acc) return &s->B.seg[i];
+  }
+  return NULL;
+}
+
+/* Rodrigues rotation by the vector th (angle |th| about th/|th|) */
+static void rot_exp(const double th[3], double Rm[9]) {
+  double a = norm3(th);
+  for (int k = 0; k < 9; ++k) Rm[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  if (!(a > 0)) return;
+  double k0 = th[0] / a, k1 = th[1] / a, k2 = th[2] / a;
+  double K[9] = {0, -k2, k1, k2, 0, -k0, -k1, k0, 0};
+  double K2[9];
+  matmul(K, K, K2);
+  double sa = sin(a), ca = 1.0 - cos(a);
+  for (int k = 0; k < 9; ++k) Rm[k] += sa * K[k] + ca * K2[k];
+}
+
+/* pair contact candidates: uniform binning of current positions */
+typedef struct {
+  int64_t *order;
+  int64_t *start;
+  int nb[3];
+  double lo[3], cell;
+} or_bins;
+
+static void pair_contact(or_scene *s) {
+  int64_t n = s->n;
+  double R2 = 2.0 * s->Rp;
+  double vmax = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    double vv = norm3(s->v + 3 * p);
+    if (vv > vmax) vmax = vv;
+  }
+  double cell = R2 + 2.0 * vmax * s->P.dt + 1e-12;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t p = 0; p < n; ++p)
+    for (int a = 0; a < 3; ++a) {
+      if (s->x[3 * p + a] < lo[a]) lo[a] = s->x[3 * p + a];
+      if (s->x[3 * p + a] > hi[a]) hi[a] = s->x[3 * p + a];
+    }
+  int nb[3];
+  for (int a = 0; a < 3; ++a) {
+    nb[a] = (int)floor((hi[a] - lo[a]) / cell) + 1;
+    if (nb[a] < 1) nb[a] = 1;
+  }
+  int64_t ncell = (int64_t)nb[0] * nb[1] * nb[2];
+  int64_t *cnt = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+  int64_t *cid = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t p = 0; p < n; ++p) {
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+      c[a] = (int)floor((s->x[3 * p + a] - lo[a]) / cell);
+      if (c[a] >= nb[a]) c[a] = nb[a] - 1;
+    }
+    cid[p] = ((int64_t)c[2] * nb[1] + c[1]) * nb[0] + c[0];
+    cnt[cid[p] + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) cnt[c + 1] += cnt[c];
+  int64_t *fill = (int64_t *)calloc((size_t)ncell, sizeof(int64_t));
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t p = 0; p < n; ++p) order[cnt[cid[p]] + fill[cid[p]]++] = p;
+
+  double meff = s->mp * s->mp / (s->mp + s->mp);
+  double dt = s->P.dt;
+  for (int64_t p = 0; p < n; ++p) s->hist_cnt_next[p] = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+      c[a] = (int)floor((s->x[3 * p + a] - lo[a]) / cell);
+      if (c[a] >= nb[a]) c[a] = nb[a] - 1;
+    }
+    int bp[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, bp, w, dw);
+    int64_t cp = or_code(s->digit + p * OR_MAX_CUTS, OR_MAX_CUTS);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dxx = -1; dxx <= 1; ++dxx) {
+          int cc[3] = {c[0] + dxx, c[1] + dy, c[2] + dz};
+          if (cc[0] < 0 || cc[1] < 0 || cc[2] < 0 || cc[0] >= nb[0] || cc[1] >= nb[1] ||
+              cc[2] >= nb[2])
+            continue;
+          int64_t ci = ((int64_t)cc[2] * nb[1] + cc[1]) * nb[0] + cc[0];
+          for (int64_t t = cnt[ci]; t < cnt[ci + 1]; ++t) {
+            int64_t q = order[t];
+            if (q <= p) continue; /* each pair once, owned by the lower index */
+            double dxv[3] = {s->x[3 * p] - s->x[3 * q], s->x[3 * p + 1] - s->x[3 * q + 1],
+                             s->x[3 * p + 2] - s->x[3 * q + 2]};
+            double dist = norm3(dxv);
+            if (!(dist > 0)) continue;
+            double npq[3] = {dxv[0] / dist, dxv[1] / dist, dxv[2] / dist};
+            double vrel[3] = {s->v[3 * p] - s->v[3 * q], s->v[3 * p + 1] - s->v[3 * q + 1],
+                              s->v[3 * p + 2] - s->v[3 * q + 2]};
+            double vn = dot3(vrel, npq);
+            /* Eq. 10: predicted overlap */
+            double dhat = R2 - (dist + (dt * vn < 0 ? dt * vn : 0.0));
+            if (!(dhat > 0)) continue;
+            /* self-contact exclusion: reference stencils share a node and the
+               codes are compatible */
+            int bq[3];
+            double wq[3][3], dwq[3][3];
+            base_of(s, s->X + 3 * q, bq, wq, dwq);
+            int share = abs(bp[0] - bq[0]) <= 2 && abs(bp[1] - bq[1]) <= 2 &&
+                        abs(bp[2] - bq[2]) <= 2;
+            int64_t cq = or_code(s->digit + q * OR_MAX_CUTS, OR_MAX_CUTS);
+            if (share && !or_conflict(cp, cq)) continue;
+            /* Eq. 11: normal force */
+            double fn = s->P.s_n * meff / (dt * dt) * dhat;
+            /* Eq. 12 with the pair history owned by p */
+            double uh[3] = {0, 0, 0};
+            for (int k = 0; k < s->hist_cnt[p]; ++k)
+              if (s->hist[p * OR_HIST + k].partner == q) {
+                memcpy(uh, s->hist[p * OR_HIST + k].u, sizeof uh);
+                break;
+              }
+            double ft[3], un[3];
+            or_friction(uh, npq, vrel, fn, meff, dt, s->P.gamma_k, s->P.gamma_c,
+                        s->P.pair_mu_s, s->P.pair_mu_d, ft, un);
+            double Jpq[3];
+            for (int i = 0; i < 3; ++i) Jpq[i] = dt * (fn * npq[i] + ft[i]);
+            /* Eq. 13: equal and opposite impulses */
+            for (int i = 0; i < 3; ++i) {
+              s->J[3 * p + i] += Jpq[i];
+              s->J[3 * q + i] -= Jpq[i];
+            }
+            int hc = s->hist_cnt_next[p];
+            if (hc < OR_HIST) {
+              s->hist_next[p * OR_HIST + hc].partner = q;
+              memcpy(s->hist_next[p * OR_HIST + hc].u, un, sizeof un);
+              s->hist_cnt_next[p] = hc + 1;
+            } else {
+              s->err |= OR_E_HIST_OVERFLOW;
+            }
+          }
+        }
+  }
+  free(cnt); free(cid); free(fill); free(order);
+  /* swap history buffers */
+  or_hist *th = s->hist; s->hist = s->hist_next; s->hist_next = th;
+  int *tc = s->hist_cnt; s->hist_cnt = s->hist_cnt_next; s->hist_cnt_next = tc;
+}
+
+static void clear_grid(or_scene *s) {
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  for (size_t i = 0; i < nn; ++i) s->nodes[i].cnt = 0;
+}
+
+/* one TLMPM substep */
+static void substep(or_scene *s) {
+  const or_params *P = &s->P;
+  int64_t n = s->n;
+  double dt = P->dt, mp = s->mp, V0 = P->V0;
+  const or_seg *sg = s->has_blade ? seg_at(s, s->step) : NULL;
+  int cut = sg ? sg->cut_id : -1;
+  or_frame fr;
+  memset(&fr, 0, sizeof fr);
+
+  if (s->has_blade) {
+    int dynamic = s->B.mass > 0;
+    if (!dynamic) { /* prescribed twist of the current segment */
+      for (int i = 0; i < 3; ++i) {
+        s->vB[i] = sg ? sg->v[i] : 0.0;
+        s->wB[i] = sg ? sg->w[i] : 0.0;
+      }
+    }
+    /* D_p is reset to zero at the beginning of each new cut (Sec. III-A) */
+    if (cut >= 0 && cut != s->cur_cut) {
+      for (int64_t p = 0; p < n; ++p) s->D[p] = 0.0;
+      s->cur_cut = cut;
+    }
+    or_make_frame(s, &fr);
+  }
+  double Wth = P->Gc * pow(V0, 2.0 / 3.0) * (1.0 - P->zeta) / P->zeta; /* Eq. 5 */
+
+  memcpy(s->digit_next, s->digit, (size_t)n * OR_MAX_CUTS);
+  double Fsum[3] = {0, 0, 0}, Tsum[3] = {0, 0, 0};
+
+  for (int64_t p = 0; p < n; ++p) {
+    double *xp = s->x + 3 * p, *vp = s->v + 3 * p;
+    double Jp[3] = {0, 0, 0};
+    /* --- tool-material contact, Eq. 14-15 with Eq. 12 friction --- */
+    if (s->has_blade && P->tool_contact_on) {
+      double xc[3], nB[3], phi;
+      or_box_closest(fr.c, fr.n, fr.e, fr.d, fr.hext, xp, s->Rp, xc, nB, &phi);
+      double rc[3] = {xc[0] - s->xB[0], xc[1] - s->xB[1], xc[2] - s->xB[2]};
+      double wr[3];
+      cross3(s->wB, rc, wr);
+      double vrel[3] = {vp[0] - (s->vB[0] + wr[0]), vp[1] - (s->vB[1] + wr[1]),
+                        vp[2] - (s->vB[2] + wr[2])};
+      double vn = dot3(vrel, nB);
+      double phihat = phi + dt * (vn < 0 ? vn : 0.0);
+      double wB = 0;
+      if (s->B.mass > 0) {
+        double rn[3], t[3];
+        cross3(rc, nB, rn);
+        matvec(fr.Iinv_w, rn, t);
+        wB = 1.0 / s->B.mass + dot3(rn, t);
+      }
+      double meff = 1.0 / (1.0 / mp + wB);
+      double Jn = P->s_n * meff / dt * (phihat < 0 ? -phihat : 0.0); /* Eq. 15 */
+      double JpB[3] = {0, 0, 0};
+      double *uh = s->ut + 3 * p;
+      if (Jn > 0) {
+        double ft[3], un[3];
+        or_friction(uh, nB, vrel, Jn / dt, meff, dt, P->gamma_k, P->gamma_c, s->B.mu_s,
+                    s->B.mu_d, ft, un);
+        for (int i = 0; i < 3; ++i) {
+          JpB[i] = Jn * nB[i] + dt * ft[i];
+          uh[i] = un[i];
+        }
+        /* --- cutting resistance, Eq. 5 (front band, cut advancing) --- */
+        if (cut >= 0) {
+          double r[3] = {xp[0] - fr.xe[0], xp[1] - fr.xe[1], xp[2] - fr.xe[2]};
+          double sp = dot3(r, fr.n), lp = dot3(r, fr.e), fp = dot3(r, fr.d);
+          double dv[3] = {fr.ve[0] - vp[0], fr.ve[1] - vp[1], fr.ve[2] - vp[2]};
+          double uc = dot3(dv, fr.d);
+          int front = fabs(sp) <= P->h && fabs(lp) <= s->B.half_len && fp >= 0.0 &&
+                      fp <= P->b_lead && uc > P->u_min;
+          if (front) {
+            double Jd = dot3(JpB, fr.d);
+            double Jc = Jd > 0 ? Jd : 0.0;
+            if (s->D[p] < 1.0) {
+              s->D[p] = or_cut_progress(s->D[p], Jc, uc, Wth);
+            } else { /* resistance released once D = 1 */
+              for (int i = 0; i < 3; ++i) JpB[i] -= Jc * fr.d[i];
+            }
+          }
+        }
+      } else {
+        uh[0] = uh[1] = uh[2] = 0.0;
+      }
+      /* --- reaction on the tool, Eq. 16 --- */
+      double FB[3] = {-JpB[0] / dt, -JpB[1] / dt, -JpB[2] / dt};
+      double tq[3];
+      cross3(rc, FB, tq);
+      for (int i = 0; i < 3; ++i) {
+        Fsum[i] += FB[i];
+        Tsum[i] += tq[i];
+        Jp[i] += JpB[i];
+      }
+    }
+    /* --- frictionless floor: Eq. 15 with w_B = 0 --- */
+    if (P->floor_on) {
+      double phi = xp[2] - P->floor_z - s->Rp;
+      double vn = vp[2];
+      double phihat = phi + dt * (vn < 0 ? vn : 0.0);
+      double Jn = P->s_n * mp / dt * (phihat < 0 ? -phihat : 0.0);
+      Jp[2] += Jn;
+    }
+    for (int i = 0; i < 3; ++i) s->J[3 * p + i] = Jp[i];
+    /* --- side labels for the next substep, Eq. 3, 4, 6 --- */
+    if (cut >= 0 && s->digit[p * OR_MAX_CUTS + cut] == 0) {
+      int dnew = or_side_label(xp, vp, fr.xe, fr.n, fr.e, fr.d, fr.ve, P->h, s->B.half_len,
+                               P->b_back, P->b_lead, dt);
+      if (dnew) s->digit_next[p * OR_MAX_CUTS + cut] = (unsigned char)dnew;
+    }
+  }
+  /* --- material-material contact, Eq. 10-13 --- */
+  if (P->pair_on) pair_contact(s);
+
+  /* --- P2G per logical grid, Eq. 2 (+ impulses, Eq. 13 and 16) --- */
+  clear_grid(s);
+  s->impulse_sum[0] = s->impulse_sum[1] = s->impulse_sum[2] = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    double Pk[9];
+    if (or_piola(s->F + 9 * p, s->mu, s->lam, Pk)) s->err |= OR_E_INVERTED;
+    int64_t c = pcode(s, p, s->digit);
+    double Jb[3];
+    for (int i = 0; i < 3; ++i) {
+      Jb[i] = s->J[3 * p + i] + mp * P->g[i] * dt;
+      s->impulse_sum[i] += Jb[i];
+    }
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double N = w[0][i] * w[1][j] * w[2][k];
+          double gN[3] = {dw[0][i] * w[1][j] * w[2][k], w[0][i] * dw[1][j] * w[2][k],
+                          w[0][i] * w[1][j] * dw[2][k]};
+          or_lgrid *g = lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 1);
+          g->m += N * mp;
+          for (int a = 0; a < 3; ++a) {
+            double PgN = Pk[3 * a] * gN[0] + Pk[3 * a + 1] * gN[1] + Pk[3 * a + 2] * gN[2];
+            g->p[a] += N * mp * s->v[3 * p + a];
+            g->dp[a] += -dt * V0 * PgN + N * Jb[a];
+          }
+        }
+  }
+  /* --- coupling (Eq. 8) and grid update (Eq. 9) --- */
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  for (size_t i = 0; i < nn; ++i) {
+    or_node *nd = &s->nodes[i];
+    int ns = nd->cnt;
+    if (ns == 0) continue;
+    int64_t *codes = (int64_t *)malloc(sizeof(int64_t) * ns);
+    double *m = (double *)malloc(sizeof(double) * ns);
+    double *S = (double *)malloc(sizeof(double) * ns * 6);
+    for (int a = 0; a < ns; ++a) {
+      codes[a] = nd->g[a].code;
+      m[a] = nd->g[a].m;
+      for (int c = 0; c < 3; ++c) {
+        S[a * 6 + c] = nd->g[a].p[c];
+        S[a * 6 + 3 + c] = nd->g[a].dp[c];
+      }
+    }
+    or_couple(ns, codes, m, 6, S);
+    for (int a = 0; a < ns; ++a) {
+      or_lgrid *g = &nd->g[a];
+      for (int c = 0; c < 3; ++c) {
+        double pb = S[a * 6 + c], dpb = S[a * 6 + 3 + c];
+        g->vold[c] = g->m > 0 ? pb / g->m : 0.0;
+        g->vnew[c] = g->m > 0 ? (pb + dpb) / g->m : 0.0;
+        g->p[c] = pb;   /* keep the coupled state for Eq. 17 */
+        g->dp[c] = dpb;
+      }
+    }
+    free(codes); free(m); free(S);
+  }
+  /* --- G2P, Eq. 17, and position update --- */
+  double beta = P->beta;
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    double vn[3] = {beta * s->v[3 * p], beta * s->v[3 * p + 1], beta * s->v[3 * p + 2]};
+    double dxp[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double N = w[0][i] * w[1][j] * w[2][k];
+          or_lgrid *g =
+              lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          if (!g || !(g->m > 0)) continue;
+          for (int a = 0; a < 3; ++a) {
+            vn[a] += N / g->m * ((1.0 - beta) * g->p[a] + g->dp[a]);
+            dxp[a] += N * g->vnew[a];
+          }
+        }
+    for (int a = 0; a < 3; ++a) {
+      s->v[3 * p + a] = vn[a];
+      s->x[3 * p + a] += dt * dxp[a];
+    }
+  }
+  /* --- MUSL re-scatter of m v^{n+1} per logical grid, with coupling --- */
+  for (size_t i = 0; i < nn; ++i)
+    for (int a = 0; a < s->nodes[i].cnt; ++a)
+      memset(s->nodes[i].g[a].pstar, 0, sizeof(double) * 3);
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double N = w[0][i] * w[1][j] * w[2][k];
+          or_lgrid *g =
+              lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          for (int a = 0; a < 3; ++a) g->pstar[a] += N * mp * s->v[3 * p + a];
+        }
+  }
+  for (size_t i = 0; i < nn; ++i) {
+    or_node *nd = &s->nodes[i];
+    int ns = nd->cnt;
+    if (ns == 0) continue;
+    int64_t *codes = (int64_t *)malloc(sizeof(int64_t) * ns);
+    double *m = (double *)malloc(sizeof(double) * ns);
+    double *S = (double *)malloc(sizeof(double) * ns * 3);
+    for (int a = 0; a < ns; ++a) {
+      codes[a] = nd->g[a].code;
+      m[a] = nd->g[a].m;
+      for (int c = 0; c < 3; ++c) S[a * 3 + c] = nd->g[a].pstar[c];
+    }
+    or_couple(ns, codes, m, 3, S);
+    for (int a = 0; a < ns; ++a)
+      for (int c = 0; c < 3; ++c)
+        nd->g[a].vstar[c] = nd->g[a].m > 0 ? S[a * 3 + c] / nd->g[a].m : 0.0;
+    free(codes); free(m); free(S);
+  }
+  /* --- deformation gradient, F += dt sum_i v*_i (x) grad0 N_ip --- */
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    double G[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double gN[3] = {dw[0][i] * w[1][j] * w[2][k], w[0][i] * dw[1][j] * w[2][k],
+                          w[0][i] * w[1][j] * dw[2][k]};
+          or_lgrid *g =
+              lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) G[3 * a + d] += g->vstar[a] * gN[d];
+        }
+    for (int k = 0; k < 9; ++k) s->F[9 * p + k] += dt * G[k];
+    for (int a = 0; a < 3; ++a)
+      if (!isfinite(s->x[3 * p + a]) || !isfinite(s->v[3 * p + a])) s->err |= OR_E_NONFINITE;
+  }
+  /* --- commit the codes assigned this substep (Sec. III-C) --- */
+  unsigned char *t = s->digit;
+  s->digit = s->digit_next;
+  s->digit_next = t;
+
+  /* --- wrench and rigid tool update at the rigid interval (Sec. III-G) --- */
+  if (s->has_blade) {
+    int64_t st = s->step;
+    if (st < s->wrench_cap) {
+      for (int i = 0; i < 3; ++i) {
+        s->wrench_hist[6 * st + i] = Fsum[i];
+        s->wrench_hist[6 * st + 3 + i] = Tsum[i];
+      }
+    }
+    for (int i = 0; i < 3; ++i) {
+      s->accF[i] += Fsum[i];
+      s->accT[i] += Tsum[i];
+    }
+    s->acc_cnt++;
+    if (s->acc_cnt >= s->B.rigid_interval) {
+      double H = dt * s->acc_cnt;
+      double Fa[3], Ta[3];
+      for (int i = 0; i < 3; ++i) {
+        Fa[i] = s->accF[i] / s->acc_cnt;
+        Ta[i] = s->accT[i] / s->acc_cnt;
+      }
+      if (s->B.mass > 0) {
+        const or_seg *tg = sg;
+        double vt[3] = {0, 0, 0}, wt[3] = {0, 0, 0};
+        if (tg)
+          for (int i = 0; i < 3; ++i) {
+            vt[i] = tg->v[i];
+            wt[i] = tg->w[i];
+          }
+        double kv = s->B.kv;
+        /* velocity servo toward the segment twist + interval-averaged reaction */
+        double dw_[3];
+        matvec(fr.Iinv_w, Ta, dw_);
+        for (int i = 0; i < 3; ++i) {
+          s->vB[i] += H * (kv * (vt[i] - s->vB[i]) + Fa[i] / s->B.mass);
+          s->wB[i] += H * (kv * (wt[i] - s->wB[i]) + dw_[i]);
+        }
+      }
+      double th[3] = {H * s->wB[0], H * s->wB[1], H * s->wB[2]};
+      double Rinc[9], Rn[9];
+      rot_exp(th, Rinc);
+      matmul(Rinc, s->R, Rn);
+      memcpy(s->R, Rn, sizeof Rn);
+      for (int i = 0; i < 3; ++i) s->xB[i] += H * s->vB[i];
+      for (int i = 0; i < 3; ++i) {
+        s->lastF[i] = Fa[i];
+        s->lastF[3 + i] = Ta[i];
+        s->accF[i] = s->accT[i] = 0;
+      }
+      s->acc_cnt = 0;
+    }
+  }
+  s->step++;
+}
+
+int or_step(or_scene *s, int nsteps) {
+  for (int k = 0; k < nsteps; ++k) substep(s);
+  return (int)s->err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* state access                                                              */
+/* ------------------------------------------------------------------------ */
+/* field ids: 0 X, 1 x, 2 v, 3 F, 4 D, 5 ut, 6 code (as double), 7 J, 8 digits (n*32) */
+
+int or_get(const or_scene *s, int field, double *out) {
+  int64_t n = s->n;
+  switch (field) {
+    case 0: memcpy(out, s->X, sizeof(double) * n * 3); return 0;
+    case 1: memcpy(out, s->x, sizeof(double) * n * 3); return 0;
+    case 2: memcpy(out, s->v, sizeof(double) * n * 3); return 0;
+    case 3: memcpy(out, s->F, sizeof(double) * n * 9); return 0;
+    case 4: memcpy(out, s->D, sizeof(double) * n); return 0;
+    case 5: memcpy(out, s->ut, sizeof(double) * n * 3); return 0;
+    case 6:
+      for (int64_t p = 0; p < n; ++p) out[p] = (double)or_code(s->digit + p * OR_MAX_CUTS, OR_MAX_CUTS);
+      return 0;
+    case 7: memcpy(out, s->J, sizeof(double) * n * 3); return 0;
+    case 8:
+      for (int64_t p = 0; p < n * OR_MAX_CUTS; ++p) out[p] = s->digit[p];
+      return 0;
+  }
+  return -1;
+}
+
+int or_set(or_scene *s, int field, const double *in) {
+  int64_t n = s->n;
+  switch (field) {
+    case 1: memcpy(s->x, in, sizeof(double) * n * 3); return 0;
+    case 2: memcpy(s->v, in, sizeof(double) * n * 3); return 0;
+    case 3: memcpy(s->F, in, sizeof(double) * n * 9); return 0;
+    case 4: memcpy(s->D, in, sizeof(double) * n); return 0;
+    case 5: memcpy(s->ut, in, sizeof(double) * n * 3); return 0;
+    case 8:
+      for (int64_t p = 0; p < n * OR_MAX_CUTS; ++p) s->digit[p] = (unsigned char)in[p];
+      return 0;
+  }
+  return -1;
+}
+
+/* tool state: xB[3], R[9], vB[3], wB[3] */
+void or_get_tool(const or_scene *s, double out[18]) {
+  memcpy(out, s->xB, sizeof(double) * 3);
+  memcpy(out + 3, s->R, sizeof(double) * 9);
+  memcpy(out + 12, s->vB, sizeof(double) * 3);
+  memcpy(out + 15, s->wB, sizeof(double) * 3);
+}
+void or_set_tool(or_scene *s, const double in[18]) {
+  memcpy(s->xB, in, sizeof(double) * 3);
+  memcpy(s->R, in + 3, sizeof(double) * 9);
+  memcpy(s->vB, in + 12, sizeof(double) * 3);
+  memcpy(s->wB, in + 15, sizeof(double) * 3);
+}
+/* blade frame at the current state: xe, n, e, d, ve (15 doubles) */
+void or_get_frame(const or_scene *s, double out[15]) {
+  or_frame fr;
+  or_make_frame(s, &fr);
+  memcpy(out, fr.xe, 24); memcpy(out + 3, fr.n, 24); memcpy(out + 6, fr.e, 24);
+  memcpy(out + 9, fr.d, 24); memcpy(out + 12, fr.ve, 24);
+}
+
+int64_t or_step_count(const or_scene *s) { return s->step; }
+unsigned or_errors(const or_scene *s) { return s->err; }
+void or_impulse_sum(const or_scene *s, double out[3]) { memcpy(out, s->impulse_sum, 24); }
+void or_last_wrench(const or_scene *s, double out[6]) { memcpy(out, s->lastF, 48); }
+int or_wrench_history(const or_scene *s, int64_t first, int64_t count, double *out) {
+  if (first < 0 || first + count > s->wrench_cap) return -1;
+  memcpy(out, s->wrench_hist + 6 * first, sizeof(double) * 6 * count);
+  return 0;
+}
+void or_grid_dims(const or_scene *s, int lo[3], int dim[3]) {
+  memcpy(lo, s->lo, sizeof(int) * 3);
+  memcpy(dim, s->dim, sizeof(int) * 3);
+}
+/* number of logical grids (occupied code slots) after the last P2G */
+int64_t or_slot_count(const or_scene *s) {
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  int64_t c = 0;
+  for (size_t i = 0; i < nn; ++i) c += s->nodes[i].cnt;
+  return c;
+}
+/* momentum sum_p m_p v_p */
+void or_momentum(const or_scene *s, double out[3]) {
+  out[0] = out[1] = out[2] = 0;
+  for (int64_t p = 0; p < s->n; ++p)
+    for (int a = 0; a < 3; ++a) out[a] += s->mp * s->v[3 * p + a];
+}

@@ -1,0 +1,342 @@
+"""ctypes shim over the FP64 C oracle (bm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the package smoke check
+and the CPU-baseline leg of the benchmark, never by the GPU library.  The shim
+only marshals arguments; every step of the method is in the C file.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_CUTS = 32
+MAX_SEG = 16
+
+E_INVERTED = 1
+E_NONFINITE = 2
+E_HIST_OVERFLOW = 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("E", C.c_double), ("nu", C.c_double), ("rho", C.c_double), ("dx", C.c_double),
+                ("origin", C.c_double * 3), ("V0", C.c_double), ("dt", C.c_double),
+                ("beta", C.c_double), ("g", C.c_double * 3), ("floor_on", C.c_int),
+                ("floor_z", C.c_double), ("s_R", C.c_double), ("s_n", C.c_double),
+                ("gamma_k", C.c_double), ("gamma_c", C.c_double), ("pair_on", C.c_int),
+                ("pair_mu_s", C.c_double), ("pair_mu_d", C.c_double), ("Gc", C.c_double),
+                ("zeta", C.c_double), ("u_min", C.c_double), ("b_back", C.c_double),
+                ("b_lead", C.c_double), ("h", C.c_double), ("tool_contact_on", C.c_int),
+                ("single_field", C.c_int)]
+
+
+class Seg(C.Structure):
+    _fields_ = [("n_steps", C.c_int), ("cut_id", C.c_int), ("v", C.c_double * 3),
+                ("w", C.c_double * 3)]
+
+
+class BladeC(C.Structure):
+    _fields_ = [("edge", C.c_double * 3), ("n", C.c_double * 3), ("e", C.c_double * 3),
+                ("d", C.c_double * 3), ("half_len", C.c_double), ("thick", C.c_double),
+                ("height", C.c_double), ("mu_s", C.c_double), ("mu_d", C.c_double),
+                ("mass", C.c_double), ("inertia", C.c_double * 9), ("x0", C.c_double * 3),
+                ("R0", C.c_double * 9), ("kv", C.c_double), ("rigid_interval", C.c_int),
+                ("nseg", C.c_int), ("seg", Seg * MAX_SEG)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            L.or_create.restype = C.c_void_p
+            L.or_create.argtypes = [C.POINTER(Params), C.POINTER(BladeC), C.c_int64, dp, C.c_int64]
+            L.or_destroy.argtypes = [C.c_void_p]
+            L.or_step.argtypes = [C.c_void_p, C.c_int]
+            L.or_step.restype = C.c_int
+            L.or_get.argtypes = [C.c_void_p, C.c_int, dp]
+            L.or_set.argtypes = [C.c_void_p, C.c_int, dp]
+            L.or_get_tool.argtypes = [C.c_void_p, dp]
+            L.or_set_tool.argtypes = [C.c_void_p, dp]
+            L.or_get_frame.argtypes = [C.c_void_p, dp]
+            L.or_step_count.argtypes = [C.c_void_p]
+            L.or_step_count.restype = C.c_int64
+            L.or_errors.argtypes = [C.c_void_p]
+            L.or_errors.restype = C.c_uint
+            L.or_impulse_sum.argtypes = [C.c_void_p, dp]
+            L.or_last_wrench.argtypes = [C.c_void_p, dp]
+            L.or_wrench_history.argtypes = [C.c_void_p, C.c_int64, C.c_int64, dp]
+            L.or_grid_dims.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.or_slot_count.argtypes = [C.c_void_p]
+            L.or_slot_count.restype = C.c_int64
+            L.or_momentum.argtypes = [C.c_void_p, dp]
+            L.or_bspline.argtypes = [C.c_double, dp, dp]
+            L.or_bspline.restype = C.c_int
+            L.or_psi.argtypes = [dp, C.c_double, C.c_double]
+            L.or_psi.restype = C.c_double
+            L.or_piola.argtypes = [dp, C.c_double, C.c_double, dp]
+            L.or_piola.restype = C.c_int
+            L.or_code.argtypes = [C.POINTER(C.c_ubyte), C.c_int]
+            L.or_code.restype = C.c_int64
+            L.or_digit.argtypes = [C.c_int64, C.c_int]
+            L.or_digit.restype = C.c_int
+            L.or_conflict.argtypes = [C.c_int64, C.c_int64]
+            L.or_conflict.restype = C.c_int
+            L.or_couple.argtypes = [C.c_int, C.POINTER(C.c_int64), dp, C.c_int, dp]
+            L.or_friction.argtypes = [dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_double, dp, dp]
+            L.or_box_closest.argtypes = [dp, dp, dp, dp, dp, dp, C.c_double, dp, dp, dp]
+            L.or_side_label.argtypes = [dp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_double]
+            L.or_side_label.restype = C.c_int
+            L.or_cut_progress.argtypes = [C.c_double] * 4
+            L.or_cut_progress.restype = C.c_double
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _arr(x, n=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    if n is not None:
+        assert a.size == n
+    return a
+
+
+# ---------------------------------------------------------------------------
+# unit-level functions
+# ---------------------------------------------------------------------------
+
+def bspline(xl: float):
+    w = np.zeros(3)
+    dw = np.zeros(3)
+    b = lib().or_bspline(float(xl), _dp(w), _dp(dw))
+    return b, w, dw
+
+
+def piola(F, mu, lam):
+    F = _arr(F, 9)
+    P = np.zeros(9)
+    clamped = lib().or_piola(_dp(F), mu, lam, _dp(P))
+    return P.reshape(3, 3), bool(clamped)
+
+
+def psi(F, mu, lam) -> float:
+    F = _arr(F, 9)
+    return lib().or_psi(_dp(F), mu, lam)
+
+
+def code(digits) -> int:
+    d = np.zeros(MAX_CUTS, dtype=np.uint8)
+    d[:len(digits)] = digits
+    return lib().or_code(d.ctypes.data_as(C.POINTER(C.c_ubyte)), MAX_CUTS)
+
+
+def digit(c: int, k: int) -> int:
+    return lib().or_digit(int(c), int(k))
+
+
+def conflict(a: int, b: int) -> bool:
+    return bool(lib().or_conflict(int(a), int(b)))
+
+
+def couple(codes, m, S):
+    codes = np.ascontiguousarray(np.asarray(codes, dtype=np.int64))
+    m = _arr(m)
+    S = np.ascontiguousarray(np.asarray(S, dtype=np.float64)).copy()
+    ns, nc = S.shape
+    lib().or_couple(ns, codes.ctypes.data_as(C.POINTER(C.c_int64)), _dp(m), nc, _dp(S))
+    return S
+
+
+def friction(u_hist, n, vrel, fn, meff, dt, gk, gc, mus, mud):
+    ft = np.zeros(3)
+    un = np.zeros(3)
+    lib().or_friction(_dp(_arr(u_hist, 3)), _dp(_arr(n, 3)), _dp(_arr(vrel, 3)), fn, meff, dt,
+                      gk, gc, mus, mud, _dp(ft), _dp(un))
+    return ft, un
+
+
+def box_closest(c, ax_n, ax_e, ax_d, hext, x, R):
+    xc = np.zeros(3)
+    nB = np.zeros(3)
+    phi = np.zeros(1)
+    lib().or_box_closest(_dp(_arr(c, 3)), _dp(_arr(ax_n, 3)), _dp(_arr(ax_e, 3)),
+                         _dp(_arr(ax_d, 3)), _dp(_arr(hext, 3)), _dp(_arr(x, 3)), R,
+                         _dp(xc), _dp(nB), _dp(phi))
+    return xc, nB, float(phi[0])
+
+
+def side_label(x, v, xe, n, e, d, ve, h, L, b_back, b_lead, dt) -> int:
+    return lib().or_side_label(_dp(_arr(x, 3)), _dp(_arr(v, 3)), _dp(_arr(xe, 3)),
+                               _dp(_arr(n, 3)), _dp(_arr(e, 3)), _dp(_arr(d, 3)),
+                               _dp(_arr(ve, 3)), h, L, b_back, b_lead, dt)
+
+
+def cut_progress(D, Jc, uc, Wth) -> float:
+    return lib().or_cut_progress(D, Jc, uc, Wth)
+
+
+# ---------------------------------------------------------------------------
+# scene
+# ---------------------------------------------------------------------------
+
+def _params(sc, single_field=False) -> Params:
+    p = Params()
+    p.E, p.nu, p.rho, p.dx = sc.E, sc.nu, sc.rho, sc.dx
+    p.origin = (C.c_double * 3)(*sc.origin)
+    p.V0, p.dt, p.beta = sc.V0, sc.dt, sc.beta
+    p.g = (C.c_double * 3)(*sc.gravity)
+    p.floor_on, p.floor_z = int(sc.floor), sc.floor_z
+    p.s_R, p.s_n, p.gamma_k, p.gamma_c = sc.s_R, sc.s_n, sc.gamma_k, sc.gamma_c
+    p.pair_on, p.pair_mu_s, p.pair_mu_d = int(sc.pair_contact), sc.pair_mu_s, sc.pair_mu_d
+    p.Gc, p.zeta, p.u_min = sc.G_c, sc.zeta, sc.u_min
+    p.b_back, p.b_lead, p.h = sc.b_back, sc.b_lead, sc.band_half_width
+    p.tool_contact_on = int(sc.tool_contact)
+    p.single_field = int(single_field)
+    return p
+
+
+def _blade(b) -> BladeC:
+    B = BladeC()
+    B.edge = (C.c_double * 3)(*b.edge_point)
+    B.n = (C.c_double * 3)(*b.normal)
+    B.e = (C.c_double * 3)(*b.edge_dir)
+    B.d = (C.c_double * 3)(*b.front_dir)
+    B.half_len, B.thick, B.height = b.half_length, b.thickness, b.height
+    B.mu_s, B.mu_d, B.mass = b.mu_s, b.mu_d, b.mass
+    B.inertia = (C.c_double * 9)(*b.inertia)
+    B.x0 = (C.c_double * 3)(*b.pose_x)
+    B.R0 = (C.c_double * 9)(*b.pose_R)
+    B.kv = b.servo_gain
+    B.rigid_interval = b.rigid_interval
+    assert len(b.segments) <= MAX_SEG
+    B.nseg = len(b.segments)
+    for i, s in enumerate(b.segments):
+        B.seg[i].n_steps = s.n_steps
+        B.seg[i].cut_id = s.cut_id
+        B.seg[i].v = (C.c_double * 3)(*s.v)
+        B.seg[i].w = (C.c_double * 3)(*s.omega)
+    return B
+
+
+class OracleScene:
+    """One FP64 scene built from a ``bm_inputs.Scene``."""
+
+    FIELDS = {"X": (0, 3), "x": (1, 3), "v": (2, 3), "F": (3, 9), "D": (4, 1),
+              "ut": (5, 3), "code": (6, 1), "J": (7, 3), "digits": (8, MAX_CUTS)}
+
+    def __init__(self, sc, single_field: bool = False, wrench_capacity: int = 0):
+        self._L = lib()
+        X = _arr(sc.X)
+        self.n = sc.n
+        self.params = _params(sc, single_field)
+        self._blade = _blade(sc.blade) if sc.blade is not None else None
+        cap = wrench_capacity if wrench_capacity > 0 else (
+            sum(s.n_steps for s in sc.blade.segments) + 16 if sc.blade is not None else 0)
+        self.wrench_capacity = cap
+        self._h = self._L.or_create(C.byref(self.params),
+                                    C.byref(self._blade) if self._blade is not None else None,
+                                    self.n, _dp(X), cap)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.or_destroy(h)
+            self._h = None
+
+    def step(self, n: int = 1) -> int:
+        return self._L.or_step(self._h, int(n))
+
+    def get(self, name: str) -> np.ndarray:
+        fid, w = self.FIELDS[name]
+        out = np.zeros(self.n * w)
+        self._L.or_get(self._h, fid, _dp(out))
+        if name == "code":
+            return out.astype(np.int64)
+        return out.reshape(self.n, w) if w > 1 else out
+
+    def set(self, name: str, value) -> None:
+        fid, w = self.FIELDS[name]
+        a = _arr(value, self.n * w)
+        if self._L.or_set(self._h, fid, _dp(a)) != 0:
+            raise ValueError(f"field {name} is read-only")
+
+    def tool(self) -> np.ndarray:
+        out = np.zeros(18)
+        self._L.or_get_tool(self._h, _dp(out))
+        return out
+
+    def set_tool(self, xB, R, vB, wB) -> None:
+        a = np.concatenate([_arr(xB, 3), _arr(R, 9), _arr(vB, 3), _arr(wB, 3)])
+        self._L.or_set_tool(self._h, _dp(a))
+
+    def frame(self) -> dict:
+        out = np.zeros(15)
+        self._L.or_get_frame(self._h, _dp(out))
+        return {"xe": out[0:3], "n": out[3:6], "e": out[6:9], "d": out[9:12], "ve": out[12:15]}
+
+    @property
+    def step_count(self) -> int:
+        return self._L.or_step_count(self._h)
+
+    @property
+    def errors(self) -> int:
+        return self._L.or_errors(self._h)
+
+    def impulse_sum(self) -> np.ndarray:
+        out = np.zeros(3)
+        self._L.or_impulse_sum(self._h, _dp(out))
+        return out
+
+    def last_wrench(self) -> np.ndarray:
+        out = np.zeros(6)
+        self._L.or_last_wrench(self._h, _dp(out))
+        return out
+
+    def wrench_history(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.step_count - first
+        out = np.zeros(6 * count)
+        if self._L.or_wrench_history(self._h, first, count, _dp(out)) != 0:
+            raise IndexError("wrench history out of range")
+        return out.reshape(count, 6)
+
+    def grid_dims(self):
+        lo = (C.c_int * 3)()
+        dim = (C.c_int * 3)()
+        self._L.or_grid_dims(self._h, lo, dim)
+        return tuple(lo), tuple(dim)
+
+    def slot_count(self) -> int:
+        return self._L.or_slot_count(self._h)
+
+    def momentum(self) -> np.ndarray:
+        out = np.zeros(3)
+        self._L.or_momentum(self._h, _dp(out))
+        return out
