@@ -698,10 +698,11 @@ static void substep(or_scene *s) {
 
   if (s->has_blade) {
     int dynamic = s->B.mass > 0;
-    if (!dynamic) { /* prescribed twist of the current segment */
+    if (!dynamic && sg) { /* prescribed twist of the current segment; with no
+                             segment left the last (or externally set) twist holds */
       for (int i = 0; i < 3; ++i) {
-        s->vB[i] = sg ? sg->v[i] : 0.0;
-        s->wB[i] = sg ? sg->w[i] : 0.0;
+        s->vB[i] = sg->v[i];
+        s->wB[i] = sg->w[i];
       }
     }
     /* D_p is reset to zero at the beginning of each new cut (Sec. III-A) */
