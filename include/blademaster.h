@@ -1,0 +1,250 @@
+/*
+ * blademaster.h -- C ABI of the GB300 TLMPM cutting library.
+ *
+ * One call of bm_step() advances a scene by whole TLMPM substeps of the
+ * cutting method of "BladeMaster: Real-Time Robotic Cutting Simulation with
+ * Online-Generated Persistent Discontinuities" (arXiv 2609.27342):
+ *   (a) side labels from the swept blade band      Sec. III-C, Eq. 3, 4, 6, 7
+ *   (b) hyperelastic stress                         Sec. III-B (neo-Hookean)
+ *   (c) label-masked P2G on the reference grid      Sec. III-B, Eq. 1, 2
+ *   (d) coupled grid update, tool and pair contact  Sec. III-D/E, Eq. 8-16
+ *   (e) PIC/FLIP G2P, MUSL re-scatter, F update     Sec. III-B, Eq. 17
+ * The problem statement the calls follow: a rigid tool's pose and twist drive
+ * each substep and its reaction wrench is returned (Sec. III-A); cuts appear
+ * online from blade motion (Sec. III-C); the rigid system may run at a lower
+ * rate and receives an interval-averaged wrench (Sec. III-G).
+ *
+ * Conventions (every call):
+ *   - SI units; doubles for tool state, float32 for particle state.
+ *   - Return value: BM_OK (0) or a negative bm_status; bm_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.
+ *   - Handles are owned by the library and released by the matching destroy.
+ *   - Device memory comes from the caller's allocator when one is given
+ *     (bm_alloc), else from cudaMalloc; all work is enqueued on the stream
+ *     given at creation.  One owner per handle: calls on one handle are not
+ *     thread-safe.
+ *   - Asynchrony: bm_step/bm_batch_step enqueue work and return launch
+ *     errors immediately; the device error word (bit set of BM_ERRBIT_*) is
+ *     sticky and is read by bm_read_state/bm_scene_info/bm_tool_wrench, which
+ *     synchronise the stream.
+ *   - Particle arrays crossing the ABI are in the caller's original particle
+ *     order, array-of-structs (x: [n][3], F: [n][9] row-major).
+ */
+#ifndef BLADEMASTER_H
+#define BLADEMASTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BM_MAX_CUTS 32     /* cut-side digits per particle (two 32-bit masks) */
+#define BM_MAX_SEGMENTS 16 /* trajectory segments per blade */
+
+typedef enum {
+  BM_OK = 0,
+  BM_E_INVALID = -1,         /* bad argument or handle */
+  BM_E_OOM = -2,             /* allocation failed (caller allocator or cudaMalloc) */
+  BM_E_CUDA = -3,            /* CUDA runtime error (message in bm_last_error) */
+  BM_E_SLOT_OVERFLOW = -4,   /* logical-grid slots exceeded their capacity */
+  BM_E_INVERTED = -5,        /* det F <= 1e-6 met (clamped, simulation continued) */
+  BM_E_NONFINITE = -6,       /* NaN/Inf in particle position or velocity */
+  BM_E_CONTACT_OVERFLOW = -7,/* pair-contact history or cell capacity exceeded */
+  BM_E_TIMEOUT = -8,         /* a bounded device wait gave up */
+  BM_E_TOO_MANY_CUTS = -9,   /* cut id outside [0, BM_MAX_CUTS) */
+  BM_E_CAPACITY = -10        /* batch pool has no room for the scene */
+} bm_status;
+
+/* bits of the sticky device error word (bm_scene_info.error_bits) */
+#define BM_ERRBIT_SLOT_OVERFLOW 1u
+#define BM_ERRBIT_INVERTED 2u
+#define BM_ERRBIT_NONFINITE 4u
+#define BM_ERRBIT_CONTACT_OVERFLOW 8u
+#define BM_ERRBIT_TOO_MANY_CUTS 16u
+
+typedef struct bm_scene_s *bm_scene_t;
+typedef struct bm_batch_s *bm_batch_t;
+
+/* Device allocator callbacks (e.g. PyTorch's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` bytes on `stream`, or NULL;
+ * free releases it.  Pass NULL for cudaMalloc/cudaFree. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, void *stream, void *ctx);
+  void *ctx;
+} bm_alloc;
+
+/* Material, discretisation and contact parameters of one scene.
+ * Particle mass m_p = rho V0 and contact radius R_p = s_R V0^(1/3) / 2
+ * (Sec. III-E) are uniform over the scene.  Fields marked "<=0 -> default"
+ * take the default when non-positive. */
+typedef struct {
+  double E, nu, rho;         /* neo-Hookean: mu = E/(2(1+nu)), lambda = E nu/((1+nu)(1-2nu)) */
+  double dx;                 /* reference-grid spacing; node i sits at origin + i dx (Eq. 1) */
+  double origin[3];
+  double V0;                 /* reference volume per particle V_p^0 */
+  double dt;                 /* substep */
+  double beta;               /* PIC/FLIP blend (Eq. 17), in [0, 1] */
+  double gravity[3];
+  int floor_enabled;         /* frictionless half-space z >= floor_z */
+  double floor_z;
+  double s_R, s_n;           /* contact radius and normal response scales (Sec. III-E) */
+  double gamma_k, gamma_c;   /* tangential stiffness / damping ratios (Eq. 12) */
+  int pair_contact;          /* material-material contact (Eq. 10-13) */
+  double pair_mu_s, pair_mu_d;
+  double G_c, zeta;          /* W_th = G_c V0^(2/3) (1 - zeta)/zeta (Eq. 5) */
+  double u_min;              /* minimum cut-advance speed (Eq. 5) */
+  double b_back, b_lead;     /* band rear / lead extent, <=0 -> dx (Eq. 4) */
+  double band_half_width;    /* h_k, <=0 -> 6 dx (Sec. III-D) */
+  int tool_contact;          /* 0: the blade only assigns labels */
+  int wrench_history;        /* substeps of per-substep wrench kept on device */
+} bm_scene_desc;
+
+/* A piece of blade trajectory: a world-frame twist (about the tool-frame
+ * origin x_B) held for n_steps substeps.  Kinematic tool: the prescribed
+ * twist.  Dynamic tool: the servo target.  cut_id >= 0 is the cut (ternary
+ * digit k of Eq. 7) this stroke creates; -1 = non-cutting move. */
+typedef struct {
+  int n_steps;
+  int cut_id;
+  double v[3], omega[3];
+} bm_segment;
+
+/* Planar blade: an oriented box, half-thickness along n, half-length along e,
+ * `height` behind the edge along -d (tool-frame axes of Eq. 3).  mass <= 0
+ * makes the tool kinematic (w_B = 0, Eq. 15). */
+typedef struct {
+  double edge_point[3], normal[3], edge_dir[3], front_dir[3]; /* tool frame */
+  double half_length, thickness, height;
+  double mu_s, mu_d;                                       /* tool friction */
+  double mass, inertia[9];                                 /* body frame, row-major */
+  double pose_x[3], pose_R[9];                             /* initial pose (tool->world) */
+  double servo_gain;                                       /* <=0 -> 1/(10 dt) */
+  int rigid_interval;                                      /* substeps per rigid update, >=1 */
+  int n_segments;
+  bm_segment segments[BM_MAX_SEGMENTS];
+} bm_blade_desc;
+
+/* Field ids for bm_read_state / bm_write_state.  Element types:
+ *   X, x, v, ut: float32 [n][3];  F: float32 [n][9];  D: float32 [n];
+ *   CODE: int64 [n] ternary code c_p of Eq. 7 (read only);
+ *   MASK1, MASK2: uint32 [n] -- bit k set <=> digit k is 1 (resp. 2). */
+enum {
+  BM_FIELD_X = 1u << 0,
+  BM_FIELD_x = 1u << 1,
+  BM_FIELD_v = 1u << 2,
+  BM_FIELD_F = 1u << 3,
+  BM_FIELD_D = 1u << 4,
+  BM_FIELD_UT = 1u << 5,
+  BM_FIELD_CODE = 1u << 6,
+  BM_FIELD_MASK1 = 1u << 7,
+  BM_FIELD_MASK2 = 1u << 8
+};
+#define BM_NUM_FIELDS 9
+
+typedef struct {
+  int64_t n_particles;
+  int64_t n_nodes;           /* reference-grid nodes covering every stencil */
+  int64_t n_slots;           /* occupied logical-grid slots (Sec. III-G compact slots) */
+  int64_t slot_capacity;
+  int64_t step;              /* substeps taken */
+  uint32_t error_bits;       /* sticky BM_ERRBIT_* word */
+  int grid_lo[3], grid_dim[3];
+} bm_scene_info;
+
+/* ---- scene ------------------------------------------------------------- */
+
+/* Create a scene from n reference positions X_ref (host, float32 [n][3]).
+ * Builds the fixed reference stencil table (Eq. 1: the node-to-particle
+ * neighbourhood never changes), sets x = X, v = 0, F = I, D = 0, all codes 0.
+ * `alloc` may be NULL.  `stream` is a cudaStream_t (NULL = default stream). */
+int bm_scene_create(const bm_scene_desc *desc, const float *X_ref, int64_t n,
+                    const bm_alloc *alloc, void *stream, bm_scene_t *out);
+
+/* Attach the scene's blade (one per scene); *blade_id receives 0. */
+int bm_add_blade(bm_scene_t s, const bm_blade_desc *b, int *blade_id);
+
+/* Override the tool pose (x_B, row-major R tool->world) and world twist
+ * (v_B, omega_B) from the next substep on -- the external rigid-system path of
+ * Sec. III-A.  pose = {x[3], R[9]}, twist = {v[3], omega[3]}. */
+int bm_set_tool_state(bm_scene_t s, int blade_id, const double pose[12], const double twist[6]);
+int bm_get_tool_state(bm_scene_t s, int blade_id, double pose[12], double twist[6]);
+
+/* Advance n_substeps substeps on the scene's stream (one launch per kernel
+ * per substep: the plain one-scene-per-launch path). */
+int bm_step(bm_scene_t s, int n_substeps);
+
+/* Copy the fields in field_mask into dst[i] (one pointer per set bit, in bit
+ * order).  dst_on_device != 0: dst are device pointers.  Synchronises the
+ * stream; returns the error word via bm_scene_info. */
+int bm_read_state(bm_scene_t s, uint32_t field_mask, void *const *dst, int dst_on_device);
+
+/* Overwrite fields (x, v, F, D, UT, MASK1, MASK2) from src, same layout.
+ * Writing masks rebuilds the logical-grid slots before the next substep. */
+int bm_write_state(bm_scene_t s, uint32_t field_mask, const void *const *src, int src_on_device);
+
+/* Interval-averaged reaction wrench {F[3], tau[3]} of the last completed
+ * rigid interval (Eq. 16, Sec. III-G); tau about x_B.  Synchronises. */
+int bm_tool_wrench(bm_scene_t s, int blade_id, double out[6]);
+
+/* Per-substep reaction wrenches of substeps [first, first+count) (count*6
+ * doubles, host).  Only the first desc.wrench_history substeps are kept. */
+int bm_wrench_history(bm_scene_t s, int blade_id, int64_t first, int64_t count, double *out);
+
+int bm_scene_info_get(bm_scene_t s, bm_scene_info *out);
+int bm_scene_destroy(bm_scene_t s);
+
+/* ---- batches of uneven scenes -------------------------------------------
+ * A batch owns packed device pools (particles, nodes, slots) with a fixed
+ * capacity.  Scenes moved into it keep their handles; bm_batch_step advances
+ * every member scene by n substeps from one CUDA-graph launch per chunk of
+ * substeps, with no host work between substeps. */
+typedef struct {
+  int64_t max_particles;   /* pool capacities */
+  int64_t max_nodes;
+  int64_t max_slots;       /* <=0 -> 4 x max_nodes */
+  int max_scenes;
+  int graph_chunk;         /* substeps per captured graph, <=0 -> 16 */
+  int particle_tile;       /* particles per CTA tile: 128, 256 or 512; <=0 -> 256 */
+  int node_tile;           /* nodes per CTA tile: 64..512; <=0 -> 128 */
+  int pair_contact;        /* reserve pair-contact history for member scenes */
+} bm_batch_desc;
+
+int bm_batch_create(const bm_batch_desc *desc, const bm_alloc *alloc, void *stream,
+                    bm_batch_t *out);
+/* Move a scene's device state into the batch pools (BM_E_CAPACITY if it
+ * does not fit).  The scene's own buffers are released. */
+int bm_batch_add(bm_batch_t b, bm_scene_t s);
+/* Move a scene out of the batch into buffers of its own. */
+int bm_batch_remove(bm_batch_t b, bm_scene_t s);
+int bm_batch_step(bm_batch_t b, int n_substeps);
+/* Bytes of device memory a scene with these parameters takes in a batch. */
+int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
+                       int64_t *particles, int64_t *nodes, int64_t *bytes);
+/* Tool state of every member, in membership order (the order of
+ * bm_batch_members): states[n][18] = {x_B[3], R[9], v_B[3], omega_B[3]};
+ * n must equal the member count.  on_device != 0: a device pointer.
+ * Stream-ordered, no synchronisation (the per-substep input of an external
+ * rigid-body system, Sec. III-A). */
+int bm_batch_set_tool_states(bm_batch_t b, const double *states, int n, int on_device);
+/* Interval-averaged wrench of every member, out[n][6] (Eq. 16, Sec. III-G).
+ * on_device != 0: a device pointer, stream-ordered; otherwise the call
+ * synchronises the stream and fills host memory. */
+int bm_batch_tool_wrenches(bm_batch_t b, double *out, int n, int on_device);
+/* Member scenes in membership order; returns the member count. */
+int bm_batch_members(bm_batch_t b, bm_scene_t *out, int cap);
+/* Largest sticky error word over the members (OR of BM_ERRBIT_*); syncs. */
+int bm_batch_errors(bm_batch_t b, uint32_t *bits);
+/* Set tile sizes used by subsequent bm_batch_step calls (autotuner hook). */
+int bm_batch_set_tiles(bm_batch_t b, int particle_tile, int node_tile);
+int bm_batch_destroy(bm_batch_t b);
+
+const char *bm_last_error(void);
+const char *bm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLADEMASTER_H */

@@ -1,0 +1,148 @@
+// Internal device-side layout of the GB300 TLMPM cutting library.
+//
+// Memory is organised as "worlds": packed pools of particles, reference-grid
+// nodes and logical-grid slots that hold one scene (the plain path) or many
+// scenes (a batch).  Every kernel walks a work list of tiles, each tile
+// naming its scene, so one code path serves both.
+//
+// Particle state is structure-of-arrays float32, particles sorted by their
+// fixed reference base cell (the TLMPM stencil never changes, Eq. 1), so the
+// node-to-particle neighbourhood is a static CSR table (cell_start) and P2G
+// is an atomic-free gather in a fixed order: deterministic, bit-identical
+// whether a scene runs alone or inside a batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/blademaster.h"
+
+#define BM_MAXS 8            // logical grids (distinct codes) per node
+#define BM_HIST 8            // pair-contact history entries per particle
+#define BM_WRENCH_W 6
+
+struct DevSeg {
+  int n_steps, cut_id;
+  double v[3], w[3];
+};
+
+// One scene, resident in device memory.  Static parameters are written at
+// creation; the tool block and counters are updated by kernels.
+struct DevScene {
+  // ranges inside the world pools
+  int p_begin, n_p;
+  int node_begin, n_node;
+  int cell_begin, n_cell;
+  int slot_begin, slot_cap;
+  int ptile_begin, n_ptile;
+  int ntile_begin, n_ntile;
+  int hist_begin;           // wrench history offset (in wrench records)
+  int hist_cap;
+  int nb[3];                // base-cell grid
+  int nn[3];                // node grid = nb + 2
+  // material / discretisation (float32 for the particle kernels)
+  float dx, inv_dx;
+  float mp, V0, Rp, dt, beta, g[3], mu, lam;
+  float Wth, u_min, b_back, b_lead, h;
+  float s_n, gamma_k, gamma_c;
+  float pair_mu_s, pair_mu_d;
+  float floor_z;
+  int floor_on, pair_on, tool_contact_on, has_blade;
+  // float64 copies used by the exact label path and the tool integrator
+  double dt_d, h_d, L_d, b_back_d, b_lead_d;
+  double origin_d[3];
+  // blade (static)
+  double edgeT[3], nT[3], eT[3], dT[3];
+  double half_len, half_thick, half_height, mu_s, mu_d;
+  double mass, Ib_inv[9], kv;
+  int rigid_interval, nseg;
+  DevSeg seg[BM_MAX_SEGMENTS];
+  // blade (dynamic, float64)
+  double xB[3], R[9], vB[3], wB[3];
+  double accF[3], accT[3];
+  int acc_cnt, cur_cut;
+  double lastW[6];
+  // frame of the current substep (written by the tool kernel / set-up)
+  int cut, reset_D;
+  double dxe[3], dn[3], de[3], dd[3], dve[3];
+  float fxe[3], fn[3], fe[3], fd[3], fve[3], fc[3], fxB[3], fvB[3], fwB[3];
+  float fIinv[9], finv_mass, fmu_s, fmu_d, fhext[3], fL;
+  // counters and flags
+  long long step;
+  unsigned int err;
+  int list_count;
+  int need_rebuild;
+  int n_slots;
+  int pad_[2];
+};
+
+struct PPool {
+  float *fx[3];
+  uint32_t *base;           // packed local base cell: bx | by << 10 | bz << 20
+  float *x[3], *v[3], *F[9], *D, *ut[3];
+  uint32_t *s1, *s2;        // bit k: digit k == 1 (s1) or == 2 (s2)
+  float *A[9];              // -dt V0 P(F), written by the pre kernel
+  float *J[3];              // contact + body impulse of this substep
+  int *perm;                // pool index -> caller's particle index
+  int *list;                // new side labels of this substep (per-scene range)
+  // pair contact
+  int *hkey;                // hashed cell of each particle
+  int *hcell;               // cell coordinates packed (for exact match)
+  int *horder;              // particles sorted by bucket
+  int *hist_partner[2];     // pair history, double buffered by step parity
+  float *hist_u[2];         // [p * BM_HIST + k] * 3
+};
+
+struct NPool {
+  int *cell_start;          // per scene n_cell + 1 entries (pool particle indices)
+  int *slot_off;            // first slot of each node (pool slot index)
+  uint8_t *slot_cnt;        // logical grids at each node
+  uint2 *tmp_codes;         // [node * BM_MAXS] scratch for the rebuild
+  int *tile_sum;            // per node tile: slots in the tile (scan scratch)
+};
+
+struct SPool {
+  float4 *vold;             // xyz = v_old (Eq. 9), w = m
+  float4 *vnew;             // xyz = v_new (Eq. 9)
+  float4 *vstar;            // xyz = v* (MUSL)
+  uint2 *code;              // (s1, s2)
+};
+
+struct HashPool {           // pair-contact spatial hash (world-wide table)
+  int *bucket_start;        // [n_buckets + 1]
+  int *bucket_fill;         // [n_buckets]
+  int *block_sum;
+  int n_buckets;
+};
+
+struct World {
+  DevScene *scenes;
+  PPool P;
+  NPool N;
+  SPool S;
+  HashPool H;
+  double *wpart;            // per particle tile wrench partials (6 doubles)
+  double *whist;            // wrench history records (6 doubles)
+};
+
+// tiles: x = scene slot, y = first pool index, z = count, w = tile id
+struct LaunchSet {
+  const int4 *ptiles;
+  int n_ptiles;
+  int ptile_size;
+  const int4 *ntiles;
+  int n_ntiles;
+  int ntile_size;
+  const int *scene_ids;     // scenes in this set
+  int n_scenes;
+  int any_pair;             // some scene has pair contact
+  int pair_n_particles;     // particles of pair-contact scenes (hash sizing)
+};
+
+// kernel launchers (bm_kernels.cu)
+cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st);
+cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t st);
+cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t st, int force);
+cudaError_t bm_launch_io(const World &w, int scene_slot, int p_begin, int n, int field, void *buf,
+                         int to_device_pool, cudaStream_t st);
+cudaError_t bm_launch_code(const World &w, int p_begin, int n, int64_t *out, cudaStream_t st);

@@ -1,0 +1,1145 @@
+// Host runtime of the GB300 TLMPM cutting library: scene construction (the
+// fixed reference stencil table of Eq. 1), packed multi-scene worlds with a
+// first-fit range allocator, CUDA-graph capture of batched substeps, state
+// I/O, and the C ABI declared in include/blademaster.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "bm_internal.cuh"
+
+// kernels used only here (bm_kernels.cu)
+cudaError_t bm_launch_set_tools(const World &w, const int *scene_ids, int n, const double *states,
+                                cudaStream_t st);
+cudaError_t bm_launch_get_wrenches(const World &w, const int *scene_ids, int n, double *out,
+                                   cudaStream_t st);
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(BM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+struct Allocator {
+  bm_alloc a{};
+  bool has = false;
+  cudaStream_t st = nullptr;
+  void *alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (has) return a.alloc(bytes, (void *)st, a.ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void release(void *p) {
+    if (!p) return;
+    if (has) a.free(p, (void *)st, a.ctx);
+    else cudaFree(p);
+  }
+};
+
+// first-fit allocator of index ranges inside a pool
+struct RangeAlloc {
+  int64_t cap = 0;
+  std::vector<std::pair<int64_t, int64_t>> fr;  // (begin, length), sorted by begin
+  void init(int64_t c) {
+    cap = c;
+    fr.clear();
+    if (c > 0) fr.push_back({0, c});
+  }
+  int64_t take(int64_t n) {
+    if (n <= 0) return 0;
+    for (size_t i = 0; i < fr.size(); ++i)
+      if (fr[i].second >= n) {
+        int64_t b = fr[i].first;
+        fr[i].first += n;
+        fr[i].second -= n;
+        if (fr[i].second == 0) fr.erase(fr.begin() + (long)i);
+        return b;
+      }
+    return -1;
+  }
+  void give(int64_t b, int64_t n) {
+    if (n <= 0) return;
+    auto it = std::lower_bound(fr.begin(), fr.end(), std::make_pair(b, (int64_t)0));
+    it = fr.insert(it, {b, n});
+    size_t i = (size_t)(it - fr.begin());
+    if (i + 1 < fr.size() && fr[i].first + fr[i].second == fr[i + 1].first) {
+      fr[i].second += fr[i + 1].second;
+      fr.erase(fr.begin() + (long)i + 1);
+    }
+    if (i > 0 && fr[i - 1].first + fr[i - 1].second == fr[i].first) {
+      fr[i - 1].second += fr[i].second;
+      fr.erase(fr.begin() + (long)i);
+    }
+  }
+};
+
+}  // namespace
+
+struct WorldH;
+
+struct bm_scene_s {
+  bm_scene_desc desc{};
+  bm_blade_desc blade{};
+  bool has_blade = false;
+  int64_t n = 0;
+  std::vector<float> X;               // caller order, [n][3]
+  std::vector<int> cell_start_rel;    // n_cell + 1, relative to the scene's first particle
+  int nb[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
+  int64_t n_cell = 0, n_node = 0, slot_cap = 0, hist_cap = 0;
+  WorldH *world = nullptr;
+  bool own_world = false;
+  int slot = -1;
+  int64_t p_begin = 0, cell_begin = 0, node_begin = 0, slot_begin = 0, hist_begin = 0;
+  int ptile_begin = 0, n_ptile = 0, ntile_begin = 0, n_ntile = 0;
+  DevScene tmpl{};                    // static fields (host template)
+  // staged fresh state, uploaded when the scene first enters a world
+  std::vector<float> h_fx[3];
+  std::vector<uint32_t> h_base;
+  std::vector<int> h_perm;
+  bool fresh = true;
+  cudaStream_t home_stream = nullptr;  // stream and allocator given at creation
+  bm_alloc home_alloc{};
+  bool has_home_alloc = false;
+};
+
+struct WorldH {
+  Allocator al;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int64_t cap_p = 0, cap_cell = 0, cap_node = 0, cap_slot = 0, cap_hist = 0;
+  int cap_scenes = 0, cap_ptile = 0, cap_ntile = 0;
+  bool pair = false;
+  World w{};
+  std::vector<void *> allocs;
+  RangeAlloc rp, rcell, rnode, rslot, rhist;
+  std::vector<int> free_slots;
+  int4 *d_ptiles = nullptr, *d_ntiles = nullptr;
+  int *d_scene_ids = nullptr, *d_slot_ids = nullptr;
+  double *d_stage = nullptr;
+  int ptile_size = 256, ntile_size = 128;
+  int graph_chunk = 16;
+  std::vector<bm_scene_s *> members;
+  bool tiles_dirty = true;
+  int n_ptiles = 0, n_ntiles = 0;
+  std::map<int, cudaGraphExec_t> graphs;
+
+  template <class T>
+  T *get(int64_t count) {
+    void *p = al.alloc(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+    if (p) allocs.push_back(p);
+    return (T *)p;
+  }
+  void drop_graphs() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+  ~WorldH() {
+    drop_graphs();
+    if (st) cudaStreamSynchronize(st);
+    for (void *p : allocs) al.release(p);
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+};
+
+struct bm_batch_s {
+  WorldH *world = nullptr;
+};
+
+namespace {
+
+int world_alloc(WorldH *W) {
+  const int64_t P = W->cap_p;
+  PPool &pp = W->w.P;
+  bool ok = true;
+  auto F = [&](float *&ptr, int64_t c) {
+    ptr = W->get<float>(c);
+    ok &= ptr != nullptr;
+  };
+  auto U = [&](uint32_t *&ptr, int64_t c) {
+    ptr = W->get<uint32_t>(c);
+    ok &= ptr != nullptr;
+  };
+  auto I = [&](int *&ptr, int64_t c) {
+    ptr = W->get<int>(c);
+    ok &= ptr != nullptr;
+  };
+  for (int a = 0; a < 3; ++a) {
+    F(pp.fx[a], P);
+    F(pp.x[a], P);
+    F(pp.v[a], P);
+    F(pp.ut[a], P);
+    F(pp.J[a], P);
+  }
+  for (int k = 0; k < 9; ++k) {
+    F(pp.F[k], P);
+    F(pp.A[k], P);
+  }
+  F(pp.D, P);
+  U(pp.base, P);
+  U(pp.s1, P);
+  U(pp.s2, P);
+  I(pp.perm, P);
+  I(pp.list, P);
+  if (W->pair) {
+    I(pp.hkey, P);
+    I(pp.hcell, P);
+    I(pp.horder, P);
+    for (int b = 0; b < 2; ++b) {
+      I(pp.hist_partner[b], P * BM_HIST);
+      F(pp.hist_u[b], P * BM_HIST * 3);
+    }
+  }
+  NPool &np = W->w.N;
+  I(np.cell_start, W->cap_cell);
+  I(np.slot_off, W->cap_node);
+  np.slot_cnt = W->get<uint8_t>(W->cap_node);
+  ok &= np.slot_cnt != nullptr;
+  np.tmp_codes = W->get<uint2>(W->cap_node * BM_MAXS);
+  ok &= np.tmp_codes != nullptr;
+  I(np.tile_sum, W->cap_ntile);
+  SPool &sp = W->w.S;
+  sp.vold = W->get<float4>(W->cap_slot);
+  sp.vnew = W->get<float4>(W->cap_slot);
+  sp.vstar = W->get<float4>(W->cap_slot);
+  sp.code = W->get<uint2>(W->cap_slot);
+  ok &= sp.vold && sp.vnew && sp.vstar && sp.code;
+  W->w.scenes = W->get<DevScene>(W->cap_scenes);
+  W->w.wpart = W->get<double>((int64_t)W->cap_ptile * 6);
+  W->w.whist = W->get<double>(std::max<int64_t>(W->cap_hist, 1) * 6);
+  W->d_ptiles = W->get<int4>(W->cap_ptile);
+  W->d_ntiles = W->get<int4>(W->cap_ntile);
+  W->d_scene_ids = W->get<int>(W->cap_scenes);
+  W->d_slot_ids = W->get<int>(W->cap_scenes);
+  W->d_stage = W->get<double>((int64_t)W->cap_scenes * 18);
+  ok &= W->w.scenes && W->w.wpart && W->w.whist && W->d_ptiles && W->d_ntiles && W->d_scene_ids &&
+        W->d_slot_ids && W->d_stage;
+  if (!ok) return fail(BM_E_OOM, "device allocation failed");
+  W->rp.init(W->cap_p);
+  W->rcell.init(W->cap_cell);
+  W->rnode.init(W->cap_node);
+  W->rslot.init(W->cap_slot);
+  W->rhist.init(W->cap_hist);
+  W->free_slots.clear();
+  for (int i = W->cap_scenes - 1; i >= 0; --i) W->free_slots.push_back(i);
+  std::vector<int> ids(W->cap_scenes);
+  for (int i = 0; i < W->cap_scenes; ++i) ids[i] = i;
+  CK(cudaMemcpy(W->d_slot_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemset(W->w.wpart, 0, sizeof(double) * (size_t)W->cap_ptile * 6));
+  return BM_OK;
+}
+
+int64_t tiles_for(int64_t n, int tile) { return (n + tile - 1) / tile; }
+
+// assign tile ranges to every member, upload the tile lists and the ranges
+int rebuild_tiles(WorldH *W) {
+  std::vector<int4> pt, nt;
+  std::vector<int> ids;
+  for (bm_scene_s *s : W->members) {
+    s->ptile_begin = (int)pt.size();
+    for (int64_t b = 0; b < s->n; b += W->ptile_size) {
+      int c = (int)std::min<int64_t>(W->ptile_size, s->n - b);
+      pt.push_back(make_int4(s->slot, (int)(s->p_begin + b), c, (int)pt.size()));
+    }
+    s->n_ptile = (int)pt.size() - s->ptile_begin;
+    s->ntile_begin = (int)nt.size();
+    for (int64_t b = 0; b < s->n_node; b += W->ntile_size) {
+      int c = (int)std::min<int64_t>(W->ntile_size, s->n_node - b);
+      nt.push_back(make_int4(s->slot, (int)(s->node_begin + b), c, (int)nt.size()));
+    }
+    s->n_ntile = (int)nt.size() - s->ntile_begin;
+    ids.push_back(s->slot);
+  }
+  if ((int64_t)pt.size() > W->cap_ptile || (int64_t)nt.size() > W->cap_ntile)
+    return fail(BM_E_CAPACITY, "tile lists exceed the batch capacity");
+  if (!pt.empty()) CK(cudaMemcpy(W->d_ptiles, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));
+  if (!nt.empty()) CK(cudaMemcpy(W->d_ntiles, nt.data(), sizeof(int4) * nt.size(), cudaMemcpyHostToDevice));
+  if (!ids.empty()) CK(cudaMemcpy(W->d_scene_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
+  for (bm_scene_s *s : W->members) {
+    int r[4] = {s->ptile_begin, s->n_ptile, s->ntile_begin, s->n_ntile};
+    CK(cudaMemcpy((char *)(W->w.scenes + s->slot) + offsetof(DevScene, ptile_begin), r, sizeof r,
+                  cudaMemcpyHostToDevice));
+  }
+  W->n_ptiles = (int)pt.size();
+  W->n_ntiles = (int)nt.size();
+  W->tiles_dirty = false;
+  W->drop_graphs();
+  return BM_OK;
+}
+
+LaunchSet scene_set(const WorldH *W, const bm_scene_s *s) {
+  LaunchSet ls{};
+  ls.ptiles = W->d_ptiles + s->ptile_begin;
+  ls.n_ptiles = s->n_ptile;
+  ls.ptile_size = W->ptile_size;
+  ls.ntiles = W->d_ntiles + s->ntile_begin;
+  ls.n_ntiles = s->n_ntile;
+  ls.ntile_size = W->ntile_size;
+  ls.scene_ids = W->d_slot_ids + s->slot;
+  ls.n_scenes = 1;
+  ls.any_pair = s->desc.pair_contact;
+  return ls;
+}
+
+LaunchSet world_set(const WorldH *W) {
+  LaunchSet ls{};
+  ls.ptiles = W->d_ptiles;
+  ls.n_ptiles = W->n_ptiles;
+  ls.ptile_size = W->ptile_size;
+  ls.ntiles = W->d_ntiles;
+  ls.n_ntiles = W->n_ntiles;
+  ls.ntile_size = W->ntile_size;
+  ls.scene_ids = W->d_scene_ids;
+  ls.n_scenes = (int)W->members.size();
+  for (auto *s : W->members) ls.any_pair |= s->desc.pair_contact;
+  return ls;
+}
+
+void fill_template(bm_scene_s *s) {
+  const bm_scene_desc &d = s->desc;
+  DevScene &t = s->tmpl;
+  std::memset(&t, 0, sizeof t);
+  t.nb[0] = s->nb[0]; t.nb[1] = s->nb[1]; t.nb[2] = s->nb[2];
+  t.nn[0] = s->nn[0]; t.nn[1] = s->nn[1]; t.nn[2] = s->nn[2];
+  t.n_p = (int)s->n;
+  t.n_node = (int)s->n_node;
+  t.n_cell = (int)s->n_cell;
+  t.slot_cap = (int)s->slot_cap;
+  t.hist_cap = (int)s->hist_cap;
+  t.dx = (float)d.dx;
+  t.inv_dx = (float)(1.0 / d.dx);
+  const double mp = d.rho * d.V0;
+  t.mp = (float)mp;
+  t.V0 = (float)d.V0;
+  t.Rp = (float)(d.s_R * std::cbrt(d.V0) / 2.0);
+  t.dt = (float)d.dt;
+  t.beta = (float)d.beta;
+  for (int a = 0; a < 3; ++a) t.g[a] = (float)d.gravity[a];
+  t.mu = (float)(d.E / (2.0 * (1.0 + d.nu)));
+  t.lam = (float)(d.E * d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
+  t.Wth = (float)(d.G_c * std::pow(d.V0, 2.0 / 3.0) * (1.0 - d.zeta) / d.zeta);
+  t.u_min = (float)d.u_min;
+  t.h_d = d.band_half_width > 0 ? d.band_half_width : 6.0 * d.dx;
+  t.b_back_d = d.b_back > 0 ? d.b_back : d.dx;
+  t.b_lead_d = d.b_lead > 0 ? d.b_lead : d.dx;
+  t.h = (float)t.h_d;
+  t.b_back = (float)t.b_back_d;
+  t.b_lead = (float)t.b_lead_d;
+  t.dt_d = d.dt;
+  t.s_n = (float)d.s_n;
+  t.gamma_k = (float)d.gamma_k;
+  t.gamma_c = (float)d.gamma_c;
+  t.pair_mu_s = (float)d.pair_mu_s;
+  t.pair_mu_d = (float)d.pair_mu_d;
+  t.floor_z = (float)d.floor_z;
+  t.floor_on = d.floor_enabled;
+  t.pair_on = d.pair_contact;
+  t.tool_contact_on = d.tool_contact;
+  for (int a = 0; a < 3; ++a) t.origin_d[a] = d.origin[a];
+  t.cur_cut = -1;
+  t.cut = -1;
+  t.R[0] = t.R[4] = t.R[8] = 1.0;
+  if (s->has_blade) {
+    const bm_blade_desc &b = s->blade;
+    t.has_blade = 1;
+    for (int a = 0; a < 3; ++a) {
+      t.edgeT[a] = b.edge_point[a];
+      t.nT[a] = b.normal[a];
+      t.eT[a] = b.edge_dir[a];
+      t.dT[a] = b.front_dir[a];
+      t.xB[a] = b.pose_x[a];
+    }
+    for (int k = 0; k < 9; ++k) t.R[k] = b.pose_R[k];
+    t.half_len = b.half_length;
+    t.L_d = b.half_length;
+    t.half_thick = 0.5 * b.thickness;
+    t.half_height = 0.5 * b.height;
+    t.mu_s = b.mu_s;
+    t.mu_d = b.mu_d;
+    t.mass = b.mass > 0 ? b.mass : 0.0;
+    if (t.mass > 0) {
+      const double *A = b.inertia;
+      double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                   A[2] * (A[3] * A[7] - A[4] * A[6]);
+      t.Ib_inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+      t.Ib_inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+      t.Ib_inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+      t.Ib_inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+      t.Ib_inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+      t.Ib_inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+      t.Ib_inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+      t.Ib_inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+      t.Ib_inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    }
+    t.kv = b.servo_gain > 0 ? b.servo_gain : 1.0 / (10.0 * d.dt);
+    t.rigid_interval = b.rigid_interval >= 1 ? b.rigid_interval : 1;
+    t.nseg = b.n_segments;
+    for (int i = 0; i < b.n_segments; ++i) {
+      t.seg[i].n_steps = b.segments[i].n_steps;
+      t.seg[i].cut_id = b.segments[i].cut_id;
+      for (int a = 0; a < 3; ++a) {
+        t.seg[i].v[a] = b.segments[i].v[a];
+        t.seg[i].w[a] = b.segments[i].omega[a];
+      }
+    }
+  }
+}
+
+// copy the fields of a DevScene that describe where it lives
+void set_ranges(const bm_scene_s *s, DevScene &t) {
+  t.p_begin = (int)s->p_begin;
+  t.node_begin = (int)s->node_begin;
+  t.cell_begin = (int)s->cell_begin;
+  t.slot_begin = (int)s->slot_begin;
+  t.hist_begin = (int)s->hist_begin;
+  t.ptile_begin = s->ptile_begin;
+  t.n_ptile = s->n_ptile;
+  t.ntile_begin = s->ntile_begin;
+  t.n_ntile = s->n_ntile;
+}
+
+// reserve ranges for s inside W; returns BM_OK or BM_E_CAPACITY
+int reserve(WorldH *W, bm_scene_s *s) {
+  if (W->free_slots.empty()) return fail(BM_E_CAPACITY, "no free scene slot");
+  if (s->desc.pair_contact && !W->pair) return fail(BM_E_CAPACITY, "batch has no pair-contact pools");
+  int64_t pb = W->rp.take(s->n);
+  int64_t cb = W->rcell.take(s->n_cell + 1);
+  int64_t nb = W->rnode.take(s->n_node);
+  int64_t sb = W->rslot.take(s->slot_cap);
+  int64_t hb = W->rhist.take(s->hist_cap);
+  if (pb < 0 || cb < 0 || nb < 0 || sb < 0 || hb < 0) {
+    if (pb >= 0) W->rp.give(pb, s->n);
+    if (cb >= 0) W->rcell.give(cb, s->n_cell + 1);
+    if (nb >= 0) W->rnode.give(nb, s->n_node);
+    if (sb >= 0) W->rslot.give(sb, s->slot_cap);
+    if (hb >= 0) W->rhist.give(hb, s->hist_cap);
+    return fail(BM_E_CAPACITY, "batch pools have no room for the scene");
+  }
+  s->slot = W->free_slots.back();
+  W->free_slots.pop_back();
+  s->p_begin = pb;
+  s->cell_begin = cb;
+  s->node_begin = nb;
+  s->slot_begin = sb;
+  s->hist_begin = hb;
+  return BM_OK;
+}
+
+void unreserve(WorldH *W, bm_scene_s *s) {
+  W->rp.give(s->p_begin, s->n);
+  W->rcell.give(s->cell_begin, s->n_cell + 1);
+  W->rnode.give(s->node_begin, s->n_node);
+  W->rslot.give(s->slot_cap ? s->slot_begin : 0, s->slot_cap);
+  W->rhist.give(s->hist_begin, s->hist_cap);
+  W->free_slots.push_back(s->slot);
+  s->slot = -1;
+}
+
+int upload_cell_start(WorldH *W, bm_scene_s *s) {
+  std::vector<int> cs(s->cell_start_rel.size());
+  for (size_t i = 0; i < cs.size(); ++i) cs[i] = s->cell_start_rel[i] + (int)s->p_begin;
+  CK(cudaMemcpyAsync(W->w.N.cell_start + s->cell_begin, cs.data(), sizeof(int) * cs.size(),
+                     cudaMemcpyHostToDevice, W->st));
+  CK(cudaStreamSynchronize(W->st));
+  return BM_OK;
+}
+
+// first placement of a freshly created scene
+int place_fresh(WorldH *W, bm_scene_s *s) {
+  int rc = reserve(W, s);
+  if (rc) return rc;
+  const int64_t n = s->n, pb = s->p_begin;
+  PPool &P = W->w.P;
+  cudaStream_t st = W->st;
+  std::vector<float> x3[3];
+  for (int a = 0; a < 3; ++a) {
+    x3[a].resize(n);
+    for (int64_t i = 0; i < n; ++i) x3[a][i] = s->X[3 * (size_t)s->h_perm[i] + a];
+  }
+  for (int a = 0; a < 3; ++a) {
+    CK(cudaMemcpyAsync(P.fx[a] + pb, s->h_fx[a].data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P.x[a] + pb, x3[a].data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(P.v[a] + pb, 0, sizeof(float) * n, st));
+    CK(cudaMemsetAsync(P.ut[a] + pb, 0, sizeof(float) * n, st));
+  }
+  std::vector<float> one((size_t)n, 1.0f);
+  for (int k = 0; k < 9; ++k) {
+    if (k % 4 == 0) CK(cudaMemcpyAsync(P.F[k] + pb, one.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(P.F[k] + pb, 0, sizeof(float) * n, st));
+  }
+  CK(cudaMemsetAsync(P.D + pb, 0, sizeof(float) * n, st));
+  CK(cudaMemsetAsync(P.s1 + pb, 0, sizeof(uint32_t) * n, st));
+  CK(cudaMemsetAsync(P.s2 + pb, 0, sizeof(uint32_t) * n, st));
+  CK(cudaMemcpyAsync(P.base + pb, s->h_base.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P.perm + pb, s->h_perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  if (W->pair) {
+    for (int b = 0; b < 2; ++b)
+      CK(cudaMemsetAsync(P.hist_partner[b] + pb * BM_HIST, 0xff, sizeof(int) * n * BM_HIST, st));
+  }
+  if (s->hist_cap) CK(cudaMemsetAsync(W->w.whist + s->hist_begin * 6, 0, sizeof(double) * 6 * s->hist_cap, st));
+  int r = upload_cell_start(W, s);
+  if (r) return r;
+  DevScene t = s->tmpl;
+  set_ranges(s, t);
+  CK(cudaMemcpyAsync(W->w.scenes + s->slot, &t, sizeof t, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  W->members.push_back(s);
+  s->world = W;
+  s->fresh = false;
+  s->h_fx[0].clear(); s->h_fx[1].clear(); s->h_fx[2].clear();
+  s->h_base.clear();
+  return BM_OK;
+}
+
+int finish_placement(WorldH *W, bm_scene_s *s) {
+  int r = rebuild_tiles(W);
+  if (r) return r;
+  LaunchSet ls = scene_set(W, s);
+  CK(bm_launch_rebuild(W->w, ls, W->st, 1));
+  CK(bm_launch_prepare(W->w, ls, W->st));
+  CK(cudaStreamSynchronize(W->st));
+  return BM_OK;
+}
+
+WorldH *new_world(const bm_alloc *alloc, cudaStream_t st) {
+  WorldH *W = new WorldH();
+  if (alloc && alloc->alloc && alloc->free) {
+    W->al.a = *alloc;
+    W->al.has = true;
+  }
+  W->al.st = st;
+  W->st = st;
+  return W;
+}
+
+// move s from its world into W (device-to-device copies of the persistent state)
+int move_scene(bm_scene_s *s, WorldH *W) {
+  WorldH *S = s->world;
+  CK(cudaStreamSynchronize(S->st));
+  DevScene cur;
+  CK(cudaMemcpy(&cur, S->w.scenes + s->slot, sizeof cur, cudaMemcpyDeviceToHost));
+  bm_scene_s old = *s;  // ranges in S
+  int rc = reserve(W, s);
+  if (rc) return rc;
+  const int64_t n = s->n;
+  const PPool &A = S->w.P;
+  PPool &B = W->w.P;
+  const int64_t ps = old.p_begin, pd = s->p_begin;
+  cudaStream_t st = W->st;
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  for (int a = 0; a < 3; ++a) {
+    CK(cp(B.fx[a] + pd, A.fx[a] + ps, sizeof(float) * n));
+    CK(cp(B.x[a] + pd, A.x[a] + ps, sizeof(float) * n));
+    CK(cp(B.v[a] + pd, A.v[a] + ps, sizeof(float) * n));
+    CK(cp(B.ut[a] + pd, A.ut[a] + ps, sizeof(float) * n));
+  }
+  for (int k = 0; k < 9; ++k) CK(cp(B.F[k] + pd, A.F[k] + ps, sizeof(float) * n));
+  CK(cp(B.D + pd, A.D + ps, sizeof(float) * n));
+  CK(cp(B.base + pd, A.base + ps, sizeof(uint32_t) * n));
+  CK(cp(B.s1 + pd, A.s1 + ps, sizeof(uint32_t) * n));
+  CK(cp(B.s2 + pd, A.s2 + ps, sizeof(uint32_t) * n));
+  CK(cp(B.perm + pd, A.perm + ps, sizeof(int) * n));
+  if (W->pair) {
+    for (int b = 0; b < 2; ++b) {
+      if (S->pair) {
+        CK(cp(B.hist_partner[b] + pd * BM_HIST, A.hist_partner[b] + ps * BM_HIST, sizeof(int) * n * BM_HIST));
+        CK(cp(B.hist_u[b] + pd * BM_HIST * 3, A.hist_u[b] + ps * BM_HIST * 3, sizeof(float) * n * BM_HIST * 3));
+      } else {
+        CK(cudaMemsetAsync(B.hist_partner[b] + pd * BM_HIST, 0xff, sizeof(int) * n * BM_HIST, st));
+      }
+    }
+  }
+  if (s->hist_cap) CK(cp(W->w.whist + s->hist_begin * 6, S->w.whist + old.hist_begin * 6, sizeof(double) * 6 * s->hist_cap));
+  CK(cudaStreamSynchronize(st));
+  int r = upload_cell_start(W, s);
+  if (r) return r;
+  // partner indices of the pair history are pool indices: rebase them
+  if (W->pair && S->pair && pd != ps) {
+    std::vector<int> h((size_t)n * BM_HIST);
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaMemcpy(h.data(), B.hist_partner[b] + pd * BM_HIST, sizeof(int) * h.size(), cudaMemcpyDeviceToHost));
+      for (auto &q : h)
+        if (q >= 0) q = q - (int)ps + (int)pd;
+      CK(cudaMemcpy(B.hist_partner[b] + pd * BM_HIST, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  set_ranges(s, cur);
+  cur.slot_cap = (int)s->slot_cap;
+  cur.list_count = 0;
+  CK(cudaMemcpy(W->w.scenes + s->slot, &cur, sizeof cur, cudaMemcpyHostToDevice));
+  // leave the old world
+  auto &mem = S->members;
+  mem.erase(std::remove(mem.begin(), mem.end(), s), mem.end());
+  {
+    bm_scene_s tmp = old;
+    unreserve(S, &tmp);
+  }
+  S->tiles_dirty = true;
+  bool drop_old = s->own_world;
+  W->members.push_back(s);
+  s->world = W;
+  s->own_world = false;
+  if (drop_old) delete S;
+  else if (!S->members.empty()) {
+    int r2 = rebuild_tiles(S);
+    if (r2) return r2;
+  }
+  return finish_placement(W, s);
+}
+
+int create_private_world(bm_scene_s *s, const bm_alloc *alloc, cudaStream_t st) {
+  WorldH *W = new_world(alloc, st);
+  W->cap_p = s->n;
+  W->cap_cell = s->n_cell + 1;
+  W->cap_node = s->n_node;
+  W->cap_slot = s->slot_cap;
+  W->cap_hist = s->hist_cap;
+  W->cap_scenes = 1;
+  W->cap_ptile = (int)tiles_for(s->n, 128) + 1;
+  W->cap_ntile = (int)tiles_for(s->n_node, 64) + 1;
+  W->pair = s->desc.pair_contact != 0;
+  int rc = world_alloc(W);
+  if (rc) {
+    delete W;
+    return rc;
+  }
+  rc = s->fresh ? place_fresh(W, s) : move_scene(s, W);
+  if (rc) return rc;
+  s->own_world = true;
+  return BM_OK;
+}
+
+int validate_desc(const bm_scene_desc *d) {
+  if (!d) return fail(BM_E_INVALID, "null scene descriptor");
+  if (!(d->dx > 0) || !(d->V0 > 0) || !(d->dt > 0) || !(d->rho > 0) || !(d->E > 0))
+    return fail(BM_E_INVALID, "dx, V0, dt, rho and E must be positive");
+  if (!(d->nu > -1.0 && d->nu < 0.5)) return fail(BM_E_INVALID, "nu must lie in (-1, 0.5)");
+  if (!(d->beta >= 0 && d->beta <= 1)) return fail(BM_E_INVALID, "beta must lie in [0, 1]");
+  if (!(d->zeta > 0 && d->zeta < 1)) return fail(BM_E_INVALID, "zeta must lie in (0, 1)");
+  return BM_OK;
+}
+
+// stencil table: base cell, fractional offset, sort by base cell (Eq. 1)
+int build_layout(bm_scene_s *s) {
+  const int64_t n = s->n;
+  const bm_scene_desc &d = s->desc;
+  std::vector<int> b3((size_t)n * 3);
+  std::vector<double> f3((size_t)n * 3);
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double xl = ((double)s->X[3 * i + a] - d.origin[a]) / d.dx;
+      double fb = std::floor(xl - 0.5);
+      if (!std::isfinite(fb) || std::fabs(fb) > 1e8) return fail(BM_E_INVALID, "particle outside the grid range");
+      int b = (int)fb;
+      b3[3 * i + a] = b;
+      f3[3 * i + a] = xl - (double)b;
+      lo[a] = std::min(lo[a], b);
+      hi[a] = std::max(hi[a], b);
+    }
+  for (int a = 0; a < 3; ++a) {
+    s->lo[a] = lo[a];
+    s->nb[a] = hi[a] - lo[a] + 1;
+    s->nn[a] = s->nb[a] + 2;
+    if (s->nb[a] > 1023) return fail(BM_E_INVALID, "more than 1023 reference cells along an axis");
+  }
+  s->n_cell = (int64_t)s->nb[0] * s->nb[1] * s->nb[2];
+  s->n_node = (int64_t)s->nn[0] * s->nn[1] * s->nn[2];
+  if (s->n_node > (int64_t)1 << 30 || n > (int64_t)1 << 30) return fail(BM_E_INVALID, "scene too large");
+  std::vector<int64_t> key((size_t)n);
+  std::vector<int> cnt((size_t)s->n_cell + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    int bx = b3[3 * i] - lo[0], by = b3[3 * i + 1] - lo[1], bz = b3[3 * i + 2] - lo[2];
+    key[i] = ((int64_t)bz * s->nb[1] + by) * s->nb[0] + bx;
+    cnt[key[i] + 1]++;
+  }
+  for (int64_t c = 0; c < s->n_cell; ++c) cnt[c + 1] += cnt[c];
+  s->cell_start_rel = cnt;
+  std::vector<int> fill((size_t)s->n_cell, 0);
+  s->h_perm.assign((size_t)n, 0);
+  for (int64_t i = 0; i < n; ++i) s->h_perm[cnt[key[i]] + fill[key[i]]++] = (int)i;  // stable
+  for (int a = 0; a < 3; ++a) s->h_fx[a].resize((size_t)n);
+  s->h_base.resize((size_t)n);
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t i = s->h_perm[j];
+    for (int a = 0; a < 3; ++a) s->h_fx[a][j] = (float)f3[3 * i + a];
+    uint32_t bx = (uint32_t)(b3[3 * i] - lo[0]), by = (uint32_t)(b3[3 * i + 1] - lo[1]),
+             bz = (uint32_t)(b3[3 * i + 2] - lo[2]);
+    s->h_base[j] = bx | (by << 10) | (bz << 20);
+  }
+  s->slot_cap = std::max<int64_t>(4 * s->n_node, 64);
+  s->hist_cap = d.wrench_history > 0 ? d.wrench_history : 0;
+  return BM_OK;
+}
+
+bool valid_scene(bm_scene_t s) { return s && s->world; }
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char *bm_last_error(void) { return g_err.c_str(); }
+const char *bm_version(void) { return "blademaster-gb300 0.1 (sm_103a)"; }
+
+int bm_scene_create(const bm_scene_desc *desc, const float *X_ref, int64_t n, const bm_alloc *alloc,
+                    void *stream, bm_scene_t *out) {
+  if (!out) return fail(BM_E_INVALID, "null output handle");
+  *out = nullptr;
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (n <= 0 || !X_ref) return fail(BM_E_INVALID, "need at least one particle");
+  bm_scene_s *s = new bm_scene_s();
+  s->desc = *desc;
+  s->home_stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    s->home_alloc = *alloc;
+    s->has_home_alloc = true;
+  }
+  s->n = n;
+  s->X.assign(X_ref, X_ref + 3 * n);
+  rc = build_layout(s);
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  fill_template(s);
+  rc = create_private_world(s, alloc, (cudaStream_t)stream);
+  if (rc) {
+    if (s->world) delete s->world;
+    delete s;
+    return rc;
+  }
+  rc = finish_placement(s->world, s);
+  if (rc) {
+    delete s->world;
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return BM_OK;
+}
+
+int bm_add_blade(bm_scene_t s, const bm_blade_desc *b, int *blade_id) {
+  if (!valid_scene(s) || !b) return fail(BM_E_INVALID, "bad scene or blade");
+  if (s->has_blade) return fail(BM_E_INVALID, "one blade per scene");
+  if (b->n_segments < 0 || b->n_segments > BM_MAX_SEGMENTS) return fail(BM_E_INVALID, "too many segments");
+  for (int i = 0; i < b->n_segments; ++i) {
+    if (b->segments[i].cut_id >= BM_MAX_CUTS || b->segments[i].cut_id < -1)
+      return fail(BM_E_TOO_MANY_CUTS, "cut id outside [-1, 32)");
+    if (b->segments[i].n_steps < 0) return fail(BM_E_INVALID, "negative segment length");
+  }
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  DevScene cur;
+  CK(cudaMemcpy(&cur, W->w.scenes + s->slot, sizeof cur, cudaMemcpyDeviceToHost));
+  s->blade = *b;
+  s->has_blade = true;
+  fill_template(s);
+  DevScene t = s->tmpl;
+  set_ranges(s, t);
+  t.step = cur.step;
+  t.err = cur.err;
+  t.n_slots = cur.n_slots;
+  t.need_rebuild = cur.need_rebuild;
+  CK(cudaMemcpy(W->w.scenes + s->slot, &t, sizeof t, cudaMemcpyHostToDevice));
+  LaunchSet ls = scene_set(W, s);
+  CK(bm_launch_prepare(W->w, ls, W->st));
+  CK(cudaStreamSynchronize(W->st));
+  if (blade_id) *blade_id = 0;
+  return BM_OK;
+}
+
+int bm_set_tool_state(bm_scene_t s, int blade_id, const double pose[12], const double twist[6]) {
+  if (!valid_scene(s) || !s->has_blade || blade_id != 0 || !pose || !twist)
+    return fail(BM_E_INVALID, "bad scene, blade or arguments");
+  WorldH *W = s->world;
+  double buf[18];
+  std::memcpy(buf, pose, sizeof(double) * 12);
+  std::memcpy(buf + 12, twist, sizeof(double) * 6);
+  CK(cudaMemcpyAsync((char *)(W->w.scenes + s->slot) + offsetof(DevScene, xB), buf, sizeof buf,
+                     cudaMemcpyHostToDevice, W->st));
+  CK(bm_launch_prepare(W->w, scene_set(W, s), W->st));
+  CK(cudaStreamSynchronize(W->st));
+  return BM_OK;
+}
+
+int bm_get_tool_state(bm_scene_t s, int blade_id, double pose[12], double twist[6]) {
+  if (!valid_scene(s) || !s->has_blade || blade_id != 0) return fail(BM_E_INVALID, "bad scene or blade");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  double buf[18];
+  CK(cudaMemcpy(buf, (char *)(W->w.scenes + s->slot) + offsetof(DevScene, xB), sizeof buf,
+                cudaMemcpyDeviceToHost));
+  if (pose) std::memcpy(pose, buf, sizeof(double) * 12);
+  if (twist) std::memcpy(twist, buf + 12, sizeof(double) * 6);
+  return BM_OK;
+}
+
+int bm_step(bm_scene_t s, int n_substeps) {
+  if (!valid_scene(s) || n_substeps < 0) return fail(BM_E_INVALID, "bad scene or step count");
+  WorldH *W = s->world;
+  if (W->tiles_dirty) {
+    int r = rebuild_tiles(W);
+    if (r) return r;
+  }
+  LaunchSet ls = scene_set(W, s);
+  for (int k = 0; k < n_substeps; ++k) CK(bm_launch_substep(W->w, ls, W->st));
+  return BM_OK;
+}
+
+int bm_read_state(bm_scene_t s, uint32_t field_mask, void *const *dst, int dst_on_device) {
+  if (!valid_scene(s) || !dst) return fail(BM_E_INVALID, "bad scene or destination");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  const int64_t n = s->n;
+  int j = 0;
+  for (int f = 0; f < BM_NUM_FIELDS; ++f) {
+    if (!(field_mask & (1u << f))) continue;
+    void *d = dst[j++];
+    if (!d) return fail(BM_E_INVALID, "null destination pointer");
+    size_t w = (f == 3) ? 9 : (f == 1 || f == 2 || f == 5 || f == 0) ? 3 : 1;
+    size_t es = (f == 6) ? 8 : 4;
+    size_t bytes = (size_t)n * w * es;
+    if (f == 0) {
+      CK(cudaMemcpy(d, s->X.data(), bytes, dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+      continue;
+    }
+    void *tgt = d;
+    void *tmp = nullptr;
+    if (!dst_on_device) {
+      CK(cudaMalloc(&tmp, bytes));
+      tgt = tmp;
+    }
+    cudaError_t e = (f == 6) ? bm_launch_code(W->w, (int)s->p_begin, (int)n, (int64_t *)tgt, W->st)
+                             : bm_launch_io(W->w, s->slot, (int)s->p_begin, (int)n, f, tgt, 0, W->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(W->st);
+    if (e == cudaSuccess && tmp) e = cudaMemcpy(d, tmp, bytes, cudaMemcpyDeviceToHost);
+    if (tmp) cudaFree(tmp);
+    CK(e);
+  }
+  return BM_OK;
+}
+
+int bm_write_state(bm_scene_t s, uint32_t field_mask, const void *const *src, int src_on_device) {
+  if (!valid_scene(s) || !src) return fail(BM_E_INVALID, "bad scene or source");
+  if (field_mask & (BM_FIELD_X | BM_FIELD_CODE)) return fail(BM_E_INVALID, "X and CODE are read-only");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  const int64_t n = s->n;
+  int j = 0;
+  bool masks = false;
+  for (int f = 0; f < BM_NUM_FIELDS; ++f) {
+    if (!(field_mask & (1u << f))) continue;
+    const void *d = src[j++];
+    if (!d) return fail(BM_E_INVALID, "null source pointer");
+    size_t w = (f == 3) ? 9 : (f == 1 || f == 2 || f == 5) ? 3 : 1;
+    size_t bytes = (size_t)n * w * 4;
+    void *buf = (void *)d;
+    void *tmp = nullptr;
+    if (!src_on_device) {
+      CK(cudaMalloc(&tmp, bytes));
+      CK(cudaMemcpy(tmp, d, bytes, cudaMemcpyHostToDevice));
+      buf = tmp;
+    }
+    cudaError_t e = bm_launch_io(W->w, s->slot, (int)s->p_begin, (int)n, f, buf, 1, W->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(W->st);
+    if (tmp) cudaFree(tmp);
+    CK(e);
+    if (f == 7 || f == 8) masks = true;
+  }
+  if (masks) {
+    CK(bm_launch_rebuild(W->w, scene_set(W, s), W->st, 1));
+    CK(cudaStreamSynchronize(W->st));
+  }
+  return BM_OK;
+}
+
+int bm_scene_info_get(bm_scene_t s, bm_scene_info *out) {
+  if (!valid_scene(s) || !out) return fail(BM_E_INVALID, "bad scene");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  DevScene cur;
+  CK(cudaMemcpy(&cur, W->w.scenes + s->slot, sizeof cur, cudaMemcpyDeviceToHost));
+  out->n_particles = s->n;
+  out->n_nodes = s->n_node;
+  out->n_slots = cur.n_slots;
+  out->slot_capacity = s->slot_cap;
+  out->step = cur.step;
+  out->error_bits = cur.err;
+  for (int a = 0; a < 3; ++a) {
+    out->grid_lo[a] = s->lo[a];
+    out->grid_dim[a] = s->nn[a];
+  }
+  return BM_OK;
+}
+
+int bm_tool_wrench(bm_scene_t s, int blade_id, double out[6]) {
+  if (!valid_scene(s) || !s->has_blade || blade_id != 0 || !out) return fail(BM_E_INVALID, "bad scene or blade");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  CK(cudaMemcpy(out, (char *)(W->w.scenes + s->slot) + offsetof(DevScene, lastW), sizeof(double) * 6,
+                cudaMemcpyDeviceToHost));
+  return BM_OK;
+}
+
+int bm_wrench_history(bm_scene_t s, int blade_id, int64_t first, int64_t count, double *out) {
+  if (!valid_scene(s) || !s->has_blade || blade_id != 0 || !out || first < 0 || count < 0 ||
+      first + count > s->hist_cap)
+    return fail(BM_E_INVALID, "bad scene, blade or history range");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  if (count)
+    CK(cudaMemcpy(out, W->w.whist + (s->hist_begin + first) * 6, sizeof(double) * 6 * count,
+                  cudaMemcpyDeviceToHost));
+  return BM_OK;
+}
+
+int bm_scene_destroy(bm_scene_t s) {
+  if (!s) return fail(BM_E_INVALID, "null scene");
+  WorldH *W = s->world;
+  if (W) {
+    cudaStreamSynchronize(W->st);
+    if (s->own_world) {
+      delete W;
+    } else {
+      auto &mem = W->members;
+      mem.erase(std::remove(mem.begin(), mem.end(), s), mem.end());
+      unreserve(W, s);
+      W->tiles_dirty = true;
+    }
+  }
+  delete s;
+  return BM_OK;
+}
+
+int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n, int64_t *particles,
+                       int64_t *nodes, int64_t *bytes) {
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (n <= 0 || !X_ref) return fail(BM_E_INVALID, "need at least one particle");
+  bm_scene_s s;
+  s.desc = *desc;
+  s.n = n;
+  s.X.assign(X_ref, X_ref + 3 * n);
+  rc = build_layout(&s);
+  if (rc) return rc;
+  if (particles) *particles = n;
+  if (nodes) *nodes = s.n_node;
+  const int64_t per_p = 4 * (3 * 5 + 18 + 1) + 4 * 3 + 4 * 2 + (desc->pair_contact ? (3 * 4 + 2 * BM_HIST * 16) : 0);
+  const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (4 * 16 + 8);
+  if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.hist_cap * 48;
+  return BM_OK;
+}
+
+// ---- batches ---------------------------------------------------------------
+
+int bm_batch_create(const bm_batch_desc *desc, const bm_alloc *alloc, void *stream, bm_batch_t *out) {
+  if (!desc || !out) return fail(BM_E_INVALID, "null descriptor or output");
+  *out = nullptr;
+  if (desc->max_particles <= 0 || desc->max_nodes <= 0 || desc->max_scenes <= 0)
+    return fail(BM_E_INVALID, "batch capacities must be positive");
+  cudaStream_t st = (cudaStream_t)stream;
+  bool own = false;
+  if (!st) {
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    own = true;
+  }
+  WorldH *W = new_world(alloc, st);
+  W->own_stream = own;
+  W->cap_p = desc->max_particles;
+  W->cap_node = desc->max_nodes;
+  W->cap_slot = desc->max_slots > 0 ? desc->max_slots : 4 * desc->max_nodes;
+  W->cap_cell = desc->max_nodes + desc->max_scenes;
+  W->cap_scenes = desc->max_scenes;
+  W->cap_hist = 0;
+  W->cap_ptile = (int)tiles_for(desc->max_particles, 128) + desc->max_scenes;
+  W->cap_ntile = (int)tiles_for(desc->max_nodes, 64) + desc->max_scenes;
+  W->pair = desc->pair_contact != 0;
+  W->ptile_size = desc->particle_tile > 0 ? desc->particle_tile : 256;
+  W->ntile_size = desc->node_tile > 0 ? desc->node_tile : 128;
+  W->graph_chunk = desc->graph_chunk > 0 ? desc->graph_chunk : 16;
+  if (W->ptile_size < 128 || W->ptile_size > 512 || W->ptile_size % 32 || W->ntile_size < 64 ||
+      W->ntile_size > 512 || W->ntile_size % 32) {
+    delete W;
+    return fail(BM_E_INVALID, "tile sizes must be multiples of 32 in [128,512] / [64,512]");
+  }
+  int rc = world_alloc(W);
+  if (rc) {
+    delete W;
+    return rc;
+  }
+  bm_batch_s *b = new bm_batch_s();
+  b->world = W;
+  *out = b;
+  return BM_OK;
+}
+
+int bm_batch_add(bm_batch_t b, bm_scene_t s) {
+  if (!b || !valid_scene(s)) return fail(BM_E_INVALID, "bad batch or scene");
+  if (s->world == b->world) return BM_OK;
+  if (s->hist_cap) return fail(BM_E_INVALID, "scenes with a wrench history cannot join a batch");
+  return move_scene(s, b->world);
+}
+
+int bm_batch_remove(bm_batch_t b, bm_scene_t s) {
+  if (!b || !valid_scene(s) || s->world != b->world) return fail(BM_E_INVALID, "scene is not in this batch");
+  int rc = create_private_world(s, s->has_home_alloc ? &s->home_alloc : nullptr, s->home_stream);
+  if (rc) return rc;
+  return BM_OK;
+}
+
+int bm_batch_set_tiles(bm_batch_t b, int particle_tile, int node_tile) {
+  if (!b) return fail(BM_E_INVALID, "bad batch");
+  if (particle_tile < 128 || particle_tile > 512 || particle_tile % 32 || node_tile < 64 ||
+      node_tile > 512 || node_tile % 32)
+    return fail(BM_E_INVALID, "tile sizes must be multiples of 32 in [128,512] / [64,512]");
+  WorldH *W = b->world;
+  CK(cudaStreamSynchronize(W->st));
+  W->ptile_size = particle_tile;
+  W->ntile_size = node_tile;
+  W->tiles_dirty = true;
+  return rebuild_tiles(W);
+}
+
+int bm_batch_step(bm_batch_t b, int n_substeps) {
+  if (!b || n_substeps < 0) return fail(BM_E_INVALID, "bad batch or step count");
+  WorldH *W = b->world;
+  if (W->members.empty() || n_substeps == 0) return BM_OK;
+  if (W->tiles_dirty) {
+    int r = rebuild_tiles(W);
+    if (r) return r;
+  }
+  LaunchSet ls = world_set(W);
+  auto graph_for = [&](int k, cudaGraphExec_t *out) -> int {
+    auto it = W->graphs.find(k);
+    if (it != W->graphs.end()) {
+      *out = it->second;
+      return BM_OK;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(W->st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < k; ++i) {
+      cudaError_t e = bm_launch_substep(W->w, ls, W->st);
+      if (e != cudaSuccess) {
+        cudaStreamEndCapture(W->st, &g);
+        return fail(BM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+      }
+    }
+    CK(cudaStreamEndCapture(W->st, &g));
+    cudaGraphExec_t ex;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    W->graphs[k] = ex;
+    *out = ex;
+    return BM_OK;
+  };
+  const int chunk = W->graph_chunk;
+  int full = n_substeps / chunk, rem = n_substeps % chunk;
+  cudaGraphExec_t ex;
+  if (full) {
+    int r = graph_for(chunk, &ex);
+    if (r) return r;
+    for (int i = 0; i < full; ++i) CK(cudaGraphLaunch(ex, W->st));
+  }
+  if (rem) {
+    int r = graph_for(rem, &ex);
+    if (r) return r;
+    CK(cudaGraphLaunch(ex, W->st));
+  }
+  return BM_OK;
+}
+
+int bm_batch_members(bm_batch_t b, bm_scene_t *out, int cap) {
+  if (!b) return fail(BM_E_INVALID, "bad batch");
+  int n = (int)b->world->members.size();
+  for (int i = 0; i < n && i < cap && out; ++i) out[i] = b->world->members[i];
+  return n;
+}
+
+int bm_batch_set_tool_states(bm_batch_t b, const double *states, int n, int on_device) {
+  if (!b || !states) return fail(BM_E_INVALID, "bad batch or states");
+  WorldH *W = b->world;
+  if (n != (int)W->members.size()) return fail(BM_E_INVALID, "state count must equal the member count");
+  if (W->tiles_dirty) {
+    int r = rebuild_tiles(W);
+    if (r) return r;
+  }
+  const double *src = states;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(W->d_stage, states, sizeof(double) * 18 * (size_t)n, cudaMemcpyHostToDevice, W->st));
+    src = W->d_stage;
+  }
+  CK(bm_launch_set_tools(W->w, W->d_scene_ids, n, src, W->st));
+  return BM_OK;
+}
+
+int bm_batch_tool_wrenches(bm_batch_t b, double *out, int n, int on_device) {
+  if (!b || !out) return fail(BM_E_INVALID, "bad batch or output");
+  WorldH *W = b->world;
+  if (n != (int)W->members.size()) return fail(BM_E_INVALID, "output count must equal the member count");
+  if (W->tiles_dirty) {
+    int r = rebuild_tiles(W);
+    if (r) return r;
+  }
+  double *dst = on_device ? out : W->d_stage;
+  CK(bm_launch_get_wrenches(W->w, W->d_scene_ids, n, dst, W->st));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(out, W->d_stage, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost, W->st));
+    CK(cudaStreamSynchronize(W->st));
+  }
+  return BM_OK;
+}
+
+int bm_batch_errors(bm_batch_t b, uint32_t *bits) {
+  if (!b || !bits) return fail(BM_E_INVALID, "bad batch");
+  WorldH *W = b->world;
+  CK(cudaStreamSynchronize(W->st));
+  uint32_t acc = 0;
+  for (bm_scene_s *s : W->members) {
+    uint32_t e;
+    CK(cudaMemcpy(&e, (char *)(W->w.scenes + s->slot) + offsetof(DevScene, err), sizeof e,
+                  cudaMemcpyDeviceToHost));
+    acc |= e;
+  }
+  *bits = acc;
+  return BM_OK;
+}
+
+int bm_batch_destroy(bm_batch_t b) {
+  if (!b) return fail(BM_E_INVALID, "bad batch");
+  WorldH *W = b->world;
+  // member scenes lose their storage: detach them
+  for (bm_scene_s *s : W->members) s->world = nullptr;
+  delete W;
+  delete b;
+  return BM_OK;
+}
+
+}  // extern "C"

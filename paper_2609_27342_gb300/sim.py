@@ -1,0 +1,282 @@
+"""Thin Python binding over the C ABI: scenes and batches.
+
+Only argument marshalling lives here; every step of the substep runs in the
+library's CUDA kernels.  PyTorch supplies device memory (optionally, through
+its caching allocator) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Dict, Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from . import _abi as A
+
+
+def _d3(v):
+    return A.D3(*[float(t) for t in v])
+
+
+def scene_desc(sc, wrench_history: int = 0) -> A.SceneDesc:
+    """C descriptor from a ``bm_inputs.Scene``-like object."""
+    d = A.SceneDesc()
+    d.E, d.nu, d.rho, d.dx = sc.E, sc.nu, sc.rho, sc.dx
+    d.origin = _d3(sc.origin)
+    d.V0, d.dt, d.beta = sc.V0, sc.dt, sc.beta
+    d.gravity = _d3(sc.gravity)
+    d.floor_enabled, d.floor_z = int(sc.floor), sc.floor_z
+    d.s_R, d.s_n, d.gamma_k, d.gamma_c = sc.s_R, sc.s_n, sc.gamma_k, sc.gamma_c
+    d.pair_contact, d.pair_mu_s, d.pair_mu_d = int(sc.pair_contact), sc.pair_mu_s, sc.pair_mu_d
+    d.G_c, d.zeta, d.u_min = sc.G_c, sc.zeta, sc.u_min
+    d.b_back, d.b_lead, d.band_half_width = sc.b_back, sc.b_lead, sc.band_half_width
+    d.tool_contact = int(sc.tool_contact)
+    d.wrench_history = int(wrench_history)
+    return d
+
+
+def blade_desc(b) -> A.BladeDesc:
+    B = A.BladeDesc()
+    B.edge_point, B.normal = _d3(b.edge_point), _d3(b.normal)
+    B.edge_dir, B.front_dir = _d3(b.edge_dir), _d3(b.front_dir)
+    B.half_length, B.thickness, B.height = b.half_length, b.thickness, b.height
+    B.mu_s, B.mu_d, B.mass = b.mu_s, b.mu_d, b.mass
+    B.inertia = A.D9(*b.inertia)
+    B.pose_x = _d3(b.pose_x)
+    B.pose_R = A.D9(*b.pose_R)
+    B.servo_gain = b.servo_gain
+    B.rigid_interval = b.rigid_interval
+    if len(b.segments) > A.MAX_SEGMENTS:
+        raise ValueError("too many trajectory segments")
+    B.n_segments = len(b.segments)
+    for i, s in enumerate(b.segments):
+        B.segments[i].n_steps = int(s.n_steps)
+        B.segments[i].cut_id = int(s.cut_id)
+        B.segments[i].v = _d3(s.v)
+        B.segments[i].omega = _d3(s.omega)
+    return B
+
+
+class TorchAllocator:
+    """bm_alloc callbacks backed by PyTorch's caching allocator."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self._torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                              stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._a = A.ALLOC_FN(_alloc)
+        self._f = A.FREE_FN(_free)
+        self.struct = A.Alloc(self._a, self._f, None)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    h = getattr(stream, "cuda_stream", stream)
+    return int(h) if h else None
+
+
+class Scene:
+    """One simulation scene on the GPU (C handle ``bm_scene_t``)."""
+
+    def __init__(self, sc, stream=None, allocator: Optional[TorchAllocator] = None,
+                 wrench_history: int = 0):
+        self._L = A.load()
+        X = np.ascontiguousarray(np.asarray(sc.X, dtype=np.float32))
+        self.n = int(X.shape[0])
+        self.spec = sc
+        self._alloc = allocator
+        self._desc = scene_desc(sc, wrench_history)
+        h = C.c_void_p()
+        A.check(self._L.bm_scene_create(
+            C.byref(self._desc), X.ctypes.data_as(C.POINTER(C.c_float)), self.n,
+            C.byref(allocator.struct) if allocator is not None else None,
+            _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.batch = None
+        if sc.blade is not None:
+            self._blade = blade_desc(sc.blade)
+            bid = C.c_int()
+            A.check(self._L.bm_add_blade(self._h, C.byref(self._blade), C.byref(bid)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.bm_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        A.check(self._L.bm_step(self._h, int(n)))
+
+    def read(self, *names: str) -> Dict[str, np.ndarray]:
+        names = names or ("x", "v")
+        order = sorted(names, key=lambda k: A.FIELDS[k][0])
+        mask, outs, ptrs = 0, {}, []
+        for k in order:
+            bit, w, dt = A.FIELDS[k]
+            mask |= bit
+            a = np.zeros((self.n, w) if w > 1 else (self.n,), dtype=dt)
+            outs[k] = a
+            ptrs.append(a.ctypes.data)
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        A.check(self._L.bm_read_state(self._h, mask, arr, 0))
+        return outs
+
+    def read_device(self, fields: Dict[str, "object"]) -> None:
+        """Read into device tensors (dict name -> contiguous torch tensor)."""
+        order = sorted(fields, key=lambda k: A.FIELDS[k][0])
+        mask = 0
+        ptrs = []
+        for k in order:
+            mask |= A.FIELDS[k][0]
+            ptrs.append(fields[k].data_ptr())
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        A.check(self._L.bm_read_state(self._h, mask, arr, 1))
+
+    def write(self, **fields) -> None:
+        order = sorted(fields, key=lambda k: A.FIELDS[k][0])
+        mask, keep, ptrs = 0, [], []
+        for k in order:
+            bit, w, dt = A.FIELDS[k]
+            a = np.ascontiguousarray(np.asarray(fields[k], dtype=dt).reshape(self.n, w) if w > 1
+                                     else np.asarray(fields[k], dtype=dt).reshape(self.n))
+            mask |= bit
+            keep.append(a)
+            ptrs.append(a.ctypes.data)
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        A.check(self._L.bm_write_state(self._h, mask, arr, 0))
+
+    def info(self) -> A.SceneInfo:
+        out = A.SceneInfo()
+        A.check(self._L.bm_scene_info_get(self._h, C.byref(out)))
+        return out
+
+    def tool_wrench(self) -> np.ndarray:
+        out = np.zeros(6)
+        A.check(self._L.bm_tool_wrench(self._h, 0, out.ctypes.data_as(A.PD)))
+        return out
+
+    def wrench_history(self, first: int, count: int) -> np.ndarray:
+        out = np.zeros((count, 6))
+        A.check(self._L.bm_wrench_history(self._h, 0, first, count, out.ctypes.data_as(A.PD)))
+        return out
+
+    def set_tool_state(self, xB, R, vB, wB) -> None:
+        pose = np.ascontiguousarray(np.concatenate([np.ravel(xB), np.ravel(R)]).astype(np.float64))
+        tw = np.ascontiguousarray(np.concatenate([np.ravel(vB), np.ravel(wB)]).astype(np.float64))
+        A.check(self._L.bm_set_tool_state(self._h, 0, pose.ctypes.data_as(A.PD),
+                                          tw.ctypes.data_as(A.PD)))
+
+    def tool_state(self) -> np.ndarray:
+        pose = np.zeros(12)
+        tw = np.zeros(6)
+        A.check(self._L.bm_get_tool_state(self._h, 0, pose.ctypes.data_as(A.PD),
+                                          tw.ctypes.data_as(A.PD)))
+        return np.concatenate([pose, tw])
+
+
+def footprint(sc) -> tuple:
+    L = A.load()
+    X = np.ascontiguousarray(np.asarray(sc.X, dtype=np.float32))
+    d = scene_desc(sc)
+    p, nd, b = C.c_int64(), C.c_int64(), C.c_int64()
+    A.check(L.bm_scene_footprint(C.byref(d), X.ctypes.data_as(C.POINTER(C.c_float)), X.shape[0],
+                                 C.byref(p), C.byref(nd), C.byref(b)))
+    return p.value, nd.value, b.value
+
+
+class Batch:
+    """Packed pools holding many scenes, stepped by CUDA-graph launches."""
+
+    def __init__(self, max_particles: int, max_nodes: int, max_scenes: int,
+                 max_slots: int = 0, graph_chunk: int = 16, particle_tile: int = 256,
+                 node_tile: int = 128, pair_contact: bool = False, stream=None,
+                 allocator: Optional[TorchAllocator] = None):
+        self._L = A.load()
+        d = A.BatchDesc(int(max_particles), int(max_nodes), int(max_slots), int(max_scenes),
+                        int(graph_chunk), int(particle_tile), int(node_tile), int(pair_contact))
+        h = C.c_void_p()
+        self._alloc = allocator
+        A.check(self._L.bm_batch_create(C.byref(d),
+                                        C.byref(allocator.struct) if allocator else None,
+                                        _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.scenes: List[Scene] = []
+
+    def add(self, s: Scene) -> None:
+        A.check(self._L.bm_batch_add(self._h, s.handle))
+        s.batch = self
+        self.scenes.append(s)
+
+    def remove(self, s: Scene) -> None:
+        A.check(self._L.bm_batch_remove(self._h, s.handle))
+        s.batch = None
+        self.scenes.remove(s)
+
+    def step(self, n: int = 1) -> None:
+        A.check(self._L.bm_batch_step(self._h, int(n)))
+
+    def set_tiles(self, particle_tile: int, node_tile: int) -> None:
+        A.check(self._L.bm_batch_set_tiles(self._h, int(particle_tile), int(node_tile)))
+
+    def members(self) -> list:
+        n = self._L.bm_batch_members(self._h, None, 0)
+        arr = (C.c_void_p * max(n, 1))()
+        self._L.bm_batch_members(self._h, arr, n)
+        return [arr[i] for i in range(n)]
+
+    def set_tool_states(self, states: np.ndarray) -> None:
+        st = np.ascontiguousarray(states, dtype=np.float64)
+        A.check(self._L.bm_batch_set_tool_states(self._h, st.ctypes.data_as(A.PD), st.shape[0], 0))
+
+    def set_tool_states_ptr(self, ptr: int, n: int, on_device: bool) -> None:
+        A.check(self._L.bm_batch_set_tool_states(self._h, C.cast(ptr, A.PD), n, int(on_device)))
+
+    def tool_wrenches(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        n = len(self.scenes)
+        out = np.zeros((n, 6)) if out is None else out
+        A.check(self._L.bm_batch_tool_wrenches(self._h, out.ctypes.data_as(A.PD), n, 0))
+        return out
+
+    def tool_wrenches_ptr(self, ptr: int, n: int, on_device: bool) -> None:
+        A.check(self._L.bm_batch_tool_wrenches(self._h, C.cast(ptr, A.PD), n, int(on_device)))
+
+    def errors(self) -> int:
+        b = C.c_uint32()
+        A.check(self._L.bm_batch_errors(self._h, C.byref(b)))
+        return b.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            for s in self.scenes:
+                s.close()
+            self.scenes = []
+            self._L.bm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,314 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (float32 path vs float64 oracle, same seeded inputs):
+  * side labels fed identical positions, velocities and tool state: bit-exact;
+  * after 100 substeps: positions within 1e-5 of the domain size, the reaction
+    wrench within 1e-4 relative, label disagreement at most 1e-4 of the
+    particles, each within 1e-5 dx of a band threshold;
+  * batched vs plain, and any tile size: bit-identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bm_inputs as bi
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2609_27342_gb300 as p
+    from paper_2609_27342_gb300 import build
+    build.build()
+    p.load()
+    return p
+
+
+def domain(sc):
+    return float(np.max(sc.X.max(0) - sc.X.min(0)))
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def digits0(g):
+    m = g.read("mask1", "mask2")
+    return np.where(m["mask1"] & 1, 1, np.where(m["mask2"] & 1, 2, 0))
+
+
+# --------------------------------------------------------------------------
+# side labels are bit-exact when fed the oracle's inputs (Eq. 3, 4, 6)
+# --------------------------------------------------------------------------
+
+def test_labels_bit_exact_on_shared_inputs(pkg):
+    dx = 5e-3
+    X = bi.lattice_cuboid((0.04, 0.02, 0.02), dx)
+    n = X.shape[0]
+    xe = f32([0.02, 0.01, 0.012])
+    blade = bi.Blade(pose_x=tuple(xe), segments=[bi.Segment(100, v=(0, 0, -0.5), cut_id=0)])
+    sc = bi.Scene(X=X, dx=dx, V0=dx ** 3 / 8, blade=blade, gravity=(0, 0, 0), floor=False)
+    rng = np.random.default_rng(11)
+    h, L, bb = 6 * dx, 0.05, dx
+    # positions chosen on and around every threshold of the band predicate
+    x = np.empty((n, 3))
+    x[:, 1] = xe[1] + rng.uniform(-0.06, 0.06, n)
+    x[:, 0] = xe[0] + rng.choice([0.0, h, -h, 1e-9, -1e-9, 0.003, -0.003], n) + \
+        rng.choice([0.0, 0.0, 1e-9, -1e-9], n)
+    x[:, 2] = xe[2] + rng.choice([0.0, 1e-9, -1e-9, bb, -bb, bb + 2.5e-5, dx * 0.5, -dx * 0.3], n)
+    x[: n // 8, 1] = xe[1] + rng.choice([L, -L, L + 1e-9, -L - 1e-9], n // 8)
+    x = f32(x)
+    v = f32(rng.normal(0, 0.05, (n, 3)))
+    o = O.OracleScene(sc)
+    o.set("x", x)
+    o.set("v", v)
+    g = pkg.Scene(sc)
+    g.write(x=x, v=v)
+    R = np.eye(3)
+    o.set_tool(xe, R, (0, 0, -0.5), (0, 0, 0))
+    g.set_tool_state(xe, R, (0, 0, -0.5), (0, 0, 0))
+    o.step(1)
+    g.step(1)
+    od = o.get("digits")[:, 0].astype(int)
+    gd = digits0(g)
+    assert np.array_equal(od, gd), np.nonzero(od != gd)
+    assert (od == 1).sum() > 50 and (od == 2).sum() > 50
+    # the exact path was exercised: particles sit on s = 0 and f = 0 exactly
+    s = x[:, 0] - xe[0]
+    f = -(x[:, 2] - xe[2])
+    assert np.sum(s == 0) > 10 and np.sum(f == 0) > 10
+
+
+# --------------------------------------------------------------------------
+# one substep, every field
+# --------------------------------------------------------------------------
+
+def _touching_block(speed=0.5, n_down=200, size=(0.04, 0.02, 0.02), **kw):
+    return bi.single_cut_cuboid(size=size, edge_z0=size[2] + 0.00005, speed=speed,
+                                n_down=n_down, **kw)
+
+
+def test_one_substep_all_fields(pkg):
+    sc = _touching_block()
+    o = O.OracleScene(sc)
+    g = pkg.Scene(sc, wrench_history=8)
+    for _ in range(3):
+        o.step(1)
+        g.step(1)
+    r = g.read("x", "v", "F", "D", "ut")
+    L = domain(sc)
+    assert np.max(np.abs(r["x"] - o.get("x"))) < 1e-7 * L
+    vs = max(1e-3, np.max(np.abs(o.get("v"))))
+    assert np.max(np.abs(r["v"] - o.get("v"))) < 2e-5 * vs
+    assert np.max(np.abs(r["F"] - o.get("F"))) < 1e-5
+    assert np.max(np.abs(r["D"] - o.get("D"))) < 1e-4
+    wo = o.wrench_history(0, 3)
+    wg = g.wrench_history(0, 3)
+    scale = np.max(np.abs(wo[:, :3]))
+    assert scale > 0
+    assert np.max(np.abs(wg[:, :3] - wo[:, :3])) < 1e-4 * scale
+    info = g.info()
+    assert info.step == 3 and info.error_bits == 0
+    lo, dim = o.grid_dims()
+    assert tuple(info.grid_lo) == lo and tuple(info.grid_dim) == dim
+
+
+# --------------------------------------------------------------------------
+# 100 substeps on the single-cut cuboid (16,000 particles)
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def run100(pkg):
+    sc = bi.single_cut_cuboid(edge_z0=0.0505, speed=1.0, n_down=500)
+    o = O.OracleScene(sc)
+    o.step(100)
+    g = pkg.Scene(sc, wrench_history=100)
+    g.step(100)
+    return sc, o, g
+
+
+def test_positions_after_100_substeps(run100):
+    sc, o, g = run100
+    r = g.read("x")
+    err = np.max(np.abs(r["x"] - o.get("x")))
+    assert err <= 1e-5 * domain(sc), err
+
+
+def test_wrench_after_100_substeps(run100):
+    sc, o, g = run100
+    wo = o.wrench_history(0, 100)
+    wg = g.wrench_history(0, 100)
+    Fo, Fg = wo[-1, :3], wg[-1, :3]
+    assert np.linalg.norm(Fo) > 0
+    assert np.linalg.norm(Fg - Fo) <= 1e-4 * np.linalg.norm(Fo)
+    To, Tg = wo[-1, 3:], wg[-1, 3:]
+    assert np.linalg.norm(Tg - To) <= 1e-4 * max(np.linalg.norm(To), 1e-3 * np.linalg.norm(Fo))
+    # whole trajectory, relative to its peak
+    assert np.max(np.abs(wg[:, :3] - wo[:, :3])) <= 1e-4 * np.max(np.abs(wo[:, :3]))
+
+
+def test_label_disagreement_after_100_substeps(run100):
+    sc, o, g = run100
+    od = o.get("digits")[:, 0].astype(int)
+    gd = digits0(g)
+    assert (od > 0).sum() > 500, "the cut must have labelled particles"
+    bad = np.nonzero(od != gd)[0]
+    assert len(bad) <= 1e-4 * sc.n
+    # any disagreement must sit on a band threshold (1e-5 dx) of the oracle state
+    if len(bad):
+        fr = o.frame()
+        x = o.get("x")[bad]
+        r = x - fr["xe"]
+        s, f = r @ fr["n"], r @ fr["d"]
+        h = 6 * sc.dx
+        near = np.minimum.reduce([np.abs(s), np.abs(np.abs(s) - h), np.abs(f), np.abs(f + sc.dx)])
+        assert np.all(near <= 1e-5 * sc.dx)
+
+
+def test_compact_slots_match_active_codes(run100):
+    """Sec. III-G: one slot per (node, code) that some particle of the node's
+    fixed reference neighbourhood carries -- counted here from positions and
+    codes alone."""
+    sc, o, g = run100
+    codes = g.read("code")["code"]
+    base = np.floor((sc.X - np.asarray(sc.origin)) / sc.dx - 0.5).astype(np.int64)
+    lo = base.min(0)
+    dim = base.max(0) - lo + 3
+    off = np.array([(i, j, k) for k in range(3) for j in range(3) for i in range(3)])
+    nodes = (base[:, None, :] - lo + off[None, :, :])
+    lin = (nodes[..., 2] * dim[1] + nodes[..., 1]) * dim[0] + nodes[..., 0]
+    pairs = np.stack([lin.ravel(), np.repeat(codes, 27)], axis=1)
+    expect = len(np.unique(pairs, axis=0))
+    info = g.info()
+    assert info.n_slots == expect
+    assert info.n_slots <= info.slot_capacity
+
+
+# --------------------------------------------------------------------------
+# determinism: batch vs plain, tile sizes
+# --------------------------------------------------------------------------
+
+def test_batched_equals_plain_bitwise(pkg):
+    scenes = [_touching_block(size=(0.04, 0.02, 0.02)),
+              _touching_block(size=(0.03, 0.015, 0.02), speed=0.3),
+              bi.single_cut_cuboid(size=(0.05, 0.02, 0.025), edge_z0=0.026, speed=0.8)]
+    plain = [pkg.Scene(s) for s in scenes]
+    for p in plain:
+        p.step(24)
+    ref = [p.read("x", "v", "F", "mask1", "mask2") for p in plain]
+    for tiles in [(256, 128), (128, 64), (512, 256)]:
+        b = pkg.Batch(max_particles=sum(s.n for s in scenes) + 1000, max_nodes=200000,
+                      max_scenes=8, graph_chunk=8, particle_tile=tiles[0], node_tile=tiles[1])
+        gs = [pkg.Scene(s) for s in scenes]
+        for s in gs:
+            b.add(s)
+        b.step(24)
+        for s, r in zip(gs, ref):
+            got = s.read("x", "v", "F", "mask1", "mask2")
+            for k in r:
+                assert np.array_equal(got[k], r[k]), (tiles, k)
+        b.close()
+
+
+def test_batch_remove_keeps_state(pkg):
+    sc = _touching_block()
+    b = pkg.Batch(max_particles=20000, max_nodes=20000, max_scenes=4)
+    s = pkg.Scene(sc)
+    b.add(s)
+    b.step(10)
+    x10 = s.read("x")["x"]
+    b.remove(s)
+    assert np.array_equal(s.read("x")["x"], x10)
+    s.step(5)
+    o = O.OracleScene(sc)
+    o.step(15)
+    assert np.max(np.abs(s.read("x")["x"] - o.get("x"))) < 1e-5 * domain(sc)
+    b.close()
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+
+def _compare(pkg, sc, steps, tol_rel=1e-5):
+    o = O.OracleScene(sc)
+    o.step(steps)
+    g = pkg.Scene(sc)
+    g.step(steps)
+    err = np.max(np.abs(g.read("x")["x"] - o.get("x")))
+    assert err <= tol_rel * max(domain(sc), sc.dx), err
+    assert g.info().error_bits == 0
+    return o, g
+
+
+def test_single_particle(pkg):
+    dx = 5e-3
+    sc = bi.Scene(X=np.array([[0.0123, 0.0071, 0.0031]]), dx=dx, V0=dx ** 3 / 8)
+    _compare(pkg, sc, 30)
+
+
+def test_ragged_tail_and_jitter(pkg):
+    X = bi.lattice_cuboid((0.035, 0.015, 0.02), 5e-3, jitter=0.4, seed=5)
+    X = X[: X.shape[0] - 37]  # ragged: not a multiple of any tile
+    blade = bi.Blade(pose_x=(0.0175, 0.0075, 0.0201),
+                     segments=[bi.Segment(100, v=(0, 0, -0.6), cut_id=0)])
+    sc = bi.Scene(X=X, dx=5e-3, V0=(5e-3) ** 3 / 8, blade=blade)
+    _compare(pkg, sc, 40)
+
+
+def test_cylinder_partial_cells(pkg):
+    X = bi.lattice_cylinder(0.04, 0.01, 2e-3)
+    blade = bi.Blade(pose_x=(0.02, 0.01, 0.0201), pose_R=bi.rot_z(15.0),
+                     segments=[bi.Segment(100, v=(0, 0, -0.8), cut_id=0)])
+    sc = bi.Scene(X=X, dx=2e-3, V0=(2e-3) ** 3 / 8, E=5e4, nu=0.35, dt=5e-5, blade=blade)
+    _compare(pkg, sc, 40)
+
+
+def test_many_cuts_and_high_digits(pkg):
+    """Intersecting strokes on cut ids 0, 5 and 31 (the last mask bit)."""
+    X = bi.lattice_cuboid((0.03, 0.03, 0.02), 5e-3)
+    wz = math.radians(60.0) / (5 * 1e-4)
+    segs = [bi.Segment(30, v=(0, 0, -8.0), cut_id=0), bi.Segment(30, v=(0, 0, 8.0), cut_id=0),
+            bi.Segment(5, omega=(0, 0, wz)),
+            bi.Segment(30, v=(0, 0, -8.0), cut_id=5), bi.Segment(30, v=(0, 0, 8.0), cut_id=5),
+            bi.Segment(5, omega=(0, 0, wz)),
+            bi.Segment(30, v=(0, 0, -8.0), cut_id=31)]
+    blade = bi.Blade(pose_x=(0.015, 0.015, 0.021), segments=segs)
+    sc = bi.Scene(X=X, dx=5e-3, V0=(5e-3) ** 3 / 8, blade=blade, tool_contact=False,
+                  gravity=(0, 0, 0), floor=False)
+    o, g = _compare(pkg, sc, 160)
+    oc = o.get("code")
+    gc = g.read("code")["code"]
+    assert np.array_equal(oc, gc)
+    assert len(np.unique(gc)) >= 6
+    assert np.any(gc >= 3 ** 31)
+
+
+def test_rest_is_exact_on_gpu(pkg):
+    X = bi.lattice_cuboid((0.02, 0.02, 0.02), 5e-3)
+    sc = bi.Scene(X=X, dx=5e-3, V0=(5e-3) ** 3 / 8, gravity=(0, 0, 0), floor=False)
+    g = pkg.Scene(sc)
+    g.step(10)
+    r = g.read("x", "v", "F")
+    assert np.array_equal(r["x"], X.astype(np.float32))
+    assert np.all(r["v"] == 0) and np.all(r["F"] == np.eye(3).ravel()[None].astype(np.float32))
+
+
+def test_momentum_balance_on_gpu(pkg):
+    """Eq. 18 on the float32 path: P changes only by the applied impulses."""
+    sc = _touching_block(size=(0.03, 0.02, 0.02)).replace(gravity=(0, 0, 0), floor=False)
+    g = pkg.Scene(sc, wrench_history=40)
+    m = sc.rho * sc.V0
+    P = [m * g.read("v")["v"].astype(np.float64).sum(0)]
+    for _ in range(20):
+        g.step(1)
+        P.append(m * g.read("v")["v"].astype(np.float64).sum(0))
+    W = g.wrench_history(0, 20)
+    dP = np.diff(np.array(P), axis=0)
+    # the only impulse is the tool's: dP = -dt * F_B
+    assert np.max(np.abs(dP + sc.dt * W[:, :3])) <= 1e-4 * np.max(np.abs(sc.dt * W[:, :3]))
