@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: batched TLMPM cutting substeps on GB300.
+
+Workload: 256 uneven cuboid scenes (particle counts log-uniform in 4k-64k,
+E log-uniform 1e4-1e6 Pa, nu uniform 0.25-0.45, seeded blade planes and
+speeds 0.05-0.5 m/s, per-scene CFL substep), held in one packed batch and
+advanced by CUDA-graph launches.  One "step" is one substep of every scene.
+Metric: particle-substeps/s (whole job, all ranks).
+
+Keys beyond the value: the plain one-scene-per-launch path on the same scenes
+(``plain``), the end-to-end rate through the C ABI with per-step host I/O
+(``e2e``), the dominant kernel's roofline (``roofline``, live CUDA events),
+sampled SM clocks (``clocks``) and the FP64 oracle on the host cores
+(``cpu_baseline``).  ``--impl reference`` times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import bm_inputs as bi  # noqa: E402
+
+METRIC = "particle-substeps/s (batched, 256 uneven scenes)"
+UNIT = "particle-substeps/s"
+WORKLOAD = "batched 256 uneven neo-Hookean cuboids, 4k-64k particles, 1 cut each"
+N_SCENES = 256
+SEED = 2
+SMS = 152
+FP32_LANES = 128
+FALLBACK_HBM_GBS = 6800.0
+
+# Per-kernel algorithmic traffic (bytes) and FP32 work (flop, FMA = 2) per
+# particle, per node and per occupied slot -- the compulsory reads/writes of
+# each kernel's own inputs and outputs (see the design notes).
+KERNEL_MODEL = {
+    "k_pre": {"bytes": (148, 0, 0), "flops": (420, 0, 0)},
+    "k_p2g": {"bytes": (80, 9, 32), "flops": (27 * 54, 0, 60)},
+    "k_g2p": {"bytes": (72, 0, 32), "flops": (27 * 16 + 40, 0, 0)},
+    "k_musl": {"bytes": (32, 9, 16), "flops": (27 * 21, 0, 10)},
+    "k_fupd": {"bytes": (96, 0, 16), "flops": (27 * 26 + 40, 0, 0)},
+}
+STEP_ALGORITHMIC_BYTES = 156  # per particle-substep: the state the method must move
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.path = tempfile.mktemp(prefix="bm_clocks_", suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_2609_27342_gb300", "csrc", "bm_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, units: dict):
+    """Per-launch DRAM traffic from the committed ncu summary, scaled by units,
+    or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return k["bytes_per_particle"] * units["particles"]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (host cores)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(scenes, seconds: float = 12.0, min_rounds: int = 2, max_rounds: int = 10 ** 6,
+                threads: int = 0):
+    """Run oracle substeps of the given scenes in parallel threads until the
+    time budget is spent.  Returns (particle-substeps/s, threads, rounds)."""
+    from oracle import oracle as O
+    O.build()
+    threads = threads or os.cpu_count() or 1
+    objs = [O.OracleScene(sc) for sc in scenes]
+    pool = ThreadPoolExecutor(max_workers=threads)
+    total, rounds = 0, 0
+    t0 = time.perf_counter()
+    while rounds < max_rounds and (rounds < min_rounds or time.perf_counter() - t0 < seconds):
+        list(pool.map(lambda o: o.step(1), objs))
+        total += sum(o.n for o in objs)
+        rounds += 1
+    wall = time.perf_counter() - t0
+    pool.shutdown()
+    return total / wall, min(threads, len(objs)), rounds, wall
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_native(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2609_27342_gb300 import build as B
+    B.build()
+    import paper_2609_27342_gb300 as pkg
+    pkg.load()
+
+    scenes = bi.batched_scenes(N_SCENES, seed=SEED, n_substeps=100000)
+    n_particles = sum(s.n for s in scenes)
+    stream = torch.cuda.Stream()
+    nodes = [pkg.footprint(s)[1] for s in scenes]
+
+    # plain one-scene-per-launch path on the same scenes
+    plain_objs = [pkg.Scene(s, stream=stream) for s in scenes]
+    plain_steps = args.plain_steps
+    for o in plain_objs:
+        o.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for o in plain_objs:
+            o.step(plain_steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    plain_rate = n_particles * plain_steps / (plain_ms * 1e-3)
+    log(f"plain path: {plain_rate:.3e} p-s/s ({plain_ms:.1f} ms for {plain_steps} substeps)")
+
+    batch = pkg.Batch(max_particles=n_particles, max_nodes=sum(nodes), max_scenes=N_SCENES,
+                      graph_chunk=args.chunk, particle_tile=args.ptile, node_tile=args.ntile,
+                      stream=stream)
+    for o in plain_objs:
+        batch.add(o)
+    # warm-up (also captures the graphs)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    infos = [o.info() for o in plain_objs]
+    n_slots = sum(i.n_slots for i in infos)
+    n_nodes = sum(i.n_nodes for i in infos)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_particles * args.steps / (ms * 1e-3)
+    err_bits = batch.errors()
+
+    # per-kernel device times over the same number of substeps (live events)
+    prof = batch.profile(max(3, min(args.steps, 20)))
+    ktimes = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
+    units = {"particles": n_particles, "nodes": n_nodes, "slots": n_slots}
+    dom = max(KERNEL_MODEL, key=lambda k: ktimes.get(k, 0.0))
+    mb, mf = KERNEL_MODEL[dom]["bytes"], KERNEL_MODEL[dom]["flops"]
+    alg_bytes = mb[0] * n_particles + mb[1] * n_nodes + mb[2] * n_slots
+    alg_flops = mf[0] * n_particles + mf[1] * n_nodes + mf[2] * n_slots
+    t_dom = ktimes[dom] * 1e-3
+    hbm_peak, hbm_src = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or 1900.0
+    alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    gbs = alg_bytes / t_dom / 1e9
+    tfs = alg_flops / t_dom / 1e12
+    hbm_frac, alu_frac = gbs / hbm_peak, tfs / alu_peak
+    if hbm_frac >= alu_frac:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "peak_source": hbm_src}
+    else:
+        roof = {"bound": "alu", "achieved": round(tfs, 3), "peak": round(alu_peak, 2),
+                "unit": "TFLOP/s", "frac": round(alu_frac, 4),
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"}
+    traffic = ncu_traffic(dom, units)
+    roof.update({"kernel": dom, "traffic": traffic, "algorithmic_bytes": alg_bytes,
+                 "algorithmic_flops": alg_flops, "avg_launch_ms": round(ktimes[dom], 4),
+                 "hbm_frac": round(hbm_frac, 4), "alu_frac": round(alu_frac, 4),
+                 "kernel_ms": {k: round(v, 4) for k, v in ktimes.items()}})
+    step_ms = ms / args.steps
+    step_roof = STEP_ALGORITHMIC_BYTES * n_particles / (step_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI: host tool states in, wrenches out, each step
+    n = len(plain_objs)
+    h_states = torch.empty((n, 18), dtype=torch.float64, pin_memory=True)
+    h_wr = torch.empty((n, 6), dtype=torch.float64, pin_memory=True)
+    st0 = np.stack([o.tool_state() for o in plain_objs])
+    vel = st0[:, 12:15].copy()
+    dts = np.array([s.dt for s in scenes])
+    pose = st0.copy()
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pose[:, 0:3] += vel * dts[:, None]
+        h_states.numpy()[:] = pose
+        batch.set_tool_states_ptr(h_states.data_ptr(), n, False)
+        batch.step(1)
+        batch.tool_wrenches_ptr(h_wr.data_ptr(), n, False)
+    wall = time.perf_counter() - t0
+    e2e_value = world * n_particles * e2e_steps / wall
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = scenes[:16]
+        rate, thr, rounds, wall_c = oracle_rate(sample, seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"first 16 of the 256 scenes ({sum(s.n for s in sample)} particles), "
+                         f"{rounds} substeps each, FP64 C oracle, one scene per thread, "
+                         f"{wall_c:.1f} s wall"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scenes": N_SCENES, "particles": n_particles,
+                       "nodes": n_nodes, "slots": n_slots, "seed": SEED,
+                       "substeps_timed": args.steps, "graph_chunk": args.chunk,
+                       "particle_tile": args.ptile, "node_tile": args.ntile,
+                       "parallelism": f"scene-sharded x{world} (each rank its own batch)",
+                       "l2": "inputs larger than L2 (state ~1.2 GB vs 129 MB L2)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 18 * 8,
+                    "d2h_bytes_per_step": n * 6 * 8, "steps": e2e_steps,
+                    "api": "bm_batch_set_tool_states + bm_batch_step + bm_batch_tool_wrenches"},
+            "gpu_launches": 9 * args.steps,
+            "roofline": roof,
+            "step_hbm_roofline": {"bytes_per_particle_substep": STEP_ALGORITHMIC_BYTES,
+                                  "achieved": round(step_roof, 1), "peak": hbm_peak,
+                                  "unit": "GB/s", "frac": round(step_roof / hbm_peak, 4)},
+            "plain": {"value": plain_rate, "unit": UNIT, "substeps": plain_steps,
+                      "launches_per_substep_per_scene": 9},
+            "batched_over_plain": value / world / plain_rate,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "error_bits": err_bits,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    scenes = bi.batched_scenes(N_SCENES, seed=SEED, n_substeps=100000)[:16]
+    from oracle import oracle as O
+    O.build()
+    threads = os.cpu_count() or 1
+    objs = [O.OracleScene(sc) for sc in scenes]
+    pool = ThreadPoolExecutor(max_workers=threads)
+    for _ in range(args.warmup):
+        list(pool.map(lambda o: o.step(1), objs))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        list(pool.map(lambda o: o.step(1), objs))
+    wall = time.perf_counter() - t0
+    pool.shutdown()
+    n = sum(o.n for o in objs)
+    value = n * args.steps / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scenes": N_SCENES, "seed": SEED,
+                   "sample": f"first 16 scenes ({n} particles) per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, len(objs)),
+                         "kind": "oracle",
+                         "sample": f"first 16 of the 256 scenes, {args.steps} substeps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--chunk", type=int, default=16)
+    ap.add_argument("--ptile", type=int, default=256)
+    ap.add_argument("--ntile", type=int, default=128)
+    ap.add_argument("--plain-steps", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

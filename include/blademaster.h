@@ -237,6 +237,13 @@ int bm_batch_tool_wrenches(bm_batch_t b, double *out, int n, int on_device);
 int bm_batch_members(bm_batch_t b, bm_scene_t *out, int cap);
 /* Largest sticky error word over the members (OR of BM_ERRBIT_*); syncs. */
 int bm_batch_errors(bm_batch_t b, uint32_t *bits);
+/* Profiling hook: run n_substeps eagerly (no graph) with CUDA events around
+ * every kernel launch on the batch stream; ms[k] receives the summed device
+ * time of kernel k over the run and launches[k] its launch count (cap >= 9
+ * entries; names from bm_kernel_name).  Returns the kernel count (>= 0) or
+ * a bm_status.  Advances the simulation like bm_batch_step. */
+int bm_batch_profile(bm_batch_t b, int n_substeps, double *ms, int *launches, int cap);
+const char *bm_kernel_name(int i);
 /* Set tile sizes used by subsequent bm_batch_step calls (autotuner hook). */
 int bm_batch_set_tiles(bm_batch_t b, int particle_tile, int node_tile);
 int bm_batch_destroy(bm_batch_t b);

@@ -115,6 +115,8 @@ SIGNATURES = {
     "bm_batch_errors": (C.c_int, [VP, C.POINTER(C.c_uint32)]),
     "bm_batch_set_tiles": (C.c_int, [VP, C.c_int, C.c_int]),
     "bm_batch_destroy": (C.c_int, [VP]),
+    "bm_batch_profile": (C.c_int, [VP, C.c_int, PD, C.POINTER(C.c_int), C.c_int]),
+    "bm_kernel_name": (C.c_char_p, [C.c_int]),
     "bm_last_error": (C.c_char_p, []),
     "bm_version": (C.c_char_p, []),
 }

@@ -17,7 +17,7 @@
 
 #include "../../include/blademaster.h"
 
-#define BM_MAXS 8            // logical grids (distinct codes) per node
+#define BM_MAXS 16           // logical grids (distinct codes) per node
 #define BM_HIST 8            // pair-contact history entries per particle
 #define BM_WRENCH_W 6
 
@@ -140,7 +140,10 @@ struct LaunchSet {
 };
 
 // kernel launchers (bm_kernels.cu)
+#define BM_NUM_KERNELS 9
+extern const char *const bm_kernel_names[BM_NUM_KERNELS];
 cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st);
+cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev);
 cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t st);
 cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t st, int force);
 cudaError_t bm_launch_io(const World &w, int scene_slot, int p_begin, int n, int field, void *buf,

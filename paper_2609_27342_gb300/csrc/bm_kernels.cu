@@ -1168,25 +1168,60 @@ cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t st, int force) {
+const char *const bm_kernel_names[BM_NUM_KERNELS] = {
+    "k_pre", "k_p2g", "k_g2p", "k_musl", "k_fupd", "k_tool", "k_slot_count", "k_slot_scan", "k_slot_fill"};
+
+// ev (optional): 2 * BM_NUM_KERNELS events recorded around each launch
+static inline void rec(cudaEvent_t *ev, int k, int after, cudaStream_t st) {
+  if (ev) cudaEventRecord(ev[2 * k + after], st);
+}
+
+static cudaError_t launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t st, int force,
+                                  cudaEvent_t *ev) {
   if (ls.n_ntiles == 0) return cudaSuccess;
+  rec(ev, 6, 0, st);
   k_slot_count<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
+  rec(ev, 6, 1, st);
+  rec(ev, 7, 0, st);
   k_slot_scan<<<ls.n_scenes, 256, 0, st>>>(w, ls, force);
+  rec(ev, 7, 1, st);
+  rec(ev, 8, 0, st);
   k_slot_fill<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
+  rec(ev, 8, 1, st);
   return cudaGetLastError();
 }
 
-cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st) {
+cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t st, int force) {
+  return launch_rebuild(w, ls, st, force, nullptr);
+}
+
+cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   if (ls.n_ptiles == 0) return cudaSuccess;
+  rec(ev, 0, 0, st);
   k_pre<<<ls.n_ptiles, ls.ptile_size, 0, st>>>(w, ls);
+  rec(ev, 0, 1, st);
+  rec(ev, 1, 0, st);
   k_p2g<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
+  rec(ev, 1, 1, st);
+  rec(ev, 2, 0, st);
   k_g2p<<<ls.n_ptiles, ls.ptile_size, 0, st>>>(w, ls);
+  rec(ev, 2, 1, st);
+  rec(ev, 3, 0, st);
   k_musl<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
+  rec(ev, 3, 1, st);
+  rec(ev, 4, 0, st);
   k_fupd<<<ls.n_ptiles, ls.ptile_size, 0, st>>>(w, ls);
+  rec(ev, 4, 1, st);
+  rec(ev, 5, 0, st);
   k_tool<<<ls.n_scenes, 256, 0, st>>>(w, ls);
+  rec(ev, 5, 1, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return bm_launch_rebuild(w, ls, st, 0);
+  return launch_rebuild(w, ls, st, 0, ev);
+}
+
+cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st) {
+  return bm_launch_substep_ev(w, ls, st, nullptr);
 }
 
 cudaError_t bm_launch_io(const World &w, int scene_slot, int p_begin, int n, int field, void *buf,

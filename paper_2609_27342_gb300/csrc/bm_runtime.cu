@@ -1076,6 +1076,45 @@ int bm_batch_step(bm_batch_t b, int n_substeps) {
   return BM_OK;
 }
 
+int bm_batch_profile(bm_batch_t b, int n_substeps, double *ms, int *launches, int cap) {
+  if (!b || n_substeps <= 0 || !ms || cap < BM_NUM_KERNELS) return fail(BM_E_INVALID, "bad arguments");
+  WorldH *W = b->world;
+  if (W->members.empty()) return 0;
+  if (W->tiles_dirty) {
+    int r = rebuild_tiles(W);
+    if (r) return r;
+  }
+  LaunchSet ls = world_set(W);
+  std::vector<cudaEvent_t> ev(2 * BM_NUM_KERNELS);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  for (int k = 0; k < BM_NUM_KERNELS; ++k) {
+    ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+  }
+  int rc = BM_OK;
+  for (int i = 0; i < n_substeps && rc == BM_OK; ++i) {
+    cudaError_t e = bm_launch_substep_ev(W->w, ls, W->st, ev.data());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(W->st);
+    if (e != cudaSuccess) {
+      rc = fail(BM_E_CUDA, std::string("profile: ") + cudaGetErrorString(e));
+      break;
+    }
+    for (int k = 0; k < BM_NUM_KERNELS; ++k) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
+        ms[k] += t;
+        if (launches) launches[k] += 1;
+      }
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  return rc ? rc : BM_NUM_KERNELS;
+}
+
+const char *bm_kernel_name(int i) {
+  return (i >= 0 && i < BM_NUM_KERNELS) ? bm_kernel_names[i] : "";
+}
+
 int bm_batch_members(bm_batch_t b, bm_scene_t *out, int cap) {
   if (!b) return fail(BM_E_INVALID, "bad batch");
   int n = (int)b->world->members.size();

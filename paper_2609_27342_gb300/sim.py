@@ -262,6 +262,13 @@ class Batch:
     def tool_wrenches_ptr(self, ptr: int, n: int, on_device: bool) -> None:
         A.check(self._L.bm_batch_tool_wrenches(self._h, C.cast(ptr, A.PD), n, int(on_device)))
 
+    def profile(self, n: int) -> Dict[str, tuple]:
+        """Per-kernel (total ms, launches) over n eager substeps (CUDA events)."""
+        ms = (C.c_double * 32)()
+        cnt = (C.c_int * 32)()
+        k = A.check(self._L.bm_batch_profile(self._h, int(n), ms, cnt, 32))
+        return {self._L.bm_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+
     def errors(self) -> int:
         b = C.c_uint32()
         A.check(self._L.bm_batch_errors(self._h, C.byref(b)))

@@ -96,24 +96,25 @@ def _touching_block(speed=0.5, n_down=200, size=(0.04, 0.02, 0.02), **kw):
 def test_one_substep_all_fields(pkg):
     sc = _touching_block()
     o = O.OracleScene(sc)
-    g = pkg.Scene(sc, wrench_history=8)
-    for _ in range(3):
+    g = pkg.Scene(sc, wrench_history=12)
+    nst = 10  # the edge reaches the top particles' spheres after ~6 substeps
+    for _ in range(nst):
         o.step(1)
         g.step(1)
     r = g.read("x", "v", "F", "D", "ut")
     L = domain(sc)
-    assert np.max(np.abs(r["x"] - o.get("x"))) < 1e-7 * L
+    assert np.max(np.abs(r["x"] - o.get("x"))) < 1e-6 * L
     vs = max(1e-3, np.max(np.abs(o.get("v"))))
     assert np.max(np.abs(r["v"] - o.get("v"))) < 2e-5 * vs
     assert np.max(np.abs(r["F"] - o.get("F"))) < 1e-5
     assert np.max(np.abs(r["D"] - o.get("D"))) < 1e-4
-    wo = o.wrench_history(0, 3)
-    wg = g.wrench_history(0, 3)
+    wo = o.wrench_history(0, nst)
+    wg = g.wrench_history(0, nst)
     scale = np.max(np.abs(wo[:, :3]))
     assert scale > 0
     assert np.max(np.abs(wg[:, :3] - wo[:, :3])) < 1e-4 * scale
     info = g.info()
-    assert info.step == 3 and info.error_bits == 0
+    assert info.step == nst and info.error_bits == 0
     lo, dim = o.grid_dims()
     assert tuple(info.grid_lo) == lo and tuple(info.grid_dim) == dim
 
