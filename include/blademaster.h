@@ -193,6 +193,24 @@ int bm_tool_wrench(bm_scene_t s, int blade_id, double out[6]);
  * doubles, host).  Only the first desc.wrench_history substeps are kept. */
 int bm_wrench_history(bm_scene_t s, int blade_id, int64_t first, int64_t count, double *out);
 
+/* bm_read_state without any device allocation -- this has no counterpart in
+ * the paper; it serves callers that must not allocate device memory while the
+ * simulation runs: a real-time control loop of the external rigid-body system
+ * reading state every tick (cudaMalloc/cudaFree synchronise the device and can
+ * stall for milliseconds), or a process whose device memory is already
+ * reserved by a framework's caching allocator, where a per-call cudaMalloc
+ * can fail.  Same layout and result as bm_read_state with host destinations
+ * (dst are host pointers).  Each field is gathered into a fixed 16 MiB
+ * staging array that the library keeps in device memory for the life of the
+ * process (every GPU that loads the library holds it), then copied to dst;
+ * a field larger than 16 MiB (e.g. F beyond 466,033 particles) is rejected
+ * with BM_E_INVALID before any work is enqueued.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current -- make that first call before any stream capture.  All
+ * calls share the one array and synchronise the scene's stream before they
+ * return; calls from several threads whose GPU work overlaps race on it. */
+int bm_read_state_noalloc(bm_scene_t s, uint32_t field_mask, void *const *dst);
+
 int bm_scene_info_get(bm_scene_t s, bm_scene_info *out);
 int bm_scene_destroy(bm_scene_t s);
 

@@ -98,6 +98,7 @@ SIGNATURES = {
     "bm_step": (C.c_int, [VP, C.c_int]),
     "bm_read_state": (C.c_int, [VP, C.c_uint32, PVP, C.c_int]),
     "bm_write_state": (C.c_int, [VP, C.c_uint32, PVP, C.c_int]),
+    "bm_read_state_noalloc": (C.c_int, [VP, C.c_uint32, PVP]),
     "bm_tool_wrench": (C.c_int, [VP, C.c_int, PD]),
     "bm_wrench_history": (C.c_int, [VP, C.c_int, C.c_int64, C.c_int64, PD]),
     "bm_scene_info_get": (C.c_int, [VP, C.POINTER(SceneInfo)]),

@@ -9,6 +9,7 @@
 #include <cstddef>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -700,6 +701,92 @@ bool valid_scene(bm_scene_t s) { return s && s->world; }
 }  // namespace
 
 // ============================================================================
+// State read without allocation
+//
+// bm_read_state() gathers a field into a temporary device buffer it
+// allocates per call.  The variant below gathers into a fixed staging array
+// that lives in the library's own device memory instead, so it never calls
+// cudaMalloc/cudaFree.  The array is a file-scope __device__ symbol: every
+// GPU that loads the library reserves BM_NOALLOC_STAGE_BYTES for it until the
+// process exits.  In host code the symbol name is only a host-side stand-in,
+// so its device address is looked up once per device with
+// cudaGetSymbolAddress() (with that device current) and passed to the kernel.
+// ============================================================================
+#define BM_NOALLOC_STAGE_BYTES (16u << 20)  // 16 MiB per requested field
+
+static __device__ __align__(256) unsigned char bm_noalloc_stage[BM_NOALLOC_STAGE_BYTES];
+
+namespace {
+
+std::mutex g_stage_mu;
+std::vector<void *> g_stage_ptr;  // device ordinal -> device address of the array
+
+// set-up, once per device: resolve the array's device address
+int stage_address(void **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_stage_mu);
+  if ((int)g_stage_ptr.size() <= dev) g_stage_ptr.resize((size_t)dev + 1, nullptr);
+  if (!g_stage_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, bm_noalloc_stage);
+    if (e != cudaSuccess || !p)
+      return fail(BM_E_CUDA, std::string("cudaGetSymbolAddress(staging array): ") + cudaGetErrorString(e));
+    g_stage_ptr[dev] = p;
+  }
+  *out = g_stage_ptr[dev];
+  return BM_OK;
+}
+
+// variant of the state gather kernel: pool order -> caller order, into the
+// staging array (every element of the used range is written, so nothing in
+// the array needs clearing between calls)
+__global__ void k_gather_stage(World w, int p_begin, int n, int field, void *stage) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = p_begin + i;
+  const int o = w.P.perm[p];
+  const PPool &P = w.P;
+  float *fb = (float *)stage;
+  uint32_t *ub = (uint32_t *)stage;
+  switch (field) {
+    case 1:
+      for (int a = 0; a < 3; ++a) fb[3 * o + a] = P.x[a][p];
+      break;
+    case 2:
+      for (int a = 0; a < 3; ++a) fb[3 * o + a] = P.v[a][p];
+      break;
+    case 3:
+      for (int a = 0; a < 9; ++a) fb[9 * o + a] = P.F[a][p];
+      break;
+    case 4:
+      fb[o] = P.D[p];
+      break;
+    case 5:
+      for (int a = 0; a < 3; ++a) fb[3 * o + a] = P.ut[a][p];
+      break;
+    case 6: {
+      const uint32_t s1 = P.s1[p], s2 = P.s2[p];
+      int64_t c = 0, pw = 1;
+      for (int k = 0; k < BM_MAX_CUTS; ++k) {
+        c += (((s1 >> k) & 1u) ? 1 : (((s2 >> k) & 1u) ? 2 : 0)) * pw;
+        pw *= 3;
+      }
+      ((int64_t *)stage)[o] = c;
+      break;
+    }
+    case 7:
+      ub[o] = P.s1[p];
+      break;
+    case 8:
+      ub[o] = P.s2[p];
+      break;
+  }
+}
+
+}  // namespace
+
+// ============================================================================
 // C ABI
 // ============================================================================
 extern "C" {
@@ -875,6 +962,43 @@ int bm_write_state(bm_scene_t s, uint32_t field_mask, const void *const *src, in
   }
   if (masks) {
     CK(bm_launch_rebuild(W->w, scene_set(W, s), W->st, 1));
+    CK(cudaStreamSynchronize(W->st));
+  }
+  return BM_OK;
+}
+
+int bm_read_state_noalloc(bm_scene_t s, uint32_t field_mask, void *const *dst) {
+  if (!valid_scene(s) || !dst) return fail(BM_E_INVALID, "bad scene or destination");
+  WorldH *W = s->world;
+  const int64_t n = s->n;
+  // size check first: nothing is launched for a request the array cannot hold
+  for (int f = 0; f < BM_NUM_FIELDS; ++f) {
+    if (!(field_mask & (1u << f)) || f == 0) continue;
+    const size_t w = (f == 3) ? 9 : (f == 1 || f == 2 || f == 5) ? 3 : 1;
+    const size_t bytes = (size_t)n * w * ((f == 6) ? 8 : 4);
+    if (bytes > BM_NOALLOC_STAGE_BYTES)
+      return fail(BM_E_INVALID, "bm_read_state_noalloc: field " + std::to_string(f) + " of " +
+                                    std::to_string(n) + " particles needs " + std::to_string(bytes) +
+                                    " bytes; the staging array holds " +
+                                    std::to_string((size_t)BM_NOALLOC_STAGE_BYTES) + " bytes per field");
+  }
+  void *stage = nullptr;
+  int rc = stage_address(&stage);
+  if (rc) return rc;
+  int j = 0;
+  for (int f = 0; f < BM_NUM_FIELDS; ++f) {
+    if (!(field_mask & (1u << f))) continue;
+    void *d = dst[j++];
+    if (!d) return fail(BM_E_INVALID, "null destination pointer");
+    const size_t w = (f == 3) ? 9 : (f == 1 || f == 2 || f == 5 || f == 0) ? 3 : 1;
+    const size_t bytes = (size_t)n * w * ((f == 6) ? 8 : 4);
+    if (f == 0) {
+      std::memcpy(d, s->X.data(), bytes);
+      continue;
+    }
+    k_gather_stage<<<(unsigned)((n + 255) / 256), 256, 0, W->st>>>(W->w, (int)s->p_begin, (int)n, f, stage);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(d, stage, bytes, cudaMemcpyDeviceToHost, W->st));
     CK(cudaStreamSynchronize(W->st));
   }
   return BM_OK;

@@ -143,6 +143,22 @@ class Scene:
         A.check(self._L.bm_read_state(self._h, mask, arr, 0))
         return outs
 
+    def read_noalloc(self, *names: str) -> Dict[str, np.ndarray]:
+        """``read`` through the entry point that allocates no device memory
+        (fields up to 16 MiB each; see bm_read_state_noalloc)."""
+        names = names or ("x", "v")
+        order = sorted(names, key=lambda k: A.FIELDS[k][0])
+        mask, outs, ptrs = 0, {}, []
+        for k in order:
+            bit, w, dt = A.FIELDS[k]
+            mask |= bit
+            a = np.zeros((self.n, w) if w > 1 else (self.n,), dtype=dt)
+            outs[k] = a
+            ptrs.append(a.ctypes.data)
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        A.check(self._L.bm_read_state_noalloc(self._h, mask, arr))
+        return outs
+
     def read_device(self, fields: Dict[str, "object"]) -> None:
         """Read into device tensors (dict name -> contiguous torch tensor)."""
         order = sorted(fields, key=lambda k: A.FIELDS[k][0])
