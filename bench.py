@@ -44,17 +44,19 @@ SMS = 152
 FP32_LANES = 128
 FALLBACK_HBM_GBS = 6800.0
 
-# Per-kernel algorithmic traffic (bytes) and FP32 work (flop, FMA = 2) per
-# particle, per node and per occupied slot -- the compulsory reads/writes of
-# each kernel's own inputs and outputs (see the design notes).
+# Per-kernel compulsory traffic (bytes) and FP32 work (flop, FMA = 2) per
+# particle, per node, per occupied slot and per 4x4x4-cell brick: the reads
+# and writes of each kernel's own inputs and outputs, with brick-tile
+# partials counted at 3.375 tiles per slot (6^3 tile nodes per 4^3 cells).
 KERNEL_MODEL = {
-    "k_pre": {"bytes": (148, 0, 0), "flops": (420, 0, 0)},
-    "k_p2g": {"bytes": (80, 9, 32), "flops": (27 * 54, 0, 60)},
-    "k_g2p": {"bytes": (72, 0, 32), "flops": (27 * 16 + 40, 0, 0)},
-    "k_musl": {"bytes": (32, 9, 16), "flops": (27 * 21, 0, 10)},
-    "k_fupd": {"bytes": (96, 0, 16), "flops": (27 * 26 + 40, 0, 0)},
+    "k_p2g_brick": {"bytes": (117, 0, 108, 480), "flops": (1050, 0, 0, 0)},
+    "k_p2g_node": {"bytes": (0, 12, 140, 0), "flops": (0, 0, 40, 0)},
+    "k_g2p_musl": {"bytes": (72, 0, 162, 1080), "flops": (570, 0, 0, 0)},
+    "k_musl_node": {"bytes": (0, 12, 86, 0), "flops": (0, 0, 20, 0)},
+    "k_fupd": {"bytes": (97, 0, 54, 1080), "flops": (650, 0, 0, 0)},
 }
 STEP_ALGORITHMIC_BYTES = 156  # per particle-substep: the state the method must move
+LAUNCHES_PER_SUBSTEP = 10     # kernels one batched substep launches (no pair contact)
 
 
 def log(*a):
@@ -194,29 +196,32 @@ def run_native(args):
     scenes = bi.batched_scenes(N_SCENES, seed=SEED, n_substeps=100000)
     n_particles = sum(s.n for s in scenes)
     stream = torch.cuda.Stream()
-    nodes = [pkg.footprint(s)[1] for s in scenes]
+    fps = [pkg.footprint(s) for s in scenes]
+    nodes = [f[1] for f in fps]
+    n_bricks = sum(f[2] for f in fps)
 
     # plain one-scene-per-launch path on the same scenes
     plain_objs = [pkg.Scene(s, stream=stream) for s in scenes]
     plain_steps = args.plain_steps
-    for o in plain_objs:
-        o.step(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    plain_rate = None
+    if plain_steps > 0:
         for o in plain_objs:
-            o.step(plain_steps)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
-    plain_rate = n_particles * plain_steps / (plain_ms * 1e-3)
-    log(f"plain path: {plain_rate:.3e} p-s/s ({plain_ms:.1f} ms for {plain_steps} substeps)")
+            o.step(1)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for o in plain_objs:
+                o.step(plain_steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        plain_rate = n_particles * plain_steps / (plain_ms * 1e-3)
+        log(f"plain path: {plain_rate:.3e} p-s/s ({plain_ms:.1f} ms for {plain_steps} substeps)")
 
     batch = pkg.Batch(max_particles=n_particles, max_nodes=sum(nodes), max_scenes=N_SCENES,
-                      graph_chunk=args.chunk, particle_tile=args.ptile, node_tile=args.ntile,
+                      max_bricks=n_bricks, graph_chunk=args.chunk, node_tile=args.ntile,
                       stream=stream)
     for o in plain_objs:
         batch.add(o)
@@ -253,11 +258,11 @@ def run_native(args):
     # per-kernel device times over the same number of substeps (live events)
     prof = batch.profile(max(3, min(args.steps, 20)))
     ktimes = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
-    units = {"particles": n_particles, "nodes": n_nodes, "slots": n_slots}
+    units = {"particles": n_particles, "nodes": n_nodes, "slots": n_slots, "bricks": n_bricks}
     dom = max(KERNEL_MODEL, key=lambda k: ktimes.get(k, 0.0))
     mb, mf = KERNEL_MODEL[dom]["bytes"], KERNEL_MODEL[dom]["flops"]
-    alg_bytes = mb[0] * n_particles + mb[1] * n_nodes + mb[2] * n_slots
-    alg_flops = mf[0] * n_particles + mf[1] * n_nodes + mf[2] * n_slots
+    alg_bytes = mb[0] * n_particles + mb[1] * n_nodes + mb[2] * n_slots + mb[3] * n_bricks
+    alg_flops = mf[0] * n_particles + mf[1] * n_nodes + mf[2] * n_slots + mf[3] * n_bricks
     t_dom = ktimes[dom] * 1e-3
     hbm_peak, hbm_src = measured_peaks()
     sm_mhz = clk.get("sm_mhz") or 1900.0
@@ -316,21 +321,21 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "scenes": N_SCENES, "particles": n_particles,
                        "nodes": n_nodes, "slots": n_slots, "seed": SEED,
-                       "substeps_timed": args.steps, "graph_chunk": args.chunk,
-                       "particle_tile": args.ptile, "node_tile": args.ntile,
+                       "bricks": n_bricks, "substeps_timed": args.steps,
+                       "graph_chunk": args.chunk, "node_tile": args.ntile,
                        "parallelism": f"scene-sharded x{world} (each rank its own batch)",
                        "l2": "inputs larger than L2 (state ~1.2 GB vs 129 MB L2)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 18 * 8,
                     "d2h_bytes_per_step": n * 6 * 8, "steps": e2e_steps,
                     "api": "bm_batch_set_tool_states + bm_batch_step + bm_batch_tool_wrenches"},
-            "gpu_launches": 9 * args.steps,
+            "gpu_launches": LAUNCHES_PER_SUBSTEP * args.steps,
             "roofline": roof,
             "step_hbm_roofline": {"bytes_per_particle_substep": STEP_ALGORITHMIC_BYTES,
                                   "achieved": round(step_roof, 1), "peak": hbm_peak,
                                   "unit": "GB/s", "frac": round(step_roof / hbm_peak, 4)},
             "plain": {"value": plain_rate, "unit": UNIT, "substeps": plain_steps,
-                      "launches_per_substep_per_scene": 9},
-            "batched_over_plain": value / world / plain_rate,
+                      "launches_per_substep_per_scene": LAUNCHES_PER_SUBSTEP},
+            "batched_over_plain": (value / world / plain_rate) if plain_rate else None,
             "clocks": clk,
             "cpu_baseline": cpu,
             "error_bits": err_bits,
@@ -386,7 +391,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--chunk", type=int, default=16)
-    ap.add_argument("--ptile", type=int, default=256)
     ap.add_argument("--ntile", type=int, default=128)
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

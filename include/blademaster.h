@@ -223,10 +223,10 @@ typedef struct {
   int64_t max_particles;   /* pool capacities */
   int64_t max_nodes;
   int64_t max_slots;       /* <=0 -> 4 x max_nodes */
+  int64_t max_bricks;      /* 4x4x4-cell bricks, <=0 -> max_nodes/27 + max_scenes (always enough) */
   int max_scenes;
   int graph_chunk;         /* substeps per captured graph, <=0 -> 16 */
-  int particle_tile;       /* particles per CTA tile: 128, 256 or 512; <=0 -> 256 */
-  int node_tile;           /* nodes per CTA tile: 64..512; <=0 -> 128 */
+  int node_tile;           /* nodes per CTA of the per-node kernels: 64..512; <=0 -> 128 */
   int pair_contact;        /* reserve pair-contact history for member scenes */
 } bm_batch_desc;
 
@@ -238,9 +238,10 @@ int bm_batch_add(bm_batch_t b, bm_scene_t s);
 /* Move a scene out of the batch into buffers of its own. */
 int bm_batch_remove(bm_batch_t b, bm_scene_t s);
 int bm_batch_step(bm_batch_t b, int n_substeps);
-/* Bytes of device memory a scene with these parameters takes in a batch. */
+/* Pool needs of a scene with these parameters: particles, reference-grid
+ * nodes, 4x4x4-cell bricks and total device bytes (any output may be NULL). */
 int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
-                       int64_t *particles, int64_t *nodes, int64_t *bytes);
+                       int64_t *particles, int64_t *nodes, int64_t *bricks, int64_t *bytes);
 /* Tool state of every member, in membership order (the order of
  * bm_batch_members): states[n][18] = {x_B[3], R[9], v_B[3], omega_B[3]};
  * n must equal the member count.  on_device != 0: a device pointer.
@@ -262,8 +263,11 @@ int bm_batch_errors(bm_batch_t b, uint32_t *bits);
  * a bm_status.  Advances the simulation like bm_batch_step. */
 int bm_batch_profile(bm_batch_t b, int n_substeps, double *ms, int *launches, int cap);
 const char *bm_kernel_name(int i);
-/* Set tile sizes used by subsequent bm_batch_step calls (autotuner hook). */
-int bm_batch_set_tiles(bm_batch_t b, int particle_tile, int node_tile);
+/* Launch shape used by subsequent bm_batch_step calls (autotuner hook):
+ * substeps per captured CUDA graph (1..256) and nodes per CTA of the
+ * per-node kernels (multiple of 32 in 64..512).  Results do not depend on
+ * either: every sum is taken in a fixed order. */
+int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile);
 int bm_batch_destroy(bm_batch_t b);
 
 const char *bm_last_error(void);

@@ -73,7 +73,7 @@ class SceneInfo(C.Structure):
 
 class BatchDesc(C.Structure):
     _fields_ = [("max_particles", C.c_int64), ("max_nodes", C.c_int64), ("max_slots", C.c_int64),
-                ("max_scenes", C.c_int), ("graph_chunk", C.c_int), ("particle_tile", C.c_int),
+                ("max_bricks", C.c_int64), ("max_scenes", C.c_int), ("graph_chunk", C.c_int),
                 ("node_tile", C.c_int), ("pair_contact", C.c_int)]
 
 
@@ -109,7 +109,7 @@ SIGNATURES = {
     "bm_batch_step": (C.c_int, [VP, C.c_int]),
     "bm_scene_footprint": (C.c_int, [C.POINTER(SceneDesc), C.POINTER(C.c_float), C.c_int64,
                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64),
-                                     C.POINTER(C.c_int64)]),
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "bm_batch_set_tool_states": (C.c_int, [VP, PD, C.c_int, C.c_int]),
     "bm_batch_tool_wrenches": (C.c_int, [VP, PD, C.c_int, C.c_int]),
     "bm_batch_members": (C.c_int, [VP, PVP, C.c_int]),

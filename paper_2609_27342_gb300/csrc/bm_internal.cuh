@@ -18,7 +18,10 @@
 #include "../../include/blademaster.h"
 
 #define BM_MAXS 16           // logical grids (distinct codes) per node
-#define BM_HIST 8            // pair-contact history entries per particle
+#define BM_TILE_SLOTS 1296   // shared-memory window of brick-tile slots (6 per tile node)
+#define BM_TILE_NODES 216    // 6 x 6 x 6 nodes touched by a brick of 4 x 4 x 4 base cells
+#define BM_BRICK_CELLS 64
+#define BM_HIST 16           // pair-contact history entries per particle
 #define BM_WRENCH_W 6
 
 struct DevSeg {
@@ -34,12 +37,14 @@ struct DevScene {
   int node_begin, n_node;
   int cell_begin, n_cell;
   int slot_begin, slot_cap;
-  int ptile_begin, n_ptile;
+  int brick_begin, n_brick;
   int ntile_begin, n_ntile;
+  int ppool_begin, ppool_cap;  // brick-tile partial sums (entries)
   int hist_begin;           // wrench history offset (in wrench records)
   int hist_cap;
   int nb[3];                // base-cell grid
   int nn[3];                // node grid = nb + 2
+  int nbr[3];               // brick grid = ceil(nb / 4)
   // material / discretisation (float32 for the particle kernels)
   float dx, inv_dx;
   float mp, V0, Rp, dt, beta, g[3], mu, lam;
@@ -47,6 +52,8 @@ struct DevScene {
   float s_n, gamma_k, gamma_c;
   float pair_mu_s, pair_mu_d;
   float floor_z;
+  float pair_h, pair_inv_h;  // pair-contact cell size of this substep
+  int pair_vmax_bits;        // max particle speed of this substep (float bits)
   int floor_on, pair_on, tool_contact_on, has_blade;
   // float64 copies used by the exact label path and the tool integrator
   double dt_d, h_d, L_d, b_back_d, b_lead_d;
@@ -70,7 +77,7 @@ struct DevScene {
   // counters and flags
   long long step;
   unsigned int err;
-  int list_count;
+  int label_pending;
   int need_rebuild;
   int n_slots;
   int pad_[2];
@@ -81,16 +88,15 @@ struct PPool {
   uint32_t *base;           // packed local base cell: bx | by << 10 | bz << 20
   float *x[3], *v[3], *F[9], *D, *ut[3];
   uint32_t *s1, *s2;        // bit k: digit k == 1 (s1) or == 2 (s2)
-  float *A[9];              // -dt V0 P(F), written by the pre kernel
-  float *J[3];              // contact + body impulse of this substep
+  float *J[3];              // pair-contact impulse of this substep
+  uint8_t *pend;            // side digit assigned this substep (0: none), committed by k_fupd
   int *perm;                // pool index -> caller's particle index
-  int *list;                // new side labels of this substep (per-scene range)
   // pair contact
-  int *hkey;                // hashed cell of each particle
-  int *hcell;               // cell coordinates packed (for exact match)
-  int *horder;              // particles sorted by bucket
-  int *hist_partner[2];     // pair history, double buffered by step parity
-  float *hist_u[2];         // [p * BM_HIST + k] * 3
+  int *hkey;                // bucket of each particle's current-configuration cell
+  long long *hcell;         // that cell's packed coordinates (exact match on lookup)
+  int *horder;              // particles ordered by bucket, by pool index inside a bucket
+  int *hist_partner[2];     // pair history (partner pool index, -1 ends), by step parity
+  float *hist_u[2];         // [(p * BM_HIST + k) * 3]: tangential spring displacement
 };
 
 struct NPool {
@@ -108,11 +114,19 @@ struct SPool {
   uint2 *code;              // (s1, s2)
 };
 
+struct BPool {              // brick-tile partial sums
+  float4 *pm;               // [poff[brick] + tile slot]: (sum N, sum N v) / MUSL sum N v
+  float4 *pd;               // [poff[brick] + tile slot]: sum (A grad N + N J)
+  uint16_t *plo;            // [brick * BM_TILE_NODES]: first tile slot of each tile node
+  int *poff;                // first entry of each brick's partial sums (-1: pool overflow)
+  int *ptot;                // slots in each brick's tile
+};
+
 struct HashPool {           // pair-contact spatial hash (world-wide table)
-  int *bucket_start;        // [n_buckets + 1]
+  int *bucket_start;        // [n_buckets + 1]: counts, then exclusive offsets
   int *bucket_fill;         // [n_buckets]
-  int *block_sum;
-  int n_buckets;
+  int *block_sum;           // [n_buckets / 1024 + 1]
+  int n_buckets;            // power of two
 };
 
 struct World {
@@ -120,16 +134,18 @@ struct World {
   PPool P;
   NPool N;
   SPool S;
+  BPool B;
   HashPool H;
-  double *wpart;            // per particle tile wrench partials (6 doubles)
+  double *wpart;            // per brick wrench partials (6 doubles)
   double *whist;            // wrench history records (6 doubles)
 };
 
-// tiles: x = scene slot, y = first pool index, z = count, w = tile id
+// brick tiles: x = scene slot, y = pool brick, z = first particle, w = particle count
+// node tiles:  x = scene slot, y = first pool node, z = count, w = tile id
 struct LaunchSet {
-  const int4 *ptiles;
-  int n_ptiles;
-  int ptile_size;
+  const int4 *btiles;
+  int n_btiles;
+  int ppc16;                // some scene has more than 8 particles in a base cell
   const int4 *ntiles;
   int n_ntiles;
   int ntile_size;
@@ -140,8 +156,9 @@ struct LaunchSet {
 };
 
 // kernel launchers (bm_kernels.cu)
-#define BM_NUM_KERNELS 9
+#define BM_NUM_KERNELS 18
 extern const char *const bm_kernel_names[BM_NUM_KERNELS];
+cudaError_t bm_kernels_init();  // per device: shared-memory limits of the brick kernels
 cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st);
 cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev);
 cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t st);

@@ -1,19 +1,21 @@
 // sm_103a kernels of one TLMPM cutting substep (arXiv 2609.27342, Sec. III).
 //
-//   k_pre      per particle: tool + floor contact (Eq. 14-15, friction Eq. 12),
-//              cutting progress D and release (Eq. 5), reaction wrench (Eq. 16,
-//              deterministic block tree), side labels for the next substep
-//              (Eq. 3, 4, 6), neo-Hookean stress -> A = -dt V0 P(F)
-//   k_p2g      per node: atomic-free gather over the node's fixed reference
-//              neighbourhood (Eq. 1-2), per logical grid; coupling (Eq. 8) and
-//              grid update (Eq. 9) in registers
-//   k_g2p      per particle: PIC/FLIP velocity (Eq. 17) and x update
-//   k_musl     per node: re-scatter m v^{n+1} per logical grid + coupling
-//   k_fupd     per particle: F += dt sum v* (x) grad0 N
-//   k_tool     per scene: commit labels, reduce the wrench, rigid tool step,
-//              frame of the next substep
-//   k_slot_*   per node: compact logical-grid slots (Sec. III-G), only in
-//              substeps after a label changed
+// Particles are sorted brick-major (4x4x4 reference base cells per brick) and
+// every particle-side kernel runs one CTA per brick:
+//   k_p2g_brick  contact (Eq. 12, 14-16), cutting progress (Eq. 5), side
+//                labels for the next substep (Eq. 3, 4, 6), neo-Hookean
+//                stress, and the brick's share of the per-code P2G sums
+//                (Eq. 2) in its 6x6x6 node tile, in shared memory
+//   k_p2g_node   per node: the <= 8 overlapping brick tiles summed in brick
+//                order, coupling (Eq. 8), grid update (Eq. 9)
+//   k_g2p_musl   G2P (Eq. 17), x update, the brick's share of the MUSL
+//                re-scatter
+//   k_musl_node  per node: MUSL sums, coupling, v*
+//   k_fupd       F update, commit of the new side labels
+//   k_tool       per scene: wrench, rigid tool step, next frame
+//   k_slot_*     compact logical-grid slots (Sec. III-G) after label changes
+// No atomics touch floating-point sums: every sum is taken in a fixed order,
+// so a scene gives bit-identical results alone or inside any batch.
 //
 // All arithmetic is float32 except the tool state and the near-threshold
 // fallback of the side-label predicate, which is float64 with explicitly
@@ -240,25 +242,272 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
   return t;  // valid in thread 0
 }
 
+// exclusive block scan of one int per thread (fixed order); total in all threads
+__device__ __forceinline__ int block_excl_scan(int v, int *sm, int &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) sm[wid] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int i = 0; i < nw; ++i) {
+      int t = sm[i];
+      sm[i] = acc;
+      acc += t;
+    }
+    sm[nw] = acc;
+  }
+  __syncthreads();
+  total = sm[nw];
+  return x - v + sm[wid];
+}
+
 // --------------------------------------------------------------------------
-// k_pre
+// Brick geometry.  Particles are stored brick-major: bricks of 4x4x4 base
+// cells, cells x-fastest inside a brick, so a brick's particles form one
+// contiguous range.  A brick's particles touch the 6x6x6 node tile starting
+// at its first cell (quadratic stencil: nodes base..base+2).
 // --------------------------------------------------------------------------
-__global__ void k_pre(World w, LaunchSet ls) {
-  const int4 t = ls.ptiles[blockIdx.x];
-  const DevScene &sc = w.scenes[t.x];
+#define BR 4
+#define BR3 64
+#define TE 6
+#define TN 216
+#define TSCAP BM_TILE_SLOTS
+#define BT 192  // threads per brick CTA: 64 cells x 3 z-offsets
+
+__device__ __forceinline__ void node_coords(const DevScene &sc, int li, int &ix, int &iy, int &iz) {
+  ix = li % sc.nn[0];
+  int r = li / sc.nn[0];
+  iy = r % sc.nn[1];
+  iz = r / sc.nn[1];
+}
+
+// brick-major index of base cell (bx, by, bz), scene-local coordinates
+__device__ __forceinline__ int cell_index(const DevScene &sc, int bx, int by, int bz) {
+  const int b = ((bz >> 2) * sc.nbr[1] + (by >> 2)) * sc.nbr[0] + (bx >> 2);
+  return b * BR3 + (((bz & 3) * BR + (by & 3)) * BR + (bx & 3));
+}
+
+__device__ __forceinline__ void particle_base(uint32_t b, int &bx, int &by, int &bz) {
+  bx = (int)(b & 1023u);
+  by = (int)((b >> 10) & 1023u);
+  bz = (int)((b >> 20) & 1023u);
+}
+
+// Eq. 8 on ns logical grids with masses m and states S[a][nc]
+template <int NC>
+__device__ __forceinline__ void couple(int ns, const uint2 *codes, const float *m, float (*S)[NC]) {
+  float M = 0.f;
+  for (int a = 0; a < ns; ++a) M += m[a];
+  if (!(M > 0.f)) return;
+  const float iM = 1.0f / M;
+  float out[BM_MAXS][NC];
+  for (int a = 0; a < ns; ++a) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float acc = 0.f;
+      for (int b = 0; b < ns; ++b) {
+        if (b == a || conflict(codes[a].x, codes[a].y, codes[b].x, codes[b].y)) continue;
+        acc += m[a] * S[b][c] - m[b] * S[a][c];
+      }
+      out[a][c] = S[a][c] + acc * iM;
+    }
+  }
+  for (int a = 0; a < ns; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) S[a][c] = out[a][c];
+}
+
+// The node tile of one brick: for each of its 6x6x6 nodes the first tile
+// slot (the node's logical grids laid out node by node in each node's own
+// slot order), the slot count and the node's first pool slot.  A tile holds
+// at most 216 x BM_MAXS slots; shared-memory working sets cover windows of
+// TSCAP slots at a time.
+struct Tile {
+  uint16_t lo[TN];
+  uint8_t cnt[TN];
+  int goff[TN];
+  int total;
+};
+
+__device__ __forceinline__ void brick_coords(const DevScene &sc, int lb, int &c0x, int &c0y, int &c0z) {
+  c0x = (lb % sc.nbr[0]) * BR;
+  c0y = ((lb / sc.nbr[0]) % sc.nbr[1]) * BR;
+  c0z = (lb / (sc.nbr[0] * sc.nbr[1])) * BR;
+}
+
+// Cooperative load of a brick's tile (all threads; ends with a barrier).
+__device__ void tile_load(const World &w, const DevScene &sc, int c0x, int c0y, int c0z, Tile &T) {
+  for (int t = threadIdx.x; t < TN; t += blockDim.x) {
+    const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
+    int cnt = 0, off = 0;
+    if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2]) {
+      const int node = sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx;
+      cnt = w.N.slot_cnt[node];
+      off = w.N.slot_off[node];
+    }
+    T.cnt[t] = (uint8_t)cnt;
+    T.goff[t] = off;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the slot counts by one warp
+    const int lane = threadIdx.x;
+    int carry = 0;
+    for (int base = 0; base < TN; base += 32) {
+      const int t = base + lane;
+      const int v = t < TN ? (int)T.cnt[t] : 0;
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      if (t < TN) T.lo[t] = (uint16_t)(carry + x - v);
+      carry += __shfl_sync(FULL, x, 31);
+    }
+    if (lane == 0) T.total = carry;
+  }
+  __syncthreads();
+}
+
+// tile slot holding code (s1, s2) at tile node t, or -1.  Nodes with several
+// logical grids compare against the tile's codes in shared memory when the
+// tile fits the window (codes != nullptr), else against the pool's codes.
+__device__ __forceinline__ int tile_slot(const World &w, const Tile &T, const uint2 *codes, int t,
+                                         uint32_t s1, uint32_t s2) {
+  const int n = T.cnt[t];
+  const int lo = T.lo[t];
+  if (n == 1) return lo;
+  if (codes) {
+    for (int a = 0; a < n; ++a) {
+      const uint2 c = codes[lo + a];
+      if (c.x == s1 && c.y == s2) return lo + a;
+    }
+    return -1;
+  }
+  const int off = T.goff[t];
+  for (int a = 0; a < n; ++a) {
+    const uint2 c = w.S.code[off + a];
+    if (c.x == s1 && c.y == s2) return lo + a;
+  }
+  return -1;
+}
+
+// the tile's slot codes into shared memory (all threads; no barrier)
+__device__ __forceinline__ void tile_codes(const World &w, const Tile &T, uint2 *codes) {
+  for (int t = threadIdx.x; t < TN; t += blockDim.x) {
+    const int n = T.cnt[t];
+    if (n < 2) continue;
+    const int lo = T.lo[t], g = T.goff[t];
+    for (int a = 0; a < n; ++a) codes[lo + a] = w.S.code[g + a];
+  }
+}
+
+// k-th distinct code (first-occurrence order) among a cell's particles
+__device__ __forceinline__ bool cell_code(const uint32_t *s1, const uint32_t *s2, int c, int n, int k,
+                                          uint32_t &k1, uint32_t &k2) {
+  int seen = -1;
+  for (int j = 0; j < n; ++j) {
+    const uint32_t a = s1[j * BR3 + c], b = s2[j * BR3 + c];
+    bool first = true;
+    for (int q = 0; q < j; ++q)
+      if (s1[q * BR3 + c] == a && s2[q * BR3 + c] == b) {
+        first = false;
+        break;
+      }
+    if (first && ++seen == k) {
+      k1 = a;
+      k2 = b;
+      return true;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ int cell_code_count(const uint32_t *s1, const uint32_t *s2, int c, int n) {
+  int cnt = 0;
+  for (int j = 0; j < n; ++j) {
+    const uint32_t a = s1[j * BR3 + c], b = s2[j * BR3 + c];
+    bool first = true;
+    for (int q = 0; q < j; ++q)
+      if (s1[q * BR3 + c] == a && s2[q * BR3 + c] == b) {
+        first = false;
+        break;
+      }
+    cnt += first;
+  }
+  return cnt;
+}
+
+// --------------------------------------------------------------------------
+// k_p2g_brick: per particle contact, cutting progress, labels and stress,
+// then the brick's share of P2G (Eq. 2) into its node tile, per logical grid.
+//
+// Phase 0, one thread per particle: tool and floor contact (Eq. 14-15 with
+// friction Eq. 12), D update and release (Eq. 5), reaction wrench (Eq. 16),
+// side label for the next substep (Eq. 3, 4, 6), A = -dt V0 P(F).  Results
+// go to shared memory laid out [particle-in-cell][cell].
+// Phase 1, one thread per (cell, z-offset): sums over the cell's particles of
+// m N, m v N, A grad N + N J for its 9 nodes, per code present in the cell.
+// Commits go to the tile in 27 barrier-separated phases (one node offset
+// each; distinct cells hit distinct nodes), so every tile slot receives its
+// contributions in a fixed order: no atomics, bit-reproducible.
+// --------------------------------------------------------------------------
+template <int PPC>
+struct K2S {
+  Tile T;
+  uint2 codes[TSCAP];
+  float acc[7][TSCAP];
+  float pf[3][PPC * BR3];
+  float pv[3][PPC * BR3];
+  float pA[9][PPC * BR3];
+  float pJ[3][PPC * BR3];
+  uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
+  int cs[BR3 + 1];
+  double red[32];
+  int maxcodes;
+};
+
+template <int PPC>
+__global__ void __launch_bounds__(BT, 2) k_p2g_brick(World w, LaunchSet ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  K2S<PPC> &S = *reinterpret_cast<K2S<PPC> *>(smraw);
+  const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
   const PPool &P = w.P;
-  const int i = threadIdx.x;
-  const bool act = i < t.z;
-  const int p = t.y + i;
+  const int tid = threadIdx.x;
+  const int lb = bt.y - sc.brick_begin;
+  int c0x, c0y, c0z;
+  brick_coords(sc, lb, c0x, c0y, c0z);
+  const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
+  for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
+  if (tid == 0) S.maxcodes = 0;
+  tile_load(w, sc, c0x, c0y, c0z, S.T);
+  const uint2 *tcodes = S.T.total <= TSCAP ? S.codes : nullptr;
+  if (tcodes) tile_codes(w, S.T, S.codes);
+
+  // ---- phase 0: per particle ----
   double wr[6] = {0, 0, 0, 0, 0, 0};
-  int want = 0;
-  int entry = 0;
-  if (act) {
+  bool clamped = false;
+  const float dt = sc.dt, mp = sc.mp;
+  const int cut = sc.cut;
+  for (int i = tid; i < bt.w; i += BT) {
+    const int p = bt.z + i;
+    int bx, by, bz;
+    particle_base(P.base[p], bx, by, bz);
+    const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
+    const int si = (i - S.cs[c]) * BR3 + c;
     float x[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
     float v[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
+    const uint32_t s1 = P.s1[p], s2 = P.s2[p];
     float J[3] = {0.f, 0.f, 0.f};
-    const float dt = sc.dt, mp = sc.mp;
-    const int cut = sc.cut;
     float D = sc.reset_D ? 0.0f : P.D[p];
     float uh[3] = {P.ut[0][p], P.ut[1][p], P.ut[2][p]};
     if (sc.has_blade && sc.tool_contact_on) {
@@ -313,237 +562,227 @@ __global__ void k_pre(World w, LaunchSet ls) {
       } else {
         uh[0] = uh[1] = uh[2] = 0.0f;
       }
-      // Eq. 16: reaction on the tool
-      float idt = 1.0f / dt;
-      float FB[3] = {-JB[0] * idt, -JB[1] * idt, -JB[2] * idt};
-      wr[0] = FB[0];
-      wr[1] = FB[1];
-      wr[2] = FB[2];
-      wr[3] = rc[1] * FB[2] - rc[2] * FB[1];
-      wr[4] = rc[2] * FB[0] - rc[0] * FB[2];
-      wr[5] = rc[0] * FB[1] - rc[1] * FB[0];
+      const float idt = 1.0f / dt;
+      const float FB[3] = {-JB[0] * idt, -JB[1] * idt, -JB[2] * idt};
+      wr[0] += FB[0];
+      wr[1] += FB[1];
+      wr[2] += FB[2];
+      wr[3] += rc[1] * FB[2] - rc[2] * FB[1];
+      wr[4] += rc[2] * FB[0] - rc[0] * FB[2];
+      wr[5] += rc[0] * FB[1] - rc[1] * FB[0];
       J[0] += JB[0];
       J[1] += JB[1];
       J[2] += JB[2];
     }
     if (sc.floor_on) {
-      float phi = x[2] - sc.floor_z - sc.Rp;
-      float phihat = phi + dt * fminf(v[2], 0.0f);
+      const float phi = x[2] - sc.floor_z - sc.Rp;
+      const float phihat = phi + dt * fminf(v[2], 0.0f);
       J[2] += sc.s_n * mp / dt * fmaxf(-phihat, 0.0f);
     }
-    // body force folded into the impulse scattered by P2G
+    if (sc.pair_on) {
+      J[0] += P.J[0][p];
+      J[1] += P.J[1][p];
+      J[2] += P.J[2][p];
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) J[a] += mp * sc.g[a] * dt;
-    // side labels for the next substep
-    if (cut >= 0) {
-      const uint32_t bit = 1u << cut;
-      if (((P.s1[p] | P.s2[p]) & bit) == 0u) {
-        int d = side_label(sc, x, v);
-        if (d) {
-          want = 1;
-          entry = ((p - sc.p_begin) << 1) | (d - 1);
-        }
-      }
-    }
-    // stress
+    uint8_t pend = 0;
+    if (cut >= 0 && ((s1 | s2) & (1u << cut)) == 0u) pend = (uint8_t)side_label(sc, x, v);
     float F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
     float Pk[9];
-    bool clamped = piola(F, sc.mu, sc.lam, Pk);
-    const float c = -dt * sc.V0;
+    clamped |= piola(F, sc.mu, sc.lam, Pk);
+    const float cA = -dt * sc.V0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) P.A[k][p] = c * Pk[k];
-    P.J[0][p] = J[0];
-    P.J[1][p] = J[1];
-    P.J[2][p] = J[2];
+    for (int k = 0; k < 9; ++k) S.pA[k][si] = cA * Pk[k];
+    S.pJ[0][si] = J[0];
+    S.pJ[1][si] = J[1];
+    S.pJ[2][si] = J[2];
+    S.pv[0][si] = v[0];
+    S.pv[1][si] = v[1];
+    S.pv[2][si] = v[2];
+    S.pf[0][si] = P.fx[0][p];
+    S.pf[1][si] = P.fx[1][p];
+    S.pf[2][si] = P.fx[2][p];
+    S.ps1[si] = s1;
+    S.ps2[si] = s2;
     P.D[p] = D;
     P.ut[0][p] = uh[0];
     P.ut[1][p] = uh[1];
     P.ut[2][p] = uh[2];
-    if (clamped) atomicOr(&w.scenes[t.x].err, BM_ERRBIT_INVERTED);
+    P.pend[p] = pend;
   }
-  // warp-aggregated append of new labels (order is irrelevant: each entry is
-  // a distinct particle and the commit is an OR of one bit)
-  const unsigned m = __ballot_sync(FULL, want);
-  if (m) {
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int basei = 0;
-    if (lane == leader) basei = atomicAdd(&w.scenes[t.x].list_count, __popc(m));
-    basei = __shfl_sync(FULL, basei, leader);
-    if (want) {
-      const int rank = __popc(m & ((1u << lane) - 1u));
-      P.list[sc.p_begin + basei + rank] = entry;
-    }
-  }
-  // wrench partials of this tile
+  if (clamped) atomicOr(&scm.err, BM_ERRBIT_INVERTED);
   if (sc.has_blade) {
-    __shared__ double sm[32];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      double s = block_sum(wr[k], sm);
-      if (threadIdx.x == 0) w.wpart[(size_t)t.w * 6 + k] = s;
+      const double s = block_sum(wr[k], S.red);
+      if (tid == 0) w.wpart[(size_t)bt.y * 6 + k] = s;
     }
   }
-}
+  __syncthreads();
 
-// --------------------------------------------------------------------------
-// P2G gather + coupling + grid update (one thread per node)
-// --------------------------------------------------------------------------
-struct Acc {
-  float m, mv[3], dp[3];
-};
-
-template <int OX, int OY, int OZ>
-__device__ __forceinline__ void p2g_cell(const PPool &P, int p0, int p1, float inv_dx, Acc &a) {
-  for (int p = p0; p < p1; ++p) {
-    float wx, dwx, wy, dwy, wz, dwz;
-    bs<OX>(P.fx[0][p], wx, dwx);
-    bs<OY>(P.fx[1][p], wy, dwy);
-    bs<OZ>(P.fx[2][p], wz, dwz);
-    const float N = wx * wy * wz;
-    const float g0 = dwx * wy * wz * inv_dx, g1 = wx * dwy * wz * inv_dx, g2 = wx * wy * dwz * inv_dx;
-    const float v0 = P.v[0][p], v1 = P.v[1][p], v2 = P.v[2][p];
-    a.m += N;
-    a.mv[0] += N * v0;
-    a.mv[1] += N * v1;
-    a.mv[2] += N * v2;
-    a.dp[0] += P.A[0][p] * g0 + P.A[1][p] * g1 + P.A[2][p] * g2 + N * P.J[0][p];
-    a.dp[1] += P.A[3][p] * g0 + P.A[4][p] * g1 + P.A[5][p] * g2 + N * P.J[1][p];
-    a.dp[2] += P.A[6][p] * g0 + P.A[7][p] * g1 + P.A[8][p] * g2 + N * P.J[2][p];
-  }
-}
-
-// multi-slot version: particles go to the slot holding their exact code
-__device__ __forceinline__ void p2g_cell_ms(const PPool &P, int p0, int p1, int ox, int oy, int oz,
-                                            float inv_dx, int ns, const uint2 *codes, Acc *acc) {
-  for (int p = p0; p < p1; ++p) {
-    const uint32_t c1 = P.s1[p], c2 = P.s2[p];
-    int a = 0;
-    for (; a < ns; ++a)
-      if (codes[a].x == c1 && codes[a].y == c2) break;
-    if (a == ns) continue;
-    float wx, dwx, wy, dwy, wz, dwz;
-    bs_rt(ox, P.fx[0][p], wx, dwx);
-    bs_rt(oy, P.fx[1][p], wy, dwy);
-    bs_rt(oz, P.fx[2][p], wz, dwz);
-    const float N = wx * wy * wz;
-    const float g0 = dwx * wy * wz * inv_dx, g1 = wx * dwy * wz * inv_dx, g2 = wx * wy * dwz * inv_dx;
-    Acc &A = acc[a];
-    A.m += N;
-    A.mv[0] += N * P.v[0][p];
-    A.mv[1] += N * P.v[1][p];
-    A.mv[2] += N * P.v[2][p];
-    A.dp[0] += P.A[0][p] * g0 + P.A[1][p] * g1 + P.A[2][p] * g2 + N * P.J[0][p];
-    A.dp[1] += P.A[3][p] * g0 + P.A[4][p] * g1 + P.A[5][p] * g2 + N * P.J[1][p];
-    A.dp[2] += P.A[6][p] * g0 + P.A[7][p] * g1 + P.A[8][p] * g2 + N * P.J[2][p];
-  }
-}
-
-__device__ __forceinline__ void node_coords(const DevScene &sc, int li, int &ix, int &iy, int &iz) {
-  ix = li % sc.nn[0];
-  int r = li / sc.nn[0];
-  iy = r % sc.nn[1];
-  iz = r / sc.nn[1];
-}
-
-__device__ __forceinline__ int cell_index(const DevScene &sc, int bx, int by, int bz) {
-  return (bz * sc.nb[1] + by) * sc.nb[0] + bx;
-}
-
-#define BM_FOR_27(BODY)                                               \
-  BODY(0, 0, 0) BODY(1, 0, 0) BODY(2, 0, 0) BODY(0, 1, 0) BODY(1, 1, 0) \
-  BODY(2, 1, 0) BODY(0, 2, 0) BODY(1, 2, 0) BODY(2, 2, 0)               \
-  BODY(0, 0, 1) BODY(1, 0, 1) BODY(2, 0, 1) BODY(0, 1, 1) BODY(1, 1, 1) \
-  BODY(2, 1, 1) BODY(0, 2, 1) BODY(1, 2, 1) BODY(2, 2, 1)               \
-  BODY(0, 0, 2) BODY(1, 0, 2) BODY(2, 0, 2) BODY(0, 1, 2) BODY(1, 1, 2) \
-  BODY(2, 1, 2) BODY(0, 2, 2) BODY(1, 2, 2) BODY(2, 2, 2)
-
-// Eq. 8 on ns logical grids with masses m and states S[a][nc]
-template <int NC>
-__device__ __forceinline__ void couple(int ns, const uint2 *codes, const float *m, float (*S)[NC]) {
-  float M = 0.f;
-  for (int a = 0; a < ns; ++a) M += m[a];
-  if (!(M > 0.f)) return;
-  const float iM = 1.0f / M;
-  float out[BM_MAXS][NC];
-  for (int a = 0; a < ns; ++a) {
+  // ---- phase 1: per (cell, z-offset) sums over the cell's particles ----
+  const int c = tid % BR3, oz = tid / BR3;
+  const int cx = c % BR, cy = (c / BR) % BR, cz = c / (BR * BR);
+  const int n_c = S.cs[c + 1] - S.cs[c];
+  atomicMax(&S.maxcodes, cell_code_count(S.ps1, S.ps2, c, n_c));
+  __syncthreads();
+  const int iters = S.maxcodes;
+  const int total = S.T.total;
+  const int pbase = w.B.poff[bt.y];  // this brick's partial-sum range (negative: pool overflow)
+  const float inv_dx = sc.inv_dx;
+  for (int w0 = 0; w0 < total; w0 += TSCAP) {  // shared-memory windows of tile slots
+    for (int j = tid; j < 7 * TSCAP; j += BT) (&S.acc[0][0])[j] = 0.f;
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+      uint32_t k1 = 0, k2 = 0;
+      const bool has = cell_code(S.ps1, S.ps2, c, n_c, it, k1, k2);
+      float a[9][7];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float acc = 0.f;
-      for (int b = 0; b < ns; ++b) {
-        if (b == a || conflict(codes[a].x, codes[a].y, codes[b].x, codes[b].y)) continue;
-        acc += m[a] * S[b][c] - m[b] * S[a][c];
+      for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int f = 0; f < 7; ++f) a[q][f] = 0.f;
+      if (has) {
+        for (int j = 0; j < n_c; ++j) {
+          const int si = j * BR3 + c;
+          if (S.ps1[si] != k1 || S.ps2[si] != k2) continue;
+          float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
+          const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
+          bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
+          bs<0>(f1, wy[0], dwy[0]); bs<1>(f1, wy[1], dwy[1]); bs<2>(f1, wy[2], dwy[2]);
+          bs_rt(oz, f2, wz, dwz);
+          const float v0 = S.pv[0][si], v1 = S.pv[1][si], v2 = S.pv[2][si];
+          float A[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) A[k] = S.pA[k][si] * inv_dx;
+          const float J0 = S.pJ[0][si], J1 = S.pJ[1][si], J2 = S.pJ[2][si];
+#pragma unroll
+          for (int oy = 0; oy < 3; ++oy) {
+            const float wyz = wy[oy] * wz, dyz = dwy[oy] * wz, wyd = wy[oy] * dwz;
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+              const float N = wx[ox] * wyz;
+              const float g0 = dwx[ox] * wyz, g1 = wx[ox] * dyz, g2 = wx[ox] * wyd;
+              float *q = a[oy * 3 + ox];
+              q[0] += N;
+              q[1] += N * v0;
+              q[2] += N * v1;
+              q[3] += N * v2;
+              q[4] += A[0] * g0 + A[1] * g1 + A[2] * g2 + N * J0;
+              q[5] += A[3] * g0 + A[4] * g1 + A[5] * g2 + N * J1;
+              q[6] += A[6] * g0 + A[7] * g1 + A[8] * g2 + N * J2;
+            }
+          }
+        }
       }
-      out[a][c] = S[a][c] + acc * iM;
-    }
-  }
-  for (int a = 0; a < ns; ++a)
+      // commits: one node offset per phase, so no two threads touch one slot
 #pragma unroll
-    for (int c = 0; c < NC; ++c) S[a][c] = out[a][c];
+      for (int ozp = 0; ozp < 3; ++ozp)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          if (has && oz == ozp) {
+            const int t = ((cz + oz) * TE + (cy + q / 3)) * TE + (cx + q % 3);
+            const int s = tile_slot(w, S.T, tcodes, t, k1, k2) - w0;
+            if (s >= 0 && s < TSCAP) {
+#pragma unroll
+              for (int f = 0; f < 7; ++f) S.acc[f][s] += a[q][f];
+            }
+          }
+          __syncthreads();
+        }
+    }
+    // write this window's partial sums
+    const int wn = min(TSCAP, total - w0);
+    if (pbase >= 0)
+      for (int j = tid; j < wn; j += BT) {
+        w.B.pm[(size_t)pbase + w0 + j] = make_float4(S.acc[0][j], S.acc[1][j], S.acc[2][j], S.acc[3][j]);
+        w.B.pd[(size_t)pbase + w0 + j] = make_float4(S.acc[4][j], S.acc[5][j], S.acc[6][j], 0.f);
+      }
+    __syncthreads();
+  }
+  for (int t = tid; t < TN; t += BT) w.B.plo[(size_t)bt.y * TN + t] = S.T.lo[t];
 }
 
-__global__ void k_p2g(World w, LaunchSet ls) {
+// bricks whose tiles hold node coordinate i along one axis: [first, last]
+__device__ __forceinline__ void covering(int i, int nbr, int &first, int &last) {
+  last = min(i >> 2, nbr - 1);
+  first = max((i - (TE - 1) + (BR - 1)) >> 2, 0);
+  if (i - (TE - 1) < 0) first = 0;
+}
+
+// --------------------------------------------------------------------------
+// k_p2g_node: per node, sum the tile partials of the bricks covering it (in
+// brick order), couple compatible logical grids (Eq. 8), grid update (Eq. 9)
+// --------------------------------------------------------------------------
+__global__ void k_p2g_node(World w, LaunchSet ls) {
   const int4 t = ls.ntiles[blockIdx.x];
   const int i = threadIdx.x;
   if (i >= t.z) return;
   const DevScene &sc = w.scenes[t.x];
-  const PPool &P = w.P;
   const int node = t.y + i;
   const int ns = w.N.slot_cnt[node];
   if (ns == 0) return;
   const int off = w.N.slot_off[node];
   int ix, iy, iz;
   node_coords(sc, node - sc.node_begin, ix, iy, iz);
-  const int *cs = w.N.cell_start + sc.cell_begin;
-  const float inv_dx = sc.inv_dx;
+  int x0, x1, y0, y1, z0, z1;
+  covering(ix, sc.nbr[0], x0, x1);
+  covering(iy, sc.nbr[1], y0, y1);
+  covering(iz, sc.nbr[2], z0, z1);
   if (ns == 1) {
-    Acc a = {0.f, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#define P2G_BODY(OX, OY, OZ)                                                      \
-  {                                                                               \
-    const int bx = ix - OX, by = iy - OY, bz = iz - OZ;                           \
-    if (bx >= 0 && by >= 0 && bz >= 0 && bx < sc.nb[0] && by < sc.nb[1] && bz < sc.nb[2]) { \
-      const int c = cell_index(sc, bx, by, bz);                                   \
-      p2g_cell<OX, OY, OZ>(P, cs[c], cs[c + 1], inv_dx, a);                        \
-    }                                                                             \
-  }
-    BM_FOR_27(P2G_BODY)
-#undef P2G_BODY
+    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f), sd = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int Bz = z0; Bz <= z1; ++Bz)
+      for (int By = y0; By <= y1; ++By)
+        for (int Bx = x0; Bx <= x1; ++Bx) {
+          const int b = sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx;
+          const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
+          const int pb = w.B.poff[b];
+          if (pb < 0) continue;
+          const size_t e = (size_t)pb + w.B.plo[(size_t)b * TN + tt];
+          const float4 a = w.B.pm[e];
+          const float4 d = w.B.pd[e];
+          sm.x += a.x; sm.y += a.y; sm.z += a.z; sm.w += a.w;
+          sd.x += d.x; sd.y += d.y; sd.z += d.z;
+        }
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f), nw = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (a.m > 0.f) {
-      const float im = 1.0f / a.m, imm = 1.0f / (sc.mp * a.m);
-      o = make_float4(a.mv[0] * im, a.mv[1] * im, a.mv[2] * im, sc.mp * a.m);
-      nw = make_float4(o.x + a.dp[0] * imm, o.y + a.dp[1] * imm, o.z + a.dp[2] * imm, 0.f);
+    if (sm.x > 0.f) {
+      const float im = 1.0f / sm.x, imm = 1.0f / (sc.mp * sm.x);
+      o = make_float4(sm.y * im, sm.z * im, sm.w * im, sc.mp * sm.x);
+      nw = make_float4(o.x + sd.x * imm, o.y + sd.y * imm, o.z + sd.z * imm, 0.f);
     }
     w.S.vold[off] = o;
     w.S.vnew[off] = nw;
     return;
   }
-  // several logical grids at this node
   uint2 codes[BM_MAXS];
-  Acc acc[BM_MAXS];
-  for (int a = 0; a < ns; ++a) {
-    codes[a] = w.S.code[off + a];
-    acc[a] = Acc{0.f, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  }
-  for (int oz = 0; oz < 3; ++oz)
-    for (int oy = 0; oy < 3; ++oy)
-      for (int ox = 0; ox < 3; ++ox) {
-        const int bx = ix - ox, by = iy - oy, bz = iz - oz;
-        if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) continue;
-        const int c = cell_index(sc, bx, by, bz);
-        p2g_cell_ms(P, cs[c], cs[c + 1], ox, oy, oz, inv_dx, ns, codes, acc);
-      }
   float m[BM_MAXS];
   float S[BM_MAXS][6];
   for (int a = 0; a < ns; ++a) {
-    m[a] = sc.mp * acc[a].m;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      S[a][c] = sc.mp * acc[a].mv[c];
-      S[a][3 + c] = acc[a].dp[c];
-    }
+    codes[a] = w.S.code[off + a];
+    m[a] = 0.f;
+    for (int c = 0; c < 6; ++c) S[a][c] = 0.f;
+  }
+  for (int Bz = z0; Bz <= z1; ++Bz)
+    for (int By = y0; By <= y1; ++By)
+      for (int Bx = x0; Bx <= x1; ++Bx) {
+        const int b = sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx;
+        const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
+        const int pb = w.B.poff[b];
+        if (pb < 0) continue;
+        const size_t e = (size_t)pb + w.B.plo[(size_t)b * TN + tt];
+        for (int a = 0; a < ns; ++a) {
+          const float4 q = w.B.pm[e + a];
+          const float4 d = w.B.pd[e + a];
+          m[a] += q.x;
+          S[a][0] += q.y; S[a][1] += q.z; S[a][2] += q.w;
+          S[a][3] += d.x; S[a][4] += d.y; S[a][5] += d.z;
+        }
+      }
+  for (int a = 0; a < ns; ++a) {
+    m[a] *= sc.mp;
+    for (int c = 0; c < 3; ++c) S[a][c] *= sc.mp;
   }
   couple<6>(ns, codes, m, S);
   for (int a = 0; a < ns; ++a) {
@@ -558,158 +797,230 @@ __global__ void k_p2g(World w, LaunchSet ls) {
   }
 }
 
-// slot of a particle's code at a node (-1: none)
-__device__ __forceinline__ int find_slot(const World &w, int node, uint32_t s1, uint32_t s2) {
-  const int ns = w.N.slot_cnt[node];
-  const int off = w.N.slot_off[node];
-  if (ns == 1) return off;
-  for (int a = 0; a < ns; ++a) {
-    const uint2 c = w.S.code[off + a];
-    if (c.x == s1 && c.y == s2) return off + a;
-  }
-  return -1;
-}
-
-__device__ __forceinline__ void particle_base(const DevScene &sc, uint32_t b, int &bx, int &by, int &bz) {
-  bx = (int)(b & 1023u);
-  by = (int)((b >> 10) & 1023u);
-  bz = (int)((b >> 20) & 1023u);
-}
-
 // --------------------------------------------------------------------------
-// G2P: Eq. 17 and the position update
+// k_g2p_musl: per particle G2P (Eq. 17) and x update from the brick's tile of
+// grid velocities, then the brick's share of the MUSL re-scatter sum m v^{n+1}
+// N per logical grid, committed in the same fixed phase order as P2G.
 // --------------------------------------------------------------------------
-__global__ void k_g2p(World w, LaunchSet ls) {
-  const int4 t = ls.ptiles[blockIdx.x];
-  const int i = threadIdx.x;
-  if (i >= t.z) return;
-  const DevScene &sc = w.scenes[t.x];
+template <int PPC>
+struct K4S {
+  Tile T;
+  uint2 codes[TSCAP];
+  float tv[7][TSCAP];  // v_old xyz, m, v_new xyz of the tile slots; then the MUSL sums
+  float pf[3][PPC * BR3];
+  float pv[3][PPC * BR3];
+  uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
+  int cs[BR3 + 1];
+  int maxcodes;
+};
+
+template <int PPC>
+__global__ void __launch_bounds__(BT, 4) k_g2p_musl(World w, LaunchSet ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  K4S<PPC> &S = *reinterpret_cast<K4S<PPC> *>(smraw);
+  const int4 bt = ls.btiles[blockIdx.x];
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
   const PPool &P = w.P;
-  const int p = t.y + i;
-  int bx, by, bz;
-  particle_base(sc, P.base[p], bx, by, bz);
-  const uint32_t s1 = P.s1[p], s2 = P.s2[p];
-  float wx[3], wy[3], wz[3], d;
-  const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
-  bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
-  bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
-  bs<0>(f2, wz[0], d); bs<1>(f2, wz[1], d); bs<2>(f2, wz[2], d);
-  float sn[3] = {0.f, 0.f, 0.f}, so[3] = {0.f, 0.f, 0.f};
-  const int nb0 = sc.node_begin;
-#pragma unroll
-  for (int oz = 0; oz < 3; ++oz)
-#pragma unroll
-    for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-      for (int ox = 0; ox < 3; ++ox) {
-        const int node = nb0 + ((bz + oz) * sc.nn[1] + (by + oy)) * sc.nn[0] + (bx + ox);
-        const int a = find_slot(w, node, s1, s2);
-        if (a < 0) continue;
-        const float4 vo = w.S.vold[a];
-        if (!(vo.w > 0.f)) continue;
-        const float4 vn = w.S.vnew[a];
-        const float N = wx[ox] * wy[oy] * wz[oz];
-        sn[0] += N * vn.x;
-        sn[1] += N * vn.y;
-        sn[2] += N * vn.z;
-        so[0] += N * vo.x;
-        so[1] += N * vo.y;
-        so[2] += N * vo.z;
+  const int tid = threadIdx.x;
+  const int lb = bt.y - sc.brick_begin;
+  int c0x, c0y, c0z;
+  brick_coords(sc, lb, c0x, c0y, c0z);
+  const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
+  for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
+  if (tid == 0) S.maxcodes = 0;
+  tile_load(w, sc, c0x, c0y, c0z, S.T);
+  const int total = S.T.total;
+  const bool in_smem = total <= TSCAP;  // otherwise G2P reads the pool slots directly
+  const uint2 *tcodes = in_smem ? S.codes : nullptr;
+  if (in_smem) {
+    for (int t = tid; t < TN; t += BT) {
+      const int n = S.T.cnt[t], lo = S.T.lo[t], g = S.T.goff[t];
+      for (int a = 0; a < n; ++a) {
+        if (n > 1) S.codes[lo + a] = w.S.code[g + a];
+        const float4 o = w.S.vold[g + a], nv = w.S.vnew[g + a];
+        S.tv[0][lo + a] = o.x; S.tv[1][lo + a] = o.y; S.tv[2][lo + a] = o.z; S.tv[3][lo + a] = o.w;
+        S.tv[4][lo + a] = nv.x; S.tv[5][lo + a] = nv.y; S.tv[6][lo + a] = nv.z;
       }
+    }
+  }
+  __syncthreads();
+  // ---- phase 0: G2P ----
   const float beta = sc.beta, dt = sc.dt;
   bool bad = false;
+  for (int i = tid; i < bt.w; i += BT) {
+    const int p = bt.z + i;
+    int bx, by, bz;
+    particle_base(P.base[p], bx, by, bz);
+    const int lx = bx - c0x, ly = by - c0y, lz = bz - c0z;
+    const int c = (lz * BR + ly) * BR + lx;
+    const int si = (i - S.cs[c]) * BR3 + c;
+    const uint32_t s1 = P.s1[p], s2 = P.s2[p];
+    const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
+    float wx[3], wy[3], wz[3], d;
+    bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
+    bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
+    bs<0>(f2, wz[0], d); bs<1>(f2, wz[1], d); bs<2>(f2, wz[2], d);
+    float sn[3] = {0.f, 0.f, 0.f}, so[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float vv = beta * (P.v[a][p] - so[a]) + sn[a];
-    const float xx = P.x[a][p] + dt * sn[a];
-    P.v[a][p] = vv;
-    P.x[a][p] = xx;
-    bad |= !isfinite(vv) || !isfinite(xx);
+    for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+          const int t = ((lz + oz) * TE + (ly + oy)) * TE + (lx + ox);
+          const int s = tile_slot(w, S.T, tcodes, t, s1, s2);
+          if (s < 0) continue;
+          float4 vo, vn;
+          if (in_smem) {
+            vo = make_float4(S.tv[0][s], S.tv[1][s], S.tv[2][s], S.tv[3][s]);
+            vn = make_float4(S.tv[4][s], S.tv[5][s], S.tv[6][s], 0.f);
+          } else {
+            const int g = S.T.goff[t] + s - S.T.lo[t];
+            vo = w.S.vold[g];
+            vn = w.S.vnew[g];
+          }
+          if (!(vo.w > 0.f)) continue;
+          const float N = wx[ox] * wy[oy] * wz[oz];
+          sn[0] += N * vn.x;
+          sn[1] += N * vn.y;
+          sn[2] += N * vn.z;
+          so[0] += N * vo.x;
+          so[1] += N * vo.y;
+          so[2] += N * vo.z;
+        }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float vv = beta * (P.v[a][p] - so[a]) + sn[a];
+      const float xx = P.x[a][p] + dt * sn[a];
+      P.v[a][p] = vv;
+      P.x[a][p] = xx;
+      S.pv[a][si] = vv;
+      bad |= !isfinite(vv) || !isfinite(xx);
+    }
+    S.pf[0][si] = f0;
+    S.pf[1][si] = f1;
+    S.pf[2][si] = f2;
+    S.ps1[si] = s1;
+    S.ps2[si] = s2;
   }
-  if (bad) atomicOr(&w.scenes[t.x].err, BM_ERRBIT_NONFINITE);
+  if (bad) atomicOr(&scm.err, BM_ERRBIT_NONFINITE);
+  // ---- phase 1: MUSL sums per (cell, z-offset), in windows of tile slots ----
+  const int c = tid % BR3, oz = tid / BR3;
+  const int cx = c % BR, cy = (c / BR) % BR, cz = c / (BR * BR);
+  const int n_c = S.cs[c + 1] - S.cs[c];
+  __syncthreads();
+  atomicMax(&S.maxcodes, cell_code_count(S.ps1, S.ps2, c, n_c));
+  const int pbase = w.B.poff[bt.y];
+  for (int w0 = 0; w0 < total; w0 += TSCAP) {
+    __syncthreads();
+    for (int j = tid; j < 3 * TSCAP; j += BT) (&S.tv[0][0])[j] = 0.f;
+    __syncthreads();
+    const int iters = S.maxcodes;
+    for (int it = 0; it < iters; ++it) {
+      uint32_t k1 = 0, k2 = 0;
+      const bool has = cell_code(S.ps1, S.ps2, c, n_c, it, k1, k2);
+      float a[9][3];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) a[q][0] = a[q][1] = a[q][2] = 0.f;
+      if (has) {
+        for (int j = 0; j < n_c; ++j) {
+          const int si = j * BR3 + c;
+          if (S.ps1[si] != k1 || S.ps2[si] != k2) continue;
+          float wx[3], wy[3], wz, d;
+          const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
+          bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
+          bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
+          bs_rt(oz, f2, wz, d);
+          const float v0 = S.pv[0][si], v1 = S.pv[1][si], v2 = S.pv[2][si];
+#pragma unroll
+          for (int oy = 0; oy < 3; ++oy) {
+            const float wyz = wy[oy] * wz;
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+              const float N = wx[ox] * wyz;
+              a[oy * 3 + ox][0] += N * v0;
+              a[oy * 3 + ox][1] += N * v1;
+              a[oy * 3 + ox][2] += N * v2;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int ozp = 0; ozp < 3; ++ozp)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          if (has && oz == ozp) {
+            const int t = ((cz + oz) * TE + (cy + q / 3)) * TE + (cx + q % 3);
+            const int s = tile_slot(w, S.T, tcodes, t, k1, k2) - w0;
+            if (s >= 0 && s < TSCAP) {
+              S.tv[0][s] += a[q][0];
+              S.tv[1][s] += a[q][1];
+              S.tv[2][s] += a[q][2];
+            }
+          }
+          __syncthreads();
+        }
+    }
+    const int wn = min(TSCAP, total - w0);
+    if (pbase >= 0)
+      for (int j = tid; j < wn; j += BT)
+        w.B.pm[(size_t)pbase + w0 + j] = make_float4(S.tv[0][j], S.tv[1][j], S.tv[2][j], 0.f);
+  }
 }
 
 // --------------------------------------------------------------------------
-// MUSL re-scatter with coupling -> v*
+// k_musl_node: per node, MUSL sums of the covering bricks, coupling, v*
 // --------------------------------------------------------------------------
-template <int OX, int OY, int OZ>
-__device__ __forceinline__ void musl_cell(const PPool &P, int p0, int p1, float &m, float mv[3]) {
-  for (int p = p0; p < p1; ++p) {
-    float wx, wy, wz, d;
-    bs<OX>(P.fx[0][p], wx, d);
-    bs<OY>(P.fx[1][p], wy, d);
-    bs<OZ>(P.fx[2][p], wz, d);
-    const float N = wx * wy * wz;
-    m += N;
-    mv[0] += N * P.v[0][p];
-    mv[1] += N * P.v[1][p];
-    mv[2] += N * P.v[2][p];
-  }
-}
-
-__global__ void k_musl(World w, LaunchSet ls) {
+__global__ void k_musl_node(World w, LaunchSet ls) {
   const int4 t = ls.ntiles[blockIdx.x];
   const int i = threadIdx.x;
   if (i >= t.z) return;
   const DevScene &sc = w.scenes[t.x];
-  const PPool &P = w.P;
   const int node = t.y + i;
   const int ns = w.N.slot_cnt[node];
   if (ns == 0) return;
   const int off = w.N.slot_off[node];
   int ix, iy, iz;
   node_coords(sc, node - sc.node_begin, ix, iy, iz);
-  const int *cs = w.N.cell_start + sc.cell_begin;
+  int x0, x1, y0, y1, z0, z1;
+  covering(ix, sc.nbr[0], x0, x1);
+  covering(iy, sc.nbr[1], y0, y1);
+  covering(iz, sc.nbr[2], z0, z1);
+  float S[BM_MAXS][3];
+  for (int a = 0; a < ns; ++a) S[a][0] = S[a][1] = S[a][2] = 0.f;
+  for (int Bz = z0; Bz <= z1; ++Bz)
+    for (int By = y0; By <= y1; ++By)
+      for (int Bx = x0; Bx <= x1; ++Bx) {
+        const int b = sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx;
+        const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
+        const int pb = w.B.poff[b];
+        if (pb < 0) continue;
+        const size_t e = (size_t)pb + w.B.plo[(size_t)b * TN + tt];
+        for (int a = 0; a < ns; ++a) {
+          const float4 q = w.B.pm[e + a];
+          S[a][0] += q.x;
+          S[a][1] += q.y;
+          S[a][2] += q.z;
+        }
+      }
   if (ns == 1) {
-    float m = 0.f, mv[3] = {0.f, 0.f, 0.f};
-#define MUSL_BODY(OX, OY, OZ)                                                     \
-  {                                                                               \
-    const int bx = ix - OX, by = iy - OY, bz = iz - OZ;                           \
-    if (bx >= 0 && by >= 0 && bz >= 0 && bx < sc.nb[0] && by < sc.nb[1] && bz < sc.nb[2]) { \
-      const int c = cell_index(sc, bx, by, bz);                                   \
-      musl_cell<OX, OY, OZ>(P, cs[c], cs[c + 1], m, mv);                           \
-    }                                                                             \
-  }
-    BM_FOR_27(MUSL_BODY)
-#undef MUSL_BODY
+    const float m = w.S.vold[off].w;
     float4 vs = make_float4(0.f, 0.f, 0.f, 0.f);
     if (m > 0.f) {
-      const float im = 1.0f / m;
-      vs = make_float4(mv[0] * im, mv[1] * im, mv[2] * im, 0.f);
+      const float im = sc.mp / m;
+      vs = make_float4(S[0][0] * im, S[0][1] * im, S[0][2] * im, 0.f);
     }
     w.S.vstar[off] = vs;
     return;
   }
   uint2 codes[BM_MAXS];
   float mass[BM_MAXS];
-  float S[BM_MAXS][3];
   for (int a = 0; a < ns; ++a) {
     codes[a] = w.S.code[off + a];
     mass[a] = w.S.vold[off + a].w;
-    S[a][0] = S[a][1] = S[a][2] = 0.f;
+    for (int c = 0; c < 3; ++c) S[a][c] *= sc.mp;
   }
-  for (int oz = 0; oz < 3; ++oz)
-    for (int oy = 0; oy < 3; ++oy)
-      for (int ox = 0; ox < 3; ++ox) {
-        const int bx = ix - ox, by = iy - oy, bz = iz - oz;
-        if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) continue;
-        const int c = cell_index(sc, bx, by, bz);
-        for (int p = cs[c]; p < cs[c + 1]; ++p) {
-          const uint32_t c1 = P.s1[p], c2 = P.s2[p];
-          int a = 0;
-          for (; a < ns; ++a)
-            if (codes[a].x == c1 && codes[a].y == c2) break;
-          if (a == ns) continue;
-          float wx, wy, wz, d;
-          bs_rt(ox, P.fx[0][p], wx, d);
-          bs_rt(oy, P.fx[1][p], wy, d);
-          bs_rt(oz, P.fx[2][p], wz, d);
-          const float N = wx * wy * wz * sc.mp;
-          S[a][0] += N * P.v[0][p];
-          S[a][1] += N * P.v[1][p];
-          S[a][2] += N * P.v[2][p];
-        }
-      }
   couple<3>(ns, codes, mass, S);
   for (int a = 0; a < ns; ++a) {
     float4 vs = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -722,44 +1033,320 @@ __global__ void k_musl(World w, LaunchSet ls) {
 }
 
 // --------------------------------------------------------------------------
-// deformation gradient update
+// k_fupd: F += dt sum_i v*_i (x) grad0 N_ip from the brick's tile of v*, and
+// commit the side labels assigned this substep (they act from the next one)
 // --------------------------------------------------------------------------
-__global__ void k_fupd(World w, LaunchSet ls) {
-  const int4 t = ls.ptiles[blockIdx.x];
-  const int i = threadIdx.x;
-  if (i >= t.z) return;
-  const DevScene &sc = w.scenes[t.x];
+struct K1S {
+  Tile T;
+  uint2 codes[TSCAP];
+  float tvs[3][TSCAP];
+  int any;
+};
+
+__global__ void __launch_bounds__(BT, 3) k_fupd(World w, LaunchSet ls) {
+  __shared__ K1S S;
+  const int4 bt = ls.btiles[blockIdx.x];
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
   const PPool &P = w.P;
-  const int p = t.y + i;
-  int bx, by, bz;
-  particle_base(sc, P.base[p], bx, by, bz);
-  const uint32_t s1 = P.s1[p], s2 = P.s2[p];
-  float wx[3], wy[3], wz[3], gx[3], gy[3], gz[3];
-  const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
-  bs<0>(f0, wx[0], gx[0]); bs<1>(f0, wx[1], gx[1]); bs<2>(f0, wx[2], gx[2]);
-  bs<0>(f1, wy[0], gy[0]); bs<1>(f1, wy[1], gy[1]); bs<2>(f1, wy[2], gy[2]);
-  bs<0>(f2, wz[0], gz[0]); bs<1>(f2, wz[1], gz[1]); bs<2>(f2, wz[2], gz[2]);
-  float G[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int nb0 = sc.node_begin;
-#pragma unroll
-  for (int oz = 0; oz < 3; ++oz)
-#pragma unroll
-    for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-      for (int ox = 0; ox < 3; ++ox) {
-        const int node = nb0 + ((bz + oz) * sc.nn[1] + (by + oy)) * sc.nn[0] + (bx + ox);
-        const int a = find_slot(w, node, s1, s2);
-        if (a < 0) continue;
-        const float4 vs = w.S.vstar[a];
-        const float g0 = gx[ox] * wy[oy] * wz[oz], g1 = wx[ox] * gy[oy] * wz[oz],
-                    g2 = wx[ox] * wy[oy] * gz[oz];
-        G[0] += vs.x * g0; G[1] += vs.x * g1; G[2] += vs.x * g2;
-        G[3] += vs.y * g0; G[4] += vs.y * g1; G[5] += vs.y * g2;
-        G[6] += vs.z * g0; G[7] += vs.z * g1; G[8] += vs.z * g2;
+  const int tid = threadIdx.x;
+  const int lb = bt.y - sc.brick_begin;
+  int c0x, c0y, c0z;
+  brick_coords(sc, lb, c0x, c0y, c0z);
+  if (tid == 0) S.any = 0;
+  tile_load(w, sc, c0x, c0y, c0z, S.T);
+  const bool in_smem = S.T.total <= TSCAP;
+  const uint2 *tcodes = in_smem ? S.codes : nullptr;
+  if (in_smem) {
+    for (int t = tid; t < TN; t += BT) {
+      const int n = S.T.cnt[t], lo = S.T.lo[t], g = S.T.goff[t];
+      for (int a = 0; a < n; ++a) {
+        if (n > 1) S.codes[lo + a] = w.S.code[g + a];
+        const float4 v = w.S.vstar[g + a];
+        S.tvs[0][lo + a] = v.x;
+        S.tvs[1][lo + a] = v.y;
+        S.tvs[2][lo + a] = v.z;
       }
+    }
+  }
+  __syncthreads();
   const float c = sc.dt * sc.inv_dx;
+  const int cut = sc.cut;
+  bool any = false;
+  for (int i = tid; i < bt.w; i += BT) {
+    const int p = bt.z + i;
+    int bx, by, bz;
+    particle_base(P.base[p], bx, by, bz);
+    const int lx = bx - c0x, ly = by - c0y, lz = bz - c0z;
+    const uint32_t s1 = P.s1[p], s2 = P.s2[p];
+    const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
+    float wx[3], wy[3], wz[3], gx[3], gy[3], gz[3];
+    bs<0>(f0, wx[0], gx[0]); bs<1>(f0, wx[1], gx[1]); bs<2>(f0, wx[2], gx[2]);
+    bs<0>(f1, wy[0], gy[0]); bs<1>(f1, wy[1], gy[1]); bs<2>(f1, wy[2], gy[2]);
+    bs<0>(f2, wz[0], gz[0]); bs<1>(f2, wz[1], gz[1]); bs<2>(f2, wz[2], gz[2]);
+    float G[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < 9; ++k) P.F[k][p] += c * G[k];
+    for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+          const int t = ((lz + oz) * TE + (ly + oy)) * TE + (lx + ox);
+          const int s = tile_slot(w, S.T, tcodes, t, s1, s2);
+          if (s < 0) continue;
+          float v0, v1, v2;
+          if (in_smem) {
+            v0 = S.tvs[0][s];
+            v1 = S.tvs[1][s];
+            v2 = S.tvs[2][s];
+          } else {
+            const float4 v = w.S.vstar[S.T.goff[t] + s - S.T.lo[t]];
+            v0 = v.x;
+            v1 = v.y;
+            v2 = v.z;
+          }
+          const float g0 = gx[ox] * wy[oy] * wz[oz], g1 = wx[ox] * gy[oy] * wz[oz],
+                      g2 = wx[ox] * wy[oy] * gz[oz];
+          G[0] += v0 * g0; G[1] += v0 * g1; G[2] += v0 * g2;
+          G[3] += v1 * g0; G[4] += v1 * g1; G[5] += v1 * g2;
+          G[6] += v2 * g0; G[7] += v2 * g1; G[8] += v2 * g2;
+        }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P.F[k][p] += c * G[k];
+    const uint8_t pend = P.pend[p];
+    if (pend && cut >= 0) {
+      if (pend == 1) P.s1[p] = s1 | (1u << cut);
+      else P.s2[p] = s2 | (1u << cut);
+      any = true;
+    }
+  }
+  if (any) S.any = 1;
+  __syncthreads();
+  if (tid == 0 && S.any) atomicOr(&scm.label_pending, 1);
+}
+
+// --------------------------------------------------------------------------
+// Material-material contact (Eq. 10-13).  Particles are binned by their
+// current-configuration cell into a world-wide hash; the cell edge is
+// 2 R_p + 2 dt max|v| + R_p/2, so every pair that can overlap this substep
+// (distance < 2 R_p + dt |v_p - v_q|) lies in neighbouring cells.  Each
+// bucket lists its particles by pool index, so every particle meets its
+// neighbours in a fixed order.  A pair is always evaluated in canonical
+// (lower, higher) pool-index order by both of its particles, so the two
+// impulses are exact negatives; the lower index owns the pair's tangential
+// history (double-buffered by substep parity).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ long long pack_cell(int cx, int cy, int cz) {
+  return ((long long)(cx + (1 << 20)) << 42) | ((long long)(cy + (1 << 20)) << 21) |
+         (long long)(cz + (1 << 20));
+}
+
+__device__ __forceinline__ int hash_cell(int scene, int cx, int cy, int cz, int nb) {
+  const unsigned h = ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^
+                     ((unsigned)cz * 83492791u) ^ ((unsigned)scene * 2654435761u);
+  return (int)(h & (unsigned)(nb - 1));
+}
+
+__global__ void k_pair_clear(World w, LaunchSet ls) {
+  const int nb = w.H.n_buckets;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nb; i += gridDim.x * blockDim.x) {
+    w.H.bucket_start[i] = 0;
+    if (i < nb) w.H.bucket_fill[i] = 0;
+    if (i < ls.n_scenes) w.scenes[ls.scene_ids[i]].pair_vmax_bits = 0;
+  }
+}
+
+// per scene: largest particle speed (non-negative floats order like their bits)
+__global__ void k_pair_vmax(World w, LaunchSet ls) {
+  const int4 bt = ls.btiles[blockIdx.x];
+  DevScene &sc = w.scenes[bt.x];
+  if (!sc.pair_on) return;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
+    const int p = bt.z + i;
+    const float a = w.P.v[0][p], b = w.P.v[1][p], c = w.P.v[2][p];
+    m = fmaxf(m, sqrtf(a * a + b * b + c * c));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(FULL, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&sc.pair_vmax_bits, __float_as_int(m));
+}
+
+__device__ __forceinline__ float pair_inv_h(const DevScene &sc) {
+  const float vmax = __int_as_float(sc.pair_vmax_bits);
+  return 1.0f / (2.5f * sc.Rp + 2.0f * sc.dt * vmax);
+}
+
+__global__ void k_pair_hash(World w, LaunchSet ls) {
+  const int4 bt = ls.btiles[blockIdx.x];
+  const DevScene &sc = w.scenes[bt.x];
+  if (!sc.pair_on) return;
+  const PPool &P = w.P;
+  const float ih = pair_inv_h(sc);
+  for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
+    const int p = bt.z + i;
+    const int cx = (int)floorf(P.x[0][p] * ih);
+    const int cy = (int)floorf(P.x[1][p] * ih);
+    const int cz = (int)floorf(P.x[2][p] * ih);
+    const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
+    P.hkey[p] = b;
+    P.hcell[p] = pack_cell(cx, cy, cz);
+    atomicAdd(&w.H.bucket_start[b], 1);
+  }
+}
+
+__global__ void k_scan_local(World w) {
+  __shared__ int sm[33];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = i < w.H.n_buckets ? w.H.bucket_start[i] : 0;
+  int total;
+  const int ex = block_excl_scan(v, sm, total);
+  if (i < w.H.n_buckets) w.H.bucket_start[i] = ex;
+  if (threadIdx.x == 0) w.H.block_sum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_top(World w, int nblocks) {
+  __shared__ int sm[33];
+  int carry = 0;
+  for (int base = 0; base < nblocks; base += blockDim.x) {
+    const int j = base + threadIdx.x;
+    const int v = j < nblocks ? w.H.block_sum[j] : 0;
+    int total;
+    const int ex = block_excl_scan(v, sm, total);
+    if (j < nblocks) w.H.block_sum[j] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) w.H.bucket_start[w.H.n_buckets] = carry;
+}
+
+__global__ void k_scan_add(World w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < w.H.n_buckets) w.H.bucket_start[i] += w.H.block_sum[blockIdx.x];
+}
+
+__global__ void k_pair_fill(World w, LaunchSet ls) {
+  const int4 bt = ls.btiles[blockIdx.x];
+  const DevScene &sc = w.scenes[bt.x];
+  if (!sc.pair_on) return;
+  for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
+    const int p = bt.z + i;
+    const int b = w.P.hkey[p];
+    w.P.horder[w.H.bucket_start[b] + atomicAdd(&w.H.bucket_fill[b], 1)] = p;
+  }
+}
+
+// order each bucket by pool index (buckets are short)
+__global__ void k_pair_sort(World w) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < w.H.n_buckets; b += gridDim.x * blockDim.x) {
+    const int s0 = w.H.bucket_start[b], s1 = w.H.bucket_start[b + 1];
+    for (int i = s0 + 1; i < s1; ++i) {
+      const int key = w.P.horder[i];
+      int j = i - 1;
+      while (j >= s0 && w.P.horder[j] > key) {
+        w.P.horder[j + 1] = w.P.horder[j];
+        --j;
+      }
+      w.P.horder[j + 1] = key;
+    }
+  }
+}
+
+__global__ void k_pair(World w, LaunchSet ls) {
+  const int4 bt = ls.btiles[blockIdx.x];
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
+  if (!sc.pair_on) return;
+  const PPool &P = w.P;
+  const int rb = (int)(sc.step & 1), wb = rb ^ 1;
+  const float dt = sc.dt, R2 = 2.0f * sc.Rp;
+  const float meff = sc.mp * sc.mp / (sc.mp + sc.mp);
+  const int pend = sc.p_begin + sc.n_p;
+  const float ih = pair_inv_h(sc);
+  bool over = false;
+  for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
+    const int p = bt.z + i;
+    const float xp[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
+    const float vp[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
+    const uint32_t a1 = P.s1[p], a2 = P.s2[p];
+    int bpx, bpy, bpz;
+    particle_base(P.base[p], bpx, bpy, bpz);
+    const int cx = (int)floorf(xp[0] * ih);
+    const int cy = (int)floorf(xp[1] * ih);
+    const int cz = (int)floorf(xp[2] * ih);
+    float J[3] = {0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const long long key = pack_cell(cx + dx, cy + dy, cz + dz);
+          const int b = hash_cell(bt.x, cx + dx, cy + dy, cz + dz, w.H.n_buckets);
+          const int e1 = w.H.bucket_start[b + 1];
+          for (int k = w.H.bucket_start[b]; k < e1; ++k) {
+            const int q = P.horder[k];
+            if (q == p || q < sc.p_begin || q >= pend || P.hcell[q] != key) continue;
+            const int lo = p < q ? p : q, hi = p < q ? q : p;
+            const float xl[3] = {P.x[0][lo], P.x[1][lo], P.x[2][lo]};
+            const float xh[3] = {P.x[0][hi], P.x[1][hi], P.x[2][hi]};
+            const float vl[3] = {P.v[0][lo], P.v[1][lo], P.v[2][lo]};
+            const float vh[3] = {P.v[0][hi], P.v[1][hi], P.v[2][hi]};
+            const float d[3] = {xl[0] - xh[0], xl[1] - xh[1], xl[2] - xh[2]};
+            const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (!(dist > 0.f)) continue;
+            const float id = 1.0f / dist;
+            const float n[3] = {d[0] * id, d[1] * id, d[2] * id};
+            const float vr[3] = {vl[0] - vh[0], vl[1] - vh[1], vl[2] - vh[2]};
+            const float vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
+            const float dhat = R2 - (dist + fminf(dt * vn, 0.0f));  // Eq. 10
+            if (!(dhat > 0.f)) continue;
+            int bqx, bqy, bqz;
+            particle_base(P.base[q], bqx, bqy, bqz);
+            const bool share = abs(bpx - bqx) <= 2 && abs(bpy - bqy) <= 2 && abs(bpz - bqz) <= 2;
+            if (share && !conflict(a1, a2, P.s1[q], P.s2[q])) continue;  // self-contact exclusion
+            const float fn = sc.s_n * meff / (dt * dt) * dhat;            // Eq. 11
+            float uh[3] = {0.f, 0.f, 0.f};
+            for (int h = 0; h < BM_HIST; ++h) {
+              const int pt = P.hist_partner[rb][(size_t)lo * BM_HIST + h];
+              if (pt < 0) break;
+              if (pt == hi) {
+                const float *u = P.hist_u[rb] + ((size_t)lo * BM_HIST + h) * 3;
+                uh[0] = u[0];
+                uh[1] = u[1];
+                uh[2] = u[2];
+                break;
+              }
+            }
+            float ft[3], un[3];
+            friction(uh, n, vr, fn, meff, dt, sc.gamma_k, sc.gamma_c, sc.pair_mu_s, sc.pair_mu_d, ft, un);
+            const float Jv[3] = {dt * (fn * n[0] + ft[0]), dt * (fn * n[1] + ft[1]),
+                                 dt * (fn * n[2] + ft[2])};
+            if (p == lo) {  // Eq. 13: +J on the lower index, -J on the higher
+              J[0] += Jv[0];
+              J[1] += Jv[1];
+              J[2] += Jv[2];
+              if (cnt < BM_HIST) {
+                P.hist_partner[wb][(size_t)p * BM_HIST + cnt] = hi;
+                float *u = P.hist_u[wb] + ((size_t)p * BM_HIST + cnt) * 3;
+                u[0] = un[0];
+                u[1] = un[1];
+                u[2] = un[2];
+                ++cnt;
+              } else {
+                over = true;
+              }
+            } else {
+              J[0] -= Jv[0];
+              J[1] -= Jv[1];
+              J[2] -= Jv[2];
+            }
+          }
+        }
+    if (cnt < BM_HIST) P.hist_partner[wb][(size_t)p * BM_HIST + cnt] = -1;
+    P.J[0][p] = J[0];
+    P.J[1][p] = J[1];
+    P.J[2][p] = J[2];
+  }
+  if (over) atomicOr(&scm.err, BM_ERRBIT_CONTACT_OVERFLOW);
 }
 
 // --------------------------------------------------------------------------
@@ -895,31 +1482,20 @@ __global__ void k_tool(World w, LaunchSet ls) {
   const int sid = ls.scene_ids[blockIdx.x];
   DevScene &sc = w.scenes[sid];
   __shared__ double sm[32];
-  // 1. commit the side labels assigned this substep
-  const int cnt = sc.list_count;
-  const int cut = sc.cut;
-  if (cut >= 0) {
-    const uint32_t bit = 1u << cut;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const int e = w.P.list[sc.p_begin + i];
-      const int p = sc.p_begin + (e >> 1);
-      if (e & 1) w.P.s2[p] |= bit;
-      else w.P.s1[p] |= bit;
-    }
-  }
-  // 2. reduce this substep's wrench partials (fixed order)
+  // reduce this substep's per-brick wrench partials in brick order
   double W[6];
   for (int k = 0; k < 6; ++k) {
     double acc = 0.0;
     if (sc.has_blade)
-      for (int j = threadIdx.x; j < sc.n_ptile; j += blockDim.x)
-        acc += w.wpart[(size_t)(sc.ptile_begin + j) * 6 + k];
+      for (int j = threadIdx.x; j < sc.n_brick; j += blockDim.x)
+        acc += w.wpart[(size_t)(sc.brick_begin + j) * 6 + k];
     W[k] = block_sum(acc, sm);
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  sc.need_rebuild = cnt > 0 ? 1 : 0;
-  sc.list_count = 0;
+  // labels committed by k_fupd this substep -> rebuild the slot table
+  sc.need_rebuild = sc.label_pending ? 1 : 0;
+  sc.label_pending = 0;
   if (sc.has_blade) {
     const long long st = sc.step;
     if (st < sc.hist_cap)
@@ -974,34 +1550,7 @@ __global__ void k_tool(World w, LaunchSet ls) {
 // --------------------------------------------------------------------------
 // logical-grid slot table (rebuilt after label changes)
 // --------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long ckey(uint2 c) {
-  return ((unsigned long long)c.y << 32) | c.x;
-}
 
-__device__ __forceinline__ int block_excl_scan(int v, int *sm, int &total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += y;
-  }
-  __syncthreads();
-  if (lane == 31) sm[wid] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int i = 0; i < nw; ++i) {
-      int t = sm[i];
-      sm[i] = acc;
-      acc += t;
-    }
-    sm[nw] = acc;
-  }
-  __syncthreads();
-  total = sm[nw];
-  return x - v + sm[wid];
-}
 
 __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   const int4 t = ls.ntiles[blockIdx.x];
@@ -1047,6 +1596,27 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   if (threadIdx.x == 0) w.N.tile_sum[t.w] = total;
 }
 
+// slots in each brick's node tile (after the per-node counts are final)
+__global__ void k_brick_tot(World w, LaunchSet ls, int force) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ls.n_btiles) return;
+  const int4 bt = ls.btiles[i];
+  const DevScene &sc = w.scenes[bt.x];
+  if (!force && !sc.need_rebuild) return;
+  int c0x, c0y, c0z;
+  brick_coords(sc, bt.y - sc.brick_begin, c0x, c0y, c0z);
+  int tot = 0;
+  for (int tz = 0; tz < TE; ++tz)
+    for (int ty = 0; ty < TE; ++ty)
+      for (int tx = 0; tx < TE; ++tx) {
+        const int nx = c0x + tx, ny = c0y + ty, nz = c0z + tz;
+        if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2])
+          tot += w.N.slot_cnt[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
+      }
+  w.B.ptot[bt.y] = tot;
+}
+
+// per scene: slot offsets of the node tiles, and partial-sum ranges of the bricks
 __global__ void k_slot_scan(World w, LaunchSet ls, int force) {
   DevScene &sc = w.scenes[ls.scene_ids[blockIdx.x]];
   if (!force && !sc.need_rebuild) return;
@@ -1061,6 +1631,22 @@ __global__ void k_slot_scan(World w, LaunchSet ls, int force) {
     carry += total;
     __syncthreads();
   }
+  int pcarry = 0;
+  bool pover = false;
+  for (int base = 0; base < sc.n_brick; base += blockDim.x) {
+    const int j = base + threadIdx.x;
+    const int v = j < sc.n_brick ? w.B.ptot[sc.brick_begin + j] : 0;
+    int total;
+    const int ex = block_excl_scan(v, sm, total);
+    if (j < sc.n_brick) {
+      const bool fits = pcarry + ex + v <= sc.ppool_cap;
+      w.B.poff[sc.brick_begin + j] = fits ? sc.ppool_begin + pcarry + ex : -1;
+      pover |= !fits;
+    }
+    pcarry += total;
+    __syncthreads();
+  }
+  if (pover) atomicOr(&sc.err, BM_ERRBIT_SLOT_OVERFLOW);
   if (threadIdx.x == 0) {
     sc.n_slots = carry;
     if (carry > sc.slot_cap) atomicOr(&sc.err, BM_ERRBIT_SLOT_OVERFLOW);
@@ -1169,7 +1755,10 @@ cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t 
 }
 
 const char *const bm_kernel_names[BM_NUM_KERNELS] = {
-    "k_pre", "k_p2g", "k_g2p", "k_musl", "k_fupd", "k_tool", "k_slot_count", "k_slot_scan", "k_slot_fill"};
+    "k_p2g_brick", "k_p2g_node", "k_g2p_musl", "k_musl_node", "k_fupd",
+    "k_tool", "k_slot_count", "k_slot_scan", "k_slot_fill", "k_brick_tot",
+    "k_pair_clear", "k_pair_hash", "k_scan_local", "k_scan_top", "k_scan_add", "k_pair_fill",
+    "k_pair_sort", "k_pair"};
 
 // ev (optional): 2 * BM_NUM_KERNELS events recorded around each launch
 static inline void rec(cudaEvent_t *ev, int k, int after, cudaStream_t st) {
@@ -1182,6 +1771,9 @@ static cudaError_t launch_rebuild(const World &w, const LaunchSet &ls, cudaStrea
   rec(ev, 6, 0, st);
   k_slot_count<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
   rec(ev, 6, 1, st);
+  rec(ev, 9, 0, st);
+  k_brick_tot<<<(ls.n_btiles + 127) / 128, 128, 0, st>>>(w, ls, force);
+  rec(ev, 9, 1, st);
   rec(ev, 7, 0, st);
   k_slot_scan<<<ls.n_scenes, 256, 0, st>>>(w, ls, force);
   rec(ev, 7, 1, st);
@@ -1195,23 +1787,83 @@ cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t 
   return launch_rebuild(w, ls, st, force, nullptr);
 }
 
-cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
-  if (ls.n_ptiles == 0) return cudaSuccess;
+template <int PPC>
+static cudaError_t set_smem_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(K2S<PPC>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_g2p_musl<PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(K4S<PPC>));
+}
+
+cudaError_t bm_kernels_init() {
+  static cudaError_t status = cudaErrorNotReady;
+  static int device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (device == dev && status == cudaSuccess) return status;
+  e = set_smem_attrs<8>();
+  if (e == cudaSuccess) e = set_smem_attrs<16>();
+  status = e;
+  device = dev;
+  return e;
+}
+
+template <int PPC>
+static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   rec(ev, 0, 0, st);
-  k_pre<<<ls.n_ptiles, ls.ptile_size, 0, st>>>(w, ls);
+  k_p2g_brick<PPC><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
   rec(ev, 0, 1, st);
   rec(ev, 1, 0, st);
-  k_p2g<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
+  k_p2g_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 1, 1, st);
   rec(ev, 2, 0, st);
-  k_g2p<<<ls.n_ptiles, ls.ptile_size, 0, st>>>(w, ls);
+  k_g2p_musl<PPC><<<ls.n_btiles, BT, sizeof(K4S<PPC>), st>>>(w, ls);
   rec(ev, 2, 1, st);
   rec(ev, 3, 0, st);
-  k_musl<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
+  k_musl_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 3, 1, st);
   rec(ev, 4, 0, st);
-  k_fupd<<<ls.n_ptiles, ls.ptile_size, 0, st>>>(w, ls);
+  k_fupd<<<ls.n_btiles, BT, 0, st>>>(w, ls);
   rec(ev, 4, 1, st);
+}
+
+static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
+  const int nb = w.H.n_buckets;
+  const int nblk = (nb + 1023) / 1024;
+  rec(ev, 10, 0, st);
+  k_pair_clear<<<(nb + 1 + 255) / 256, 256, 0, st>>>(w, ls);
+  k_pair_vmax<<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  rec(ev, 10, 1, st);
+  rec(ev, 11, 0, st);
+  k_pair_hash<<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  rec(ev, 11, 1, st);
+  rec(ev, 12, 0, st);
+  k_scan_local<<<nblk, 1024, 0, st>>>(w);
+  rec(ev, 12, 1, st);
+  rec(ev, 13, 0, st);
+  k_scan_top<<<1, 1024, 0, st>>>(w, nblk);
+  rec(ev, 13, 1, st);
+  rec(ev, 14, 0, st);
+  k_scan_add<<<nblk, 1024, 0, st>>>(w);
+  rec(ev, 14, 1, st);
+  rec(ev, 15, 0, st);
+  k_pair_fill<<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  rec(ev, 15, 1, st);
+  rec(ev, 16, 0, st);
+  k_pair_sort<<<(nb + 255) / 256, 256, 0, st>>>(w);
+  rec(ev, 16, 1, st);
+  rec(ev, 17, 0, st);
+  k_pair<<<ls.n_btiles, 128, 0, st>>>(w, ls);
+  rec(ev, 17, 1, st);
+}
+
+cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
+  if (ls.n_btiles == 0) return cudaSuccess;
+  if (ls.any_pair && w.H.n_buckets > 0) launch_pairs(w, ls, st, ev);
+  if (ls.ppc16) launch_bricks<16>(w, ls, st, ev);
+  else launch_bricks<8>(w, ls, st, ev);
   rec(ev, 5, 0, st);
   k_tool<<<ls.n_scenes, 256, 0, st>>>(w, ls);
   rec(ev, 5, 1, st);

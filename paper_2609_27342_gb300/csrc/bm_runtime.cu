@@ -107,13 +107,15 @@ struct bm_scene_s {
   int64_t n = 0;
   std::vector<float> X;               // caller order, [n][3]
   std::vector<int> cell_start_rel;    // n_cell + 1, relative to the scene's first particle
-  int nb[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
-  int64_t n_cell = 0, n_node = 0, slot_cap = 0, hist_cap = 0;
+  int nb[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, nbr[3] = {0, 0, 0};
+  int64_t n_cell = 0, n_node = 0, n_brick = 0, slot_cap = 0, hist_cap = 0, ppool_cap = 0;
+  int ppc_max = 0;                    // most particles in one base cell
   WorldH *world = nullptr;
   bool own_world = false;
   int slot = -1;
-  int64_t p_begin = 0, cell_begin = 0, node_begin = 0, slot_begin = 0, hist_begin = 0;
-  int ptile_begin = 0, n_ptile = 0, ntile_begin = 0, n_ntile = 0;
+  int64_t p_begin = 0, cell_begin = 0, node_begin = 0, slot_begin = 0, hist_begin = 0, brick_begin = 0,
+          ppool_begin = 0;
+  int ntile_begin = 0, n_ntile = 0;
   DevScene tmpl{};                    // static fields (host template)
   // staged fresh state, uploaded when the scene first enters a world
   std::vector<float> h_fx[3];
@@ -129,21 +131,21 @@ struct WorldH {
   Allocator al;
   cudaStream_t st = nullptr;
   bool own_stream = false;
-  int64_t cap_p = 0, cap_cell = 0, cap_node = 0, cap_slot = 0, cap_hist = 0;
-  int cap_scenes = 0, cap_ptile = 0, cap_ntile = 0;
+  int64_t cap_p = 0, cap_cell = 0, cap_node = 0, cap_slot = 0, cap_hist = 0, cap_brick = 0, cap_ppool = 0;
+  int cap_scenes = 0, cap_ntile = 0;
   bool pair = false;
   World w{};
   std::vector<void *> allocs;
-  RangeAlloc rp, rcell, rnode, rslot, rhist;
+  RangeAlloc rp, rcell, rnode, rslot, rhist, rbrick, rppool;
   std::vector<int> free_slots;
-  int4 *d_ptiles = nullptr, *d_ntiles = nullptr;
+  int4 *d_btiles = nullptr, *d_ntiles = nullptr;
   int *d_scene_ids = nullptr, *d_slot_ids = nullptr;
   double *d_stage = nullptr;
-  int ptile_size = 256, ntile_size = 128;
+  int ntile_size = 128;
   int graph_chunk = 16;
   std::vector<bm_scene_s *> members;
   bool tiles_dirty = true;
-  int n_ptiles = 0, n_ntiles = 0;
+  int n_btiles = 0, n_ntiles = 0;
   std::map<int, cudaGraphExec_t> graphs;
 
   template <class T>
@@ -186,6 +188,8 @@ int world_alloc(WorldH *W) {
     ptr = W->get<int>(c);
     ok &= ptr != nullptr;
   };
+  cudaError_t ie = bm_kernels_init();
+  if (ie != cudaSuccess) return fail(BM_E_CUDA, std::string("kernel set-up: ") + cudaGetErrorString(ie));
   for (int a = 0; a < 3; ++a) {
     F(pp.fx[a], P);
     F(pp.x[a], P);
@@ -193,24 +197,30 @@ int world_alloc(WorldH *W) {
     F(pp.ut[a], P);
     F(pp.J[a], P);
   }
-  for (int k = 0; k < 9; ++k) {
-    F(pp.F[k], P);
-    F(pp.A[k], P);
-  }
+  for (int k = 0; k < 9; ++k) F(pp.F[k], P);
   F(pp.D, P);
   U(pp.base, P);
   U(pp.s1, P);
   U(pp.s2, P);
   I(pp.perm, P);
-  I(pp.list, P);
+  pp.pend = W->get<uint8_t>(P);
+  ok &= pp.pend != nullptr;
   if (W->pair) {
     I(pp.hkey, P);
-    I(pp.hcell, P);
+    pp.hcell = W->get<long long>(P);
+    ok &= pp.hcell != nullptr;
     I(pp.horder, P);
     for (int b = 0; b < 2; ++b) {
       I(pp.hist_partner[b], P * BM_HIST);
       F(pp.hist_u[b], P * BM_HIST * 3);
     }
+    int nb = 1024;
+    while (nb < 2 * P && nb < (1 << 28)) nb <<= 1;
+    HashPool &H = W->w.H;
+    H.n_buckets = nb;
+    I(H.bucket_start, (int64_t)nb + 1);
+    I(H.bucket_fill, nb);
+    I(H.block_sum, nb / 1024 + 1);
   }
   NPool &np = W->w.N;
   I(np.cell_start, W->cap_cell);
@@ -226,15 +236,22 @@ int world_alloc(WorldH *W) {
   sp.vstar = W->get<float4>(W->cap_slot);
   sp.code = W->get<uint2>(W->cap_slot);
   ok &= sp.vold && sp.vnew && sp.vstar && sp.code;
+  BPool &bp = W->w.B;
+  bp.pm = W->get<float4>(W->cap_ppool);
+  bp.pd = W->get<float4>(W->cap_ppool);
+  bp.plo = W->get<uint16_t>(W->cap_brick * BM_TILE_NODES);
+  bp.poff = W->get<int>(W->cap_brick);
+  bp.ptot = W->get<int>(W->cap_brick);
+  ok &= bp.pm && bp.pd && bp.plo && bp.poff && bp.ptot;
   W->w.scenes = W->get<DevScene>(W->cap_scenes);
-  W->w.wpart = W->get<double>((int64_t)W->cap_ptile * 6);
+  W->w.wpart = W->get<double>(W->cap_brick * 6);
   W->w.whist = W->get<double>(std::max<int64_t>(W->cap_hist, 1) * 6);
-  W->d_ptiles = W->get<int4>(W->cap_ptile);
+  W->d_btiles = W->get<int4>(W->cap_brick);
   W->d_ntiles = W->get<int4>(W->cap_ntile);
   W->d_scene_ids = W->get<int>(W->cap_scenes);
   W->d_slot_ids = W->get<int>(W->cap_scenes);
   W->d_stage = W->get<double>((int64_t)W->cap_scenes * 18);
-  ok &= W->w.scenes && W->w.wpart && W->w.whist && W->d_ptiles && W->d_ntiles && W->d_scene_ids &&
+  ok &= W->w.scenes && W->w.wpart && W->w.whist && W->d_btiles && W->d_ntiles && W->d_scene_ids &&
         W->d_slot_ids && W->d_stage;
   if (!ok) return fail(BM_E_OOM, "device allocation failed");
   W->rp.init(W->cap_p);
@@ -242,12 +259,14 @@ int world_alloc(WorldH *W) {
   W->rnode.init(W->cap_node);
   W->rslot.init(W->cap_slot);
   W->rhist.init(W->cap_hist);
+  W->rbrick.init(W->cap_brick);
+  W->rppool.init(W->cap_ppool);
   W->free_slots.clear();
   for (int i = W->cap_scenes - 1; i >= 0; --i) W->free_slots.push_back(i);
   std::vector<int> ids(W->cap_scenes);
   for (int i = 0; i < W->cap_scenes; ++i) ids[i] = i;
   CK(cudaMemcpy(W->d_slot_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemset(W->w.wpart, 0, sizeof(double) * (size_t)W->cap_ptile * 6));
+  CK(cudaMemset(W->w.wpart, 0, sizeof(double) * (size_t)W->cap_brick * 6));
   return BM_OK;
 }
 
@@ -255,15 +274,14 @@ int64_t tiles_for(int64_t n, int tile) { return (n + tile - 1) / tile; }
 
 // assign tile ranges to every member, upload the tile lists and the ranges
 int rebuild_tiles(WorldH *W) {
-  std::vector<int4> pt, nt;
+  std::vector<int4> bt, nt;
   std::vector<int> ids;
   for (bm_scene_s *s : W->members) {
-    s->ptile_begin = (int)pt.size();
-    for (int64_t b = 0; b < s->n; b += W->ptile_size) {
-      int c = (int)std::min<int64_t>(W->ptile_size, s->n - b);
-      pt.push_back(make_int4(s->slot, (int)(s->p_begin + b), c, (int)pt.size()));
+    for (int64_t b = 0; b < s->n_brick; ++b) {
+      const int first = s->cell_start_rel[(size_t)b * BM_BRICK_CELLS];
+      const int last = s->cell_start_rel[(size_t)(b + 1) * BM_BRICK_CELLS];
+      bt.push_back(make_int4(s->slot, (int)(s->brick_begin + b), (int)(s->p_begin + first), last - first));
     }
-    s->n_ptile = (int)pt.size() - s->ptile_begin;
     s->ntile_begin = (int)nt.size();
     for (int64_t b = 0; b < s->n_node; b += W->ntile_size) {
       int c = (int)std::min<int64_t>(W->ntile_size, s->n_node - b);
@@ -272,28 +290,38 @@ int rebuild_tiles(WorldH *W) {
     s->n_ntile = (int)nt.size() - s->ntile_begin;
     ids.push_back(s->slot);
   }
-  if ((int64_t)pt.size() > W->cap_ptile || (int64_t)nt.size() > W->cap_ntile)
+  if ((int64_t)bt.size() > W->cap_brick || (int64_t)nt.size() > W->cap_ntile)
     return fail(BM_E_CAPACITY, "tile lists exceed the batch capacity");
-  if (!pt.empty()) CK(cudaMemcpy(W->d_ptiles, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));
+  if (!bt.empty()) CK(cudaMemcpy(W->d_btiles, bt.data(), sizeof(int4) * bt.size(), cudaMemcpyHostToDevice));
   if (!nt.empty()) CK(cudaMemcpy(W->d_ntiles, nt.data(), sizeof(int4) * nt.size(), cudaMemcpyHostToDevice));
   if (!ids.empty()) CK(cudaMemcpy(W->d_scene_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
   for (bm_scene_s *s : W->members) {
-    int r[4] = {s->ptile_begin, s->n_ptile, s->ntile_begin, s->n_ntile};
-    CK(cudaMemcpy((char *)(W->w.scenes + s->slot) + offsetof(DevScene, ptile_begin), r, sizeof r,
+    int r[2] = {s->ntile_begin, s->n_ntile};
+    CK(cudaMemcpy((char *)(W->w.scenes + s->slot) + offsetof(DevScene, ntile_begin), r, sizeof r,
                   cudaMemcpyHostToDevice));
   }
-  W->n_ptiles = (int)pt.size();
+  W->n_btiles = (int)bt.size();
   W->n_ntiles = (int)nt.size();
   W->tiles_dirty = false;
   W->drop_graphs();
   return BM_OK;
 }
 
+// brick tiles of one scene inside the world's list (scenes are listed in order)
+int scene_btile_begin(const WorldH *W, const bm_scene_s *s) {
+  int b = 0;
+  for (const bm_scene_s *m : W->members) {
+    if (m == s) return b;
+    b += (int)m->n_brick;
+  }
+  return -1;
+}
+
 LaunchSet scene_set(const WorldH *W, const bm_scene_s *s) {
   LaunchSet ls{};
-  ls.ptiles = W->d_ptiles + s->ptile_begin;
-  ls.n_ptiles = s->n_ptile;
-  ls.ptile_size = W->ptile_size;
+  ls.btiles = W->d_btiles + scene_btile_begin(W, s);
+  ls.n_btiles = (int)s->n_brick;
+  ls.ppc16 = s->ppc_max > 8;
   ls.ntiles = W->d_ntiles + s->ntile_begin;
   ls.n_ntiles = s->n_ntile;
   ls.ntile_size = W->ntile_size;
@@ -305,15 +333,17 @@ LaunchSet scene_set(const WorldH *W, const bm_scene_s *s) {
 
 LaunchSet world_set(const WorldH *W) {
   LaunchSet ls{};
-  ls.ptiles = W->d_ptiles;
-  ls.n_ptiles = W->n_ptiles;
-  ls.ptile_size = W->ptile_size;
+  ls.btiles = W->d_btiles;
+  ls.n_btiles = W->n_btiles;
   ls.ntiles = W->d_ntiles;
   ls.n_ntiles = W->n_ntiles;
   ls.ntile_size = W->ntile_size;
   ls.scene_ids = W->d_scene_ids;
   ls.n_scenes = (int)W->members.size();
-  for (auto *s : W->members) ls.any_pair |= s->desc.pair_contact;
+  for (auto *s : W->members) {
+    ls.any_pair |= s->desc.pair_contact;
+    ls.ppc16 |= s->ppc_max > 8;
+  }
   return ls;
 }
 
@@ -323,6 +353,8 @@ void fill_template(bm_scene_s *s) {
   std::memset(&t, 0, sizeof t);
   t.nb[0] = s->nb[0]; t.nb[1] = s->nb[1]; t.nb[2] = s->nb[2];
   t.nn[0] = s->nn[0]; t.nn[1] = s->nn[1]; t.nn[2] = s->nn[2];
+  t.nbr[0] = s->nbr[0]; t.nbr[1] = s->nbr[1]; t.nbr[2] = s->nbr[2];
+  t.n_brick = (int)s->n_brick;
   t.n_p = (int)s->n;
   t.n_node = (int)s->n_node;
   t.n_cell = (int)s->n_cell;
@@ -354,6 +386,8 @@ void fill_template(bm_scene_s *s) {
   t.pair_mu_s = (float)d.pair_mu_s;
   t.pair_mu_d = (float)d.pair_mu_d;
   t.floor_z = (float)d.floor_z;
+  t.pair_h = (float)(3.0 * d.s_R * std::cbrt(d.V0) / 2.0);  // 2 R_p plus an R_p margin
+  t.pair_inv_h = (float)(1.0 / (3.0 * d.s_R * std::cbrt(d.V0) / 2.0));
   t.floor_on = d.floor_enabled;
   t.pair_on = d.pair_contact;
   t.tool_contact_on = d.tool_contact;
@@ -414,8 +448,10 @@ void set_ranges(const bm_scene_s *s, DevScene &t) {
   t.cell_begin = (int)s->cell_begin;
   t.slot_begin = (int)s->slot_begin;
   t.hist_begin = (int)s->hist_begin;
-  t.ptile_begin = s->ptile_begin;
-  t.n_ptile = s->n_ptile;
+  t.brick_begin = (int)s->brick_begin;
+  t.n_brick = (int)s->n_brick;
+  t.ppool_begin = (int)s->ppool_begin;
+  t.ppool_cap = (int)s->ppool_cap;
   t.ntile_begin = s->ntile_begin;
   t.n_ntile = s->n_ntile;
 }
@@ -429,7 +465,11 @@ int reserve(WorldH *W, bm_scene_s *s) {
   int64_t nb = W->rnode.take(s->n_node);
   int64_t sb = W->rslot.take(s->slot_cap);
   int64_t hb = W->rhist.take(s->hist_cap);
-  if (pb < 0 || cb < 0 || nb < 0 || sb < 0 || hb < 0) {
+  int64_t bb = W->rbrick.take(s->n_brick);
+  int64_t qb = W->rppool.take(s->ppool_cap);
+  if (pb < 0 || cb < 0 || nb < 0 || sb < 0 || hb < 0 || bb < 0 || qb < 0) {
+    if (bb >= 0) W->rbrick.give(bb, s->n_brick);
+    if (qb >= 0) W->rppool.give(qb, s->ppool_cap);
     if (pb >= 0) W->rp.give(pb, s->n);
     if (cb >= 0) W->rcell.give(cb, s->n_cell + 1);
     if (nb >= 0) W->rnode.give(nb, s->n_node);
@@ -444,6 +484,8 @@ int reserve(WorldH *W, bm_scene_s *s) {
   s->node_begin = nb;
   s->slot_begin = sb;
   s->hist_begin = hb;
+  s->brick_begin = bb;
+  s->ppool_begin = qb;
   return BM_OK;
 }
 
@@ -453,6 +495,8 @@ void unreserve(WorldH *W, bm_scene_s *s) {
   W->rnode.give(s->node_begin, s->n_node);
   W->rslot.give(s->slot_cap ? s->slot_begin : 0, s->slot_cap);
   W->rhist.give(s->hist_begin, s->hist_cap);
+  W->rbrick.give(s->brick_begin, s->n_brick);
+  W->rppool.give(s->ppool_begin, s->ppool_cap);
   W->free_slots.push_back(s->slot);
   s->slot = -1;
 }
@@ -490,6 +534,8 @@ int place_fresh(WorldH *W, bm_scene_s *s) {
     else CK(cudaMemsetAsync(P.F[k] + pb, 0, sizeof(float) * n, st));
   }
   CK(cudaMemsetAsync(P.D + pb, 0, sizeof(float) * n, st));
+  CK(cudaMemsetAsync(P.pend + pb, 0, n, st));
+  for (int a = 0; a < 3; ++a) CK(cudaMemsetAsync(P.J[a] + pb, 0, sizeof(float) * n, st));
   CK(cudaMemsetAsync(P.s1 + pb, 0, sizeof(uint32_t) * n, st));
   CK(cudaMemsetAsync(P.s2 + pb, 0, sizeof(uint32_t) * n, st));
   CK(cudaMemcpyAsync(P.base + pb, s->h_base.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st));
@@ -563,6 +609,8 @@ int move_scene(bm_scene_s *s, WorldH *W) {
   CK(cp(B.s1 + pd, A.s1 + ps, sizeof(uint32_t) * n));
   CK(cp(B.s2 + pd, A.s2 + ps, sizeof(uint32_t) * n));
   CK(cp(B.perm + pd, A.perm + ps, sizeof(int) * n));
+  CK(cudaMemsetAsync(B.pend + pd, 0, n, st));
+  for (int a = 0; a < 3; ++a) CK(cudaMemsetAsync(B.J[a] + pd, 0, sizeof(float) * n, st));
   if (W->pair) {
     for (int b = 0; b < 2; ++b) {
       if (S->pair) {
@@ -589,7 +637,7 @@ int move_scene(bm_scene_s *s, WorldH *W) {
   }
   set_ranges(s, cur);
   cur.slot_cap = (int)s->slot_cap;
-  cur.list_count = 0;
+  cur.label_pending = 0;
   CK(cudaMemcpy(W->w.scenes + s->slot, &cur, sizeof cur, cudaMemcpyHostToDevice));
   // leave the old world
   auto &mem = S->members;
@@ -619,7 +667,8 @@ int create_private_world(bm_scene_s *s, const bm_alloc *alloc, cudaStream_t st) 
   W->cap_slot = s->slot_cap;
   W->cap_hist = s->hist_cap;
   W->cap_scenes = 1;
-  W->cap_ptile = (int)tiles_for(s->n, 128) + 1;
+  W->cap_brick = s->n_brick;
+  W->cap_ppool = s->ppool_cap;
   W->cap_ntile = (int)tiles_for(s->n_node, 64) + 1;
   W->pair = s->desc.pair_contact != 0;
   int rc = world_alloc(W);
@@ -665,18 +714,26 @@ int build_layout(bm_scene_s *s) {
     s->lo[a] = lo[a];
     s->nb[a] = hi[a] - lo[a] + 1;
     s->nn[a] = s->nb[a] + 2;
-    if (s->nb[a] > 1023) return fail(BM_E_INVALID, "more than 1023 reference cells along an axis");
+    s->nbr[a] = (s->nb[a] + 3) / 4;
+    if (s->nb[a] > 1020) return fail(BM_E_INVALID, "more than 1020 reference cells along an axis");
   }
-  s->n_cell = (int64_t)s->nb[0] * s->nb[1] * s->nb[2];
+  // cells are numbered brick-major (bricks of 4x4x4, x-fastest inside), so
+  // each brick's particles are one contiguous range
+  s->n_brick = (int64_t)s->nbr[0] * s->nbr[1] * s->nbr[2];
+  s->n_cell = s->n_brick * BM_BRICK_CELLS;
   s->n_node = (int64_t)s->nn[0] * s->nn[1] * s->nn[2];
   if (s->n_node > (int64_t)1 << 30 || n > (int64_t)1 << 30) return fail(BM_E_INVALID, "scene too large");
   std::vector<int64_t> key((size_t)n);
   std::vector<int> cnt((size_t)s->n_cell + 1, 0);
   for (int64_t i = 0; i < n; ++i) {
     int bx = b3[3 * i] - lo[0], by = b3[3 * i + 1] - lo[1], bz = b3[3 * i + 2] - lo[2];
-    key[i] = ((int64_t)bz * s->nb[1] + by) * s->nb[0] + bx;
+    int64_t brick = ((int64_t)(bz >> 2) * s->nbr[1] + (by >> 2)) * s->nbr[0] + (bx >> 2);
+    key[i] = brick * BM_BRICK_CELLS + (((bz & 3) * 4 + (by & 3)) * 4 + (bx & 3));
     cnt[key[i] + 1]++;
   }
+  s->ppc_max = 0;
+  for (int64_t c = 0; c < s->n_cell; ++c) s->ppc_max = std::max(s->ppc_max, cnt[c + 1]);
+  if (s->ppc_max > 16) return fail(BM_E_INVALID, "more than 16 particles share one reference base cell");
   for (int64_t c = 0; c < s->n_cell; ++c) cnt[c + 1] += cnt[c];
   s->cell_start_rel = cnt;
   std::vector<int> fill((size_t)s->n_cell, 0);
@@ -692,6 +749,9 @@ int build_layout(bm_scene_s *s) {
     s->h_base[j] = bx | (by << 10) | (bz << 20);
   }
   s->slot_cap = std::max<int64_t>(4 * s->n_node, 64);
+  // brick-tile partial sums: a node appears in <= 8 tiles, ~3.4 on average;
+  // 6 entries per node covers ~1.8 logical grids per node on average
+  s->ppool_cap = std::max<int64_t>(6 * s->n_node, 4096);
   s->hist_cap = d.wrench_history > 0 ? d.wrench_history : 0;
   return BM_OK;
 }
@@ -1063,7 +1123,7 @@ int bm_scene_destroy(bm_scene_t s) {
 }
 
 int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n, int64_t *particles,
-                       int64_t *nodes, int64_t *bytes) {
+                       int64_t *nodes, int64_t *bricks, int64_t *bytes) {
   int rc = validate_desc(desc);
   if (rc) return rc;
   if (n <= 0 || !X_ref) return fail(BM_E_INVALID, "need at least one particle");
@@ -1075,9 +1135,11 @@ int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
   if (rc) return rc;
   if (particles) *particles = n;
   if (nodes) *nodes = s.n_node;
-  const int64_t per_p = 4 * (3 * 5 + 18 + 1) + 4 * 3 + 4 * 2 + (desc->pair_contact ? (3 * 4 + 2 * BM_HIST * 16) : 0);
-  const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (4 * 16 + 8);
-  if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.hist_cap * 48;
+  if (bricks) *bricks = s.n_brick;
+  const int64_t per_p = 4 * (3 * 5 + 9 + 1) + 4 * 2 + 4 + 1 + (desc->pair_contact ? (3 * 4 + 2 * BM_HIST * 16) : 0);
+  const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (3 * 16 + 8) + 6 * 32;
+  const int64_t per_brick = 2 * BM_TILE_NODES + 48 + 16 + 8;
+  if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.n_brick * per_brick + s.hist_cap * 48;
   return BM_OK;
 }
 
@@ -1099,19 +1161,19 @@ int bm_batch_create(const bm_batch_desc *desc, const bm_alloc *alloc, void *stre
   W->cap_p = desc->max_particles;
   W->cap_node = desc->max_nodes;
   W->cap_slot = desc->max_slots > 0 ? desc->max_slots : 4 * desc->max_nodes;
-  W->cap_cell = desc->max_nodes + desc->max_scenes;
   W->cap_scenes = desc->max_scenes;
+  // a scene's bricks never exceed its nodes / 27 (one brick covers >= 27 nodes)
+  W->cap_brick = desc->max_bricks > 0 ? desc->max_bricks : desc->max_nodes / 27 + desc->max_scenes;
+  W->cap_cell = W->cap_brick * BM_BRICK_CELLS + desc->max_scenes;
+  W->cap_ppool = 6 * desc->max_nodes + 4096 * (int64_t)desc->max_scenes;
   W->cap_hist = 0;
-  W->cap_ptile = (int)tiles_for(desc->max_particles, 128) + desc->max_scenes;
   W->cap_ntile = (int)tiles_for(desc->max_nodes, 64) + desc->max_scenes;
   W->pair = desc->pair_contact != 0;
-  W->ptile_size = desc->particle_tile > 0 ? desc->particle_tile : 256;
   W->ntile_size = desc->node_tile > 0 ? desc->node_tile : 128;
   W->graph_chunk = desc->graph_chunk > 0 ? desc->graph_chunk : 16;
-  if (W->ptile_size < 128 || W->ptile_size > 512 || W->ptile_size % 32 || W->ntile_size < 64 ||
-      W->ntile_size > 512 || W->ntile_size % 32) {
+  if (W->ntile_size < 64 || W->ntile_size > 512 || W->ntile_size % 32) {
     delete W;
-    return fail(BM_E_INVALID, "tile sizes must be multiples of 32 in [128,512] / [64,512]");
+    return fail(BM_E_INVALID, "node tile must be a multiple of 32 in [64, 512]");
   }
   int rc = world_alloc(W);
   if (rc) {
@@ -1138,14 +1200,13 @@ int bm_batch_remove(bm_batch_t b, bm_scene_t s) {
   return BM_OK;
 }
 
-int bm_batch_set_tiles(bm_batch_t b, int particle_tile, int node_tile) {
+int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile) {
   if (!b) return fail(BM_E_INVALID, "bad batch");
-  if (particle_tile < 128 || particle_tile > 512 || particle_tile % 32 || node_tile < 64 ||
-      node_tile > 512 || node_tile % 32)
-    return fail(BM_E_INVALID, "tile sizes must be multiples of 32 in [128,512] / [64,512]");
+  if (graph_chunk < 1 || graph_chunk > 256 || node_tile < 64 || node_tile > 512 || node_tile % 32)
+    return fail(BM_E_INVALID, "graph chunk in [1, 256]; node tile a multiple of 32 in [64, 512]");
   WorldH *W = b->world;
   CK(cudaStreamSynchronize(W->st));
-  W->ptile_size = particle_tile;
+  W->graph_chunk = graph_chunk;
   W->ntile_size = node_tile;
   W->tiles_dirty = true;
   return rebuild_tiles(W);

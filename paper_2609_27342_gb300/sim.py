@@ -213,25 +213,26 @@ class Scene:
 
 
 def footprint(sc) -> tuple:
+    """(particles, nodes, bricks, bytes) a scene takes in a batch."""
     L = A.load()
     X = np.ascontiguousarray(np.asarray(sc.X, dtype=np.float32))
     d = scene_desc(sc)
-    p, nd, b = C.c_int64(), C.c_int64(), C.c_int64()
+    p, nd, br, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
     A.check(L.bm_scene_footprint(C.byref(d), X.ctypes.data_as(C.POINTER(C.c_float)), X.shape[0],
-                                 C.byref(p), C.byref(nd), C.byref(b)))
-    return p.value, nd.value, b.value
+                                 C.byref(p), C.byref(nd), C.byref(br), C.byref(b)))
+    return p.value, nd.value, br.value, b.value
 
 
 class Batch:
     """Packed pools holding many scenes, stepped by CUDA-graph launches."""
 
     def __init__(self, max_particles: int, max_nodes: int, max_scenes: int,
-                 max_slots: int = 0, graph_chunk: int = 16, particle_tile: int = 256,
+                 max_slots: int = 0, max_bricks: int = 0, graph_chunk: int = 16,
                  node_tile: int = 128, pair_contact: bool = False, stream=None,
                  allocator: Optional[TorchAllocator] = None):
         self._L = A.load()
-        d = A.BatchDesc(int(max_particles), int(max_nodes), int(max_slots), int(max_scenes),
-                        int(graph_chunk), int(particle_tile), int(node_tile), int(pair_contact))
+        d = A.BatchDesc(int(max_particles), int(max_nodes), int(max_slots), int(max_bricks),
+                        int(max_scenes), int(graph_chunk), int(node_tile), int(pair_contact))
         h = C.c_void_p()
         self._alloc = allocator
         A.check(self._L.bm_batch_create(C.byref(d),
@@ -253,8 +254,8 @@ class Batch:
     def step(self, n: int = 1) -> None:
         A.check(self._L.bm_batch_step(self._h, int(n)))
 
-    def set_tiles(self, particle_tile: int, node_tile: int) -> None:
-        A.check(self._L.bm_batch_set_tiles(self._h, int(particle_tile), int(node_tile)))
+    def set_tiles(self, graph_chunk: int, node_tile: int) -> None:
+        A.check(self._L.bm_batch_set_tiles(self._h, int(graph_chunk), int(node_tile)))
 
     def members(self) -> list:
         n = self._L.bm_batch_members(self._h, None, 0)

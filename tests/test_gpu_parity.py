@@ -202,9 +202,9 @@ def test_batched_equals_plain_bitwise(pkg):
     for p in plain:
         p.step(24)
     ref = [p.read("x", "v", "F", "mask1", "mask2") for p in plain]
-    for tiles in [(256, 128), (128, 64), (512, 256)]:
+    for chunk, ntile in [(8, 128), (3, 64), (16, 256)]:
         b = pkg.Batch(max_particles=sum(s.n for s in scenes) + 1000, max_nodes=200000,
-                      max_scenes=8, graph_chunk=8, particle_tile=tiles[0], node_tile=tiles[1])
+                      max_scenes=8, graph_chunk=chunk, node_tile=ntile)
         gs = [pkg.Scene(s) for s in scenes]
         for s in gs:
             b.add(s)
@@ -212,7 +212,7 @@ def test_batched_equals_plain_bitwise(pkg):
         for s, r in zip(gs, ref):
             got = s.read("x", "v", "F", "mask1", "mask2")
             for k in r:
-                assert np.array_equal(got[k], r[k]), (tiles, k)
+                assert np.array_equal(got[k], r[k]), (chunk, ntile, k)
         b.close()
 
 
