@@ -18,7 +18,7 @@
 #include "../../include/blademaster.h"
 
 #define BM_MAXS 16           // logical grids (distinct codes) per node
-#define BM_TILE_SLOTS 1296   // shared-memory window of brick-tile slots (6 per tile node)
+#define BM_TILE_SLOTS 648    // tile slots cached in shared memory (3 per tile node); more use the pool
 #define BM_TILE_NODES 216    // 6 x 6 x 6 nodes touched by a brick of 4 x 4 x 4 base cells
 #define BM_BRICK_CELLS 64
 #define BM_HIST 16           // pair-contact history entries per particle
@@ -88,7 +88,8 @@ struct PPool {
   uint32_t *base;           // packed local base cell: bx | by << 10 | bz << 20
   float *x[3], *v[3], *F[9], *D, *ut[3];
   uint32_t *s1, *s2;        // bit k: digit k == 1 (s1) or == 2 (s2)
-  float *J[3];              // pair-contact impulse of this substep
+  float *A[9];              // -dt V0 P(F) / dx of this substep (k_pre -> k_p2g_brick)
+  float *J[3];              // impulse of this substep: pair contact, then the total
   uint8_t *pend;            // side digit assigned this substep (0: none), committed by k_fupd
   int *perm;                // pool index -> caller's particle index
   // pair contact
@@ -117,9 +118,9 @@ struct SPool {
 struct BPool {              // brick-tile partial sums
   float4 *pm;               // [poff[brick] + tile slot]: (sum N, sum N v) / MUSL sum N v
   float4 *pd;               // [poff[brick] + tile slot]: sum (A grad N + N J)
-  uint16_t *plo;            // [brick * BM_TILE_NODES]: first tile slot of each tile node
   int *poff;                // first entry of each brick's partial sums (-1: pool overflow)
   int *ptot;                // slots in each brick's tile
+  int *tdesc;               // [brick * BM_TILE_NODES]: first tile slot | slot count << 16
 };
 
 struct HashPool {           // pair-contact spatial hash (world-wide table)
@@ -156,7 +157,7 @@ struct LaunchSet {
 };
 
 // kernel launchers (bm_kernels.cu)
-#define BM_NUM_KERNELS 18
+#define BM_NUM_KERNELS 19
 extern const char *const bm_kernel_names[BM_NUM_KERNELS];
 cudaError_t bm_kernels_init();  // per device: shared-memory limits of the brick kernels
 cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st);

@@ -342,37 +342,25 @@ __device__ __forceinline__ void brick_coords(const DevScene &sc, int lb, int &c0
   c0z = (lb / (sc.nbr[0] * sc.nbr[1])) * BR;
 }
 
-// Cooperative load of a brick's tile (all threads; ends with a barrier).
-__device__ void tile_load(const World &w, const DevScene &sc, int c0x, int c0y, int c0z, Tile &T) {
+// Cooperative load of a brick's tile (all threads; ends with a barrier).  The
+// per-node slot counts and first tile slots come from the descriptor the
+// slot rebuild wrote for this brick; the nodes' first pool slots from the
+// slot table.
+__device__ void tile_load(const World &w, const DevScene &sc, int brick, int c0x, int c0y, int c0z,
+                          Tile &T) {
   for (int t = threadIdx.x; t < TN; t += blockDim.x) {
-    const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
-    int cnt = 0, off = 0;
-    if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2]) {
-      const int node = sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx;
-      cnt = w.N.slot_cnt[node];
-      off = w.N.slot_off[node];
+    const int d = w.B.tdesc[(size_t)brick * TN + t];
+    const int cnt = d >> 16;
+    int off = 0;
+    if (cnt) {
+      const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
+      off = w.N.slot_off[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
     }
+    T.lo[t] = (uint16_t)(d & 0xffff);
     T.cnt[t] = (uint8_t)cnt;
     T.goff[t] = off;
   }
-  __syncthreads();
-  if (threadIdx.x < 32) {  // exclusive scan of the slot counts by one warp
-    const int lane = threadIdx.x;
-    int carry = 0;
-    for (int base = 0; base < TN; base += 32) {
-      const int t = base + lane;
-      const int v = t < TN ? (int)T.cnt[t] : 0;
-      int x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-      }
-      if (t < TN) T.lo[t] = (uint16_t)(carry + x - v);
-      carry += __shfl_sync(FULL, x, 31);
-    }
-    if (lane == 0) T.total = carry;
-  }
+  if (threadIdx.x == 0) T.total = w.B.ptot[brick];
   __syncthreads();
 }
 
@@ -399,111 +387,25 @@ __device__ __forceinline__ int tile_slot(const World &w, const Tile &T, const ui
   return -1;
 }
 
-// the tile's slot codes into shared memory (all threads; no barrier)
-__device__ __forceinline__ void tile_codes(const World &w, const Tile &T, uint2 *codes) {
-  for (int t = threadIdx.x; t < TN; t += blockDim.x) {
-    const int n = T.cnt[t];
-    if (n < 2) continue;
-    const int lo = T.lo[t], g = T.goff[t];
-    for (int a = 0; a < n; ++a) codes[lo + a] = w.S.code[g + a];
-  }
-}
-
-// k-th distinct code (first-occurrence order) among a cell's particles
-__device__ __forceinline__ bool cell_code(const uint32_t *s1, const uint32_t *s2, int c, int n, int k,
-                                          uint32_t &k1, uint32_t &k2) {
-  int seen = -1;
-  for (int j = 0; j < n; ++j) {
-    const uint32_t a = s1[j * BR3 + c], b = s2[j * BR3 + c];
-    bool first = true;
-    for (int q = 0; q < j; ++q)
-      if (s1[q * BR3 + c] == a && s2[q * BR3 + c] == b) {
-        first = false;
-        break;
-      }
-    if (first && ++seen == k) {
-      k1 = a;
-      k2 = b;
-      return true;
-    }
-  }
-  return false;
-}
-
-__device__ __forceinline__ int cell_code_count(const uint32_t *s1, const uint32_t *s2, int c, int n) {
-  int cnt = 0;
-  for (int j = 0; j < n; ++j) {
-    const uint32_t a = s1[j * BR3 + c], b = s2[j * BR3 + c];
-    bool first = true;
-    for (int q = 0; q < j; ++q)
-      if (s1[q * BR3 + c] == a && s2[q * BR3 + c] == b) {
-        first = false;
-        break;
-      }
-    cnt += first;
-  }
-  return cnt;
-}
-
 // --------------------------------------------------------------------------
-// k_p2g_brick: per particle contact, cutting progress, labels and stress,
-// then the brick's share of P2G (Eq. 2) into its node tile, per logical grid.
-//
-// Phase 0, one thread per particle: tool and floor contact (Eq. 14-15 with
-// friction Eq. 12), D update and release (Eq. 5), reaction wrench (Eq. 16),
-// side label for the next substep (Eq. 3, 4, 6), A = -dt V0 P(F).  Results
-// go to shared memory laid out [particle-in-cell][cell].
-// Phase 1, one thread per (cell, z-offset): sums over the cell's particles of
-// m N, m v N, A grad N + N J for its 9 nodes, per code present in the cell.
-// Commits go to the tile in 27 barrier-separated phases (one node offset
-// each; distinct cells hit distinct nodes), so every tile slot receives its
-// contributions in a fixed order: no atomics, bit-reproducible.
+// k_pre, one thread per particle (CTA per brick): tool and floor contact
+// (Eq. 14-15 with friction Eq. 12), cutting progress D and release (Eq. 5),
+// reaction wrench (Eq. 16), side label for the next substep (Eq. 3, 4, 6),
+// and A = -dt V0 P(F) / dx with the total impulse J for P2G.
 // --------------------------------------------------------------------------
-template <int PPC>
-struct K2S {
-  Tile T;
-  uint2 codes[TSCAP];
-  float acc[7][TSCAP];
-  float pf[3][PPC * BR3];
-  float pv[3][PPC * BR3];
-  float pA[9][PPC * BR3];
-  float pJ[3][PPC * BR3];
-  uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
-  int cs[BR3 + 1];
-  double red[32];
-  int maxcodes;
-};
-
-template <int PPC>
-__global__ void __launch_bounds__(BT, 2) k_p2g_brick(World w, LaunchSet ls) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  K2S<PPC> &S = *reinterpret_cast<K2S<PPC> *>(smraw);
-  const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
+__global__ void __launch_bounds__(256) k_pre(World w, LaunchSet ls) {
+  __shared__ float red[6][8];
+  const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
   const DevScene &sc = scm;
   const PPool &P = w.P;
   const int tid = threadIdx.x;
-  const int lb = bt.y - sc.brick_begin;
-  int c0x, c0y, c0z;
-  brick_coords(sc, lb, c0x, c0y, c0z);
-  const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
-  for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
-  if (tid == 0) S.maxcodes = 0;
-  tile_load(w, sc, c0x, c0y, c0z, S.T);
-  const uint2 *tcodes = S.T.total <= TSCAP ? S.codes : nullptr;
-  if (tcodes) tile_codes(w, S.T, S.codes);
-
-  // ---- phase 0: per particle ----
-  double wr[6] = {0, 0, 0, 0, 0, 0};
-  bool clamped = false;
+  float wr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  bool clamped = false, anyc = false;
   const float dt = sc.dt, mp = sc.mp;
   const int cut = sc.cut;
-  for (int i = tid; i < bt.w; i += BT) {
+  for (int i = tid; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
-    int bx, by, bz;
-    particle_base(P.base[p], bx, by, bz);
-    const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
-    const int si = (i - S.cs[c]) * BR3 + c;
     float x[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
     float v[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
     const uint32_t s1 = P.s1[p], s2 = P.s2[p];
@@ -564,6 +466,7 @@ __global__ void __launch_bounds__(BT, 2) k_p2g_brick(World w, LaunchSet ls) {
       }
       const float idt = 1.0f / dt;
       const float FB[3] = {-JB[0] * idt, -JB[1] * idt, -JB[2] * idt};
+      anyc |= Jn > 0.0f;
       wr[0] += FB[0];
       wr[1] += FB[1];
       wr[2] += FB[2];
@@ -593,20 +496,12 @@ __global__ void __launch_bounds__(BT, 2) k_p2g_brick(World w, LaunchSet ls) {
     for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
     float Pk[9];
     clamped |= piola(F, sc.mu, sc.lam, Pk);
-    const float cA = -dt * sc.V0;
+    const float cA = -dt * sc.V0 * sc.inv_dx;  // grad N is applied per axis in units of 1/dx
 #pragma unroll
-    for (int k = 0; k < 9; ++k) S.pA[k][si] = cA * Pk[k];
-    S.pJ[0][si] = J[0];
-    S.pJ[1][si] = J[1];
-    S.pJ[2][si] = J[2];
-    S.pv[0][si] = v[0];
-    S.pv[1][si] = v[1];
-    S.pv[2][si] = v[2];
-    S.pf[0][si] = P.fx[0][p];
-    S.pf[1][si] = P.fx[1][p];
-    S.pf[2][si] = P.fx[2][p];
-    S.ps1[si] = s1;
-    S.ps2[si] = s2;
+    for (int k = 0; k < 9; ++k) P.A[k][p] = cA * Pk[k];
+    P.J[0][p] = J[0];
+    P.J[1][p] = J[1];
+    P.J[2][p] = J[2];
     P.D[p] = D;
     P.ut[0][p] = uh[0];
     P.ut[1][p] = uh[1];
@@ -615,94 +510,187 @@ __global__ void __launch_bounds__(BT, 2) k_p2g_brick(World w, LaunchSet ls) {
   }
   if (clamped) atomicOr(&scm.err, BM_ERRBIT_INVERTED);
   if (sc.has_blade) {
+    // per-brick wrench partial: float32 sums inside the brick (fixed shuffle
+    // tree, warps in order); bricks without tool contact write zeros
+    if (__syncthreads_or(anyc)) {
+      const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const double s = block_sum(wr[k], S.red);
-      if (tid == 0) w.wpart[(size_t)bt.y * 6 + k] = s;
+      for (int k = 0; k < 6; ++k) {
+        float v = wr[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+        if (lane == 0) red[k][wid] = v;
+      }
+      __syncthreads();
+      if (tid < 6) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += (double)red[tid][q];
+        w.wpart[(size_t)bt.y * 6 + tid] = s;
+      }
+    } else if (tid < 6) {
+      w.wpart[(size_t)bt.y * 6 + tid] = 0.0;
     }
   }
+}
+
+// --------------------------------------------------------------------------
+// k_p2g_brick: the brick's share of P2G (Eq. 2) into its node tile, per
+// logical grid, from the particles' A, J, v staged in shared memory.
+// --------------------------------------------------------------------------
+template <int PPC>
+struct K2S {
+  Tile T;
+  float stage[9 * 7][BT];  // per (cell, z-offset) thread: sums for its 9 nodes
+  uint2 ccode[BR3][PPC];   // distinct codes of each cell (first-occurrence order)
+  int ncode[BR3];
+  int cs[BR3 + 1];
+  int maxcodes;
+};
+
+// distinct codes of each cell, once per cell (threads of z-offset 0).
+// s1/s2 point at particle 0 of the brick's first cell (pool order) when
+// stride == 1, or at the [particle-in-cell][cell] staging when stride == 0.
+template <int PPC>
+__device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s2, const int *cs,
+                                           bool pool_order, uint2 (*ccode)[PPC], int *ncode,
+                                           int *maxcodes) {
+  const int c = threadIdx.x;
+  if (c >= BR3) return;
+  const int n = cs[c + 1] - cs[c];
+  int cnt = 0;
+  for (int j = 0; j < n; ++j) {
+    const int k = pool_order ? cs[c] + j : j * BR3 + c;
+    const uint32_t a = s1[k], b = s2[k];
+    bool seen = false;
+    for (int q = 0; q < cnt; ++q)
+      if (ccode[c][q].x == a && ccode[c][q].y == b) {
+        seen = true;
+        break;
+      }
+    if (!seen) ccode[c][cnt++] = make_uint2(a, b);
+  }
+  ncode[c] = cnt;
+  atomicMax(maxcodes, cnt);
+}
+
+template <int PPC>
+__global__ void __launch_bounds__(BT, 3) k_p2g_brick(World w, LaunchSet ls) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  K2S<PPC> &S = *reinterpret_cast<K2S<PPC> *>(smraw);
+  const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
+  const PPool &P = w.P;
+  const int tid = threadIdx.x;
+  const int lb = bt.y - sc.brick_begin;
+  int c0x, c0y, c0z;
+  brick_coords(sc, lb, c0x, c0y, c0z);
+  const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
+  for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
+  if (tid == 0) S.maxcodes = 0;
+  tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
+  cell_codes<PPC>(P.s1 + bt.z, P.s2 + bt.z, S.cs, true, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
 
   // ---- phase 1: per (cell, z-offset) sums over the cell's particles ----
+  // Each thread sums, for its cell and one z-offset, m N, m v N and
+  // A grad N + N J over the cell's particles of one code (one pass per code
+  // present in the cell) into a staging area; then each tile node adds the
+  // <= 27 staged sums of the cells around it, in a fixed order, and writes
+  // its slots' partials.  Every float sum has one owner: no atomics.
   const int c = tid % BR3, oz = tid / BR3;
-  const int cx = c % BR, cy = (c / BR) % BR, cz = c / (BR * BR);
   const int n_c = S.cs[c + 1] - S.cs[c];
-  atomicMax(&S.maxcodes, cell_code_count(S.ps1, S.ps2, c, n_c));
-  __syncthreads();
-  const int iters = S.maxcodes;
-  const int total = S.T.total;
+  const int iters = S.maxcodes > 0 ? S.maxcodes : 1;  // one pass writes zeros for empty bricks
   const int pbase = w.B.poff[bt.y];  // this brick's partial-sum range (negative: pool overflow)
-  const float inv_dx = sc.inv_dx;
-  for (int w0 = 0; w0 < total; w0 += TSCAP) {  // shared-memory windows of tile slots
-    for (int j = tid; j < 7 * TSCAP; j += BT) (&S.acc[0][0])[j] = 0.f;
-    __syncthreads();
-    for (int it = 0; it < iters; ++it) {
-      uint32_t k1 = 0, k2 = 0;
-      const bool has = cell_code(S.ps1, S.ps2, c, n_c, it, k1, k2);
-      float a[9][7];
+  for (int it = 0; it < iters; ++it) {
+    const bool has = it < S.ncode[c];
+    const uint32_t k1 = has ? S.ccode[c][it].x : 0u, k2 = has ? S.ccode[c][it].y : 0u;
+    const bool uniform = S.ncode[c] == 1;
+    float a[9][7];
 #pragma unroll
-      for (int q = 0; q < 9; ++q)
+    for (int q = 0; q < 9; ++q)
 #pragma unroll
-        for (int f = 0; f < 7; ++f) a[q][f] = 0.f;
-      if (has) {
-        for (int j = 0; j < n_c; ++j) {
-          const int si = j * BR3 + c;
-          if (S.ps1[si] != k1 || S.ps2[si] != k2) continue;
-          float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
-          const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
-          bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
-          bs<0>(f1, wy[0], dwy[0]); bs<1>(f1, wy[1], dwy[1]); bs<2>(f1, wy[2], dwy[2]);
-          bs_rt(oz, f2, wz, dwz);
-          const float v0 = S.pv[0][si], v1 = S.pv[1][si], v2 = S.pv[2][si];
-          float A[9];
+      for (int f = 0; f < 7; ++f) a[q][f] = 0.f;
+    if (has) {
+      const int p0 = bt.z + S.cs[c];
+      for (int j = 0; j < n_c; ++j) {
+        const int p = p0 + j;  // the brick's particles, read through L1
+        if (!uniform && (P.s1[p] != k1 || P.s2[p] != k2)) continue;
+        float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
+        const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
+        bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
+        bs<0>(f1, wy[0], dwy[0]); bs<1>(f1, wy[1], dwy[1]); bs<2>(f1, wy[2], dwy[2]);
+        bs_rt(oz, f2, wz, dwz);
+        const float v0 = P.v[0][p], v1 = P.v[1][p], v2 = P.v[2][p];
+        float A[9];
 #pragma unroll
-          for (int k = 0; k < 9; ++k) A[k] = S.pA[k][si] * inv_dx;
-          const float J0 = S.pJ[0][si], J1 = S.pJ[1][si], J2 = S.pJ[2][si];
+        for (int k = 0; k < 9; ++k) A[k] = P.A[k][p];
+        const float J0 = P.J[0][p], J1 = P.J[1][p], J2 = P.J[2][p];
 #pragma unroll
-          for (int oy = 0; oy < 3; ++oy) {
-            const float wyz = wy[oy] * wz, dyz = dwy[oy] * wz, wyd = wy[oy] * dwz;
+        for (int oy = 0; oy < 3; ++oy) {
+          const float wyz = wy[oy] * wz, dyz = dwy[oy] * wz, wyd = wy[oy] * dwz;
 #pragma unroll
-            for (int ox = 0; ox < 3; ++ox) {
-              const float N = wx[ox] * wyz;
-              const float g0 = dwx[ox] * wyz, g1 = wx[ox] * dyz, g2 = wx[ox] * wyd;
-              float *q = a[oy * 3 + ox];
-              q[0] += N;
-              q[1] += N * v0;
-              q[2] += N * v1;
-              q[3] += N * v2;
-              q[4] += A[0] * g0 + A[1] * g1 + A[2] * g2 + N * J0;
-              q[5] += A[3] * g0 + A[4] * g1 + A[5] * g2 + N * J1;
-              q[6] += A[6] * g0 + A[7] * g1 + A[8] * g2 + N * J2;
-            }
+          for (int ox = 0; ox < 3; ++ox) {
+            const float N = wx[ox] * wyz;
+            const float g0 = dwx[ox] * wyz, g1 = wx[ox] * dyz, g2 = wx[ox] * wyd;
+            float *q = a[oy * 3 + ox];
+            q[0] += N;
+            q[1] += N * v0;
+            q[2] += N * v1;
+            q[3] += N * v2;
+            q[4] += A[0] * g0 + A[1] * g1 + A[2] * g2 + N * J0;
+            q[5] += A[3] * g0 + A[4] * g1 + A[5] * g2 + N * J1;
+            q[6] += A[6] * g0 + A[7] * g1 + A[8] * g2 + N * J2;
           }
         }
       }
-      // commits: one node offset per phase, so no two threads touch one slot
+    }
 #pragma unroll
-      for (int ozp = 0; ozp < 3; ++ozp)
+    for (int q = 0; q < 9; ++q)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          if (has && oz == ozp) {
-            const int t = ((cz + oz) * TE + (cy + q / 3)) * TE + (cx + q % 3);
-            const int s = tile_slot(w, S.T, tcodes, t, k1, k2) - w0;
-            if (s >= 0 && s < TSCAP) {
+      for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][tid] = a[q][f];
+    __syncthreads();
+    // tile nodes gather the staged sums of the cells around them
+    if (pbase >= 0)
+      for (int t = tid; t < TN; t += BT) {
+        const int n = S.T.cnt[t];
+        if (n == 0) continue;
+        const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
+        const size_t e0 = (size_t)pbase + S.T.lo[t];
+        for (int sl = 0; sl < n; ++sl) {
+          const uint2 code = n > 1 ? w.S.code[S.T.goff[t] + sl] : make_uint2(0u, 0u);
+          float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int ozz = 0; ozz < 3; ++ozz) {
+            const int zz = tz - ozz;
+            if (zz < 0 || zz >= BR) continue;
+            for (int oyy = 0; oyy < 3; ++oyy) {
+              const int yy = ty - oyy;
+              if (yy < 0 || yy >= BR) continue;
+              for (int oxx = 0; oxx < 3; ++oxx) {
+                const int xx = tx - oxx;
+                if (xx < 0 || xx >= BR) continue;
+                const int cc = (zz * BR + yy) * BR + xx;
+                if (it >= S.ncode[cc]) continue;
+                if (n > 1 && (S.ccode[cc][it].x != code.x || S.ccode[cc][it].y != code.y)) continue;
+                const int src = ozz * BR3 + cc, q = oyy * 3 + oxx;
 #pragma unroll
-              for (int f = 0; f < 7; ++f) S.acc[f][s] += a[q][f];
+                for (int f = 0; f < 7; ++f) acc[f] += S.stage[q * 7 + f][src];
+              }
             }
           }
-          __syncthreads();
+          const size_t e = e0 + sl;
+          if (it == 0) {
+            w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            w.B.pd[e] = make_float4(acc[4], acc[5], acc[6], 0.f);
+          } else {
+            const float4 pm = w.B.pm[e], pd = w.B.pd[e];
+            w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], pm.w + acc[3]);
+            w.B.pd[e] = make_float4(pd.x + acc[4], pd.y + acc[5], pd.z + acc[6], 0.f);
+          }
         }
-    }
-    // write this window's partial sums
-    const int wn = min(TSCAP, total - w0);
-    if (pbase >= 0)
-      for (int j = tid; j < wn; j += BT) {
-        w.B.pm[(size_t)pbase + w0 + j] = make_float4(S.acc[0][j], S.acc[1][j], S.acc[2][j], S.acc[3][j]);
-        w.B.pd[(size_t)pbase + w0 + j] = make_float4(S.acc[4][j], S.acc[5][j], S.acc[6][j], 0.f);
       }
     __syncthreads();
   }
-  for (int t = tid; t < TN; t += BT) w.B.plo[(size_t)bt.y * TN + t] = S.T.lo[t];
 }
 
 // bricks whose tiles hold node coordinate i along one axis: [first, last]
@@ -740,7 +728,7 @@ __global__ void k_p2g_node(World w, LaunchSet ls) {
           const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
           const int pb = w.B.poff[b];
           if (pb < 0) continue;
-          const size_t e = (size_t)pb + w.B.plo[(size_t)b * TN + tt];
+          const size_t e = (size_t)pb + (w.B.tdesc[(size_t)b * TN + tt] & 0xffff);
           const float4 a = w.B.pm[e];
           const float4 d = w.B.pd[e];
           sm.x += a.x; sm.y += a.y; sm.z += a.z; sm.w += a.w;
@@ -771,7 +759,7 @@ __global__ void k_p2g_node(World w, LaunchSet ls) {
         const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
         const int pb = w.B.poff[b];
         if (pb < 0) continue;
-        const size_t e = (size_t)pb + w.B.plo[(size_t)b * TN + tt];
+        const size_t e = (size_t)pb + (w.B.tdesc[(size_t)b * TN + tt] & 0xffff);
         for (int a = 0; a < ns; ++a) {
           const float4 q = w.B.pm[e + a];
           const float4 d = w.B.pd[e + a];
@@ -806,10 +794,15 @@ template <int PPC>
 struct K4S {
   Tile T;
   uint2 codes[TSCAP];
-  float tv[7][TSCAP];  // v_old xyz, m, v_new xyz of the tile slots; then the MUSL sums
+  union {
+    float tv[7][TSCAP];       // v_old xyz, m, v_new xyz of the tile slots (G2P)
+    float stage[9 * 3][BT];   // then: per (cell, z-offset) MUSL sums for 9 nodes
+  };
   float pf[3][PPC * BR3];
   float pv[3][PPC * BR3];
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
+  uint2 ccode[BR3][PPC];
+  int ncode[BR3];
   int cs[BR3 + 1];
   int maxcodes;
 };
@@ -829,7 +822,7 @@ __global__ void __launch_bounds__(BT, 4) k_g2p_musl(World w, LaunchSet ls) {
   const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
   for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
   if (tid == 0) S.maxcodes = 0;
-  tile_load(w, sc, c0x, c0y, c0z, S.T);
+  tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
   const int total = S.T.total;
   const bool in_smem = total <= TSCAP;  // otherwise G2P reads the pool slots directly
   const uint2 *tcodes = in_smem ? S.codes : nullptr;
@@ -905,67 +898,88 @@ __global__ void __launch_bounds__(BT, 4) k_g2p_musl(World w, LaunchSet ls) {
     S.ps2[si] = s2;
   }
   if (bad) atomicOr(&scm.err, BM_ERRBIT_NONFINITE);
-  // ---- phase 1: MUSL sums per (cell, z-offset), in windows of tile slots ----
+  // ---- phase 1: MUSL sums m v^{n+1} N per (cell, z-offset), staged, then
+  // gathered by the tile nodes in a fixed order (as in k_p2g_brick) ----
   const int c = tid % BR3, oz = tid / BR3;
-  const int cx = c % BR, cy = (c / BR) % BR, cz = c / (BR * BR);
   const int n_c = S.cs[c + 1] - S.cs[c];
+  __syncthreads();  // G2P reads of the tile velocities are done: stage may reuse them
+  cell_codes<PPC>(S.ps1, S.ps2, S.cs, false, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
-  atomicMax(&S.maxcodes, cell_code_count(S.ps1, S.ps2, c, n_c));
+  const int iters = S.maxcodes > 0 ? S.maxcodes : 1;
   const int pbase = w.B.poff[bt.y];
-  for (int w0 = 0; w0 < total; w0 += TSCAP) {
-    __syncthreads();
-    for (int j = tid; j < 3 * TSCAP; j += BT) (&S.tv[0][0])[j] = 0.f;
-    __syncthreads();
-    const int iters = S.maxcodes;
-    for (int it = 0; it < iters; ++it) {
-      uint32_t k1 = 0, k2 = 0;
-      const bool has = cell_code(S.ps1, S.ps2, c, n_c, it, k1, k2);
-      float a[9][3];
+  for (int it = 0; it < iters; ++it) {
+    const bool has = it < S.ncode[c];
+    const uint32_t k1 = has ? S.ccode[c][it].x : 0u, k2 = has ? S.ccode[c][it].y : 0u;
+    const bool uniform = S.ncode[c] == 1;
+    float a[9][3];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) a[q][0] = a[q][1] = a[q][2] = 0.f;
-      if (has) {
-        for (int j = 0; j < n_c; ++j) {
-          const int si = j * BR3 + c;
-          if (S.ps1[si] != k1 || S.ps2[si] != k2) continue;
-          float wx[3], wy[3], wz, d;
-          const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
-          bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
-          bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
-          bs_rt(oz, f2, wz, d);
-          const float v0 = S.pv[0][si], v1 = S.pv[1][si], v2 = S.pv[2][si];
+    for (int q = 0; q < 9; ++q) a[q][0] = a[q][1] = a[q][2] = 0.f;
+    if (has) {
+      for (int j = 0; j < n_c; ++j) {
+        const int si = j * BR3 + c;
+        if (!uniform && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
+        float wx[3], wy[3], wz, d;
+        const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
+        bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
+        bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
+        bs_rt(oz, f2, wz, d);
+        const float v0 = S.pv[0][si], v1 = S.pv[1][si], v2 = S.pv[2][si];
 #pragma unroll
-          for (int oy = 0; oy < 3; ++oy) {
-            const float wyz = wy[oy] * wz;
+        for (int oy = 0; oy < 3; ++oy) {
+          const float wyz = wy[oy] * wz;
 #pragma unroll
-            for (int ox = 0; ox < 3; ++ox) {
-              const float N = wx[ox] * wyz;
-              a[oy * 3 + ox][0] += N * v0;
-              a[oy * 3 + ox][1] += N * v1;
-              a[oy * 3 + ox][2] += N * v2;
-            }
+          for (int ox = 0; ox < 3; ++ox) {
+            const float N = wx[ox] * wyz;
+            a[oy * 3 + ox][0] += N * v0;
+            a[oy * 3 + ox][1] += N * v1;
+            a[oy * 3 + ox][2] += N * v2;
           }
         }
       }
+    }
 #pragma unroll
-      for (int ozp = 0; ozp < 3; ++ozp)
+    for (int q = 0; q < 9; ++q)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          if (has && oz == ozp) {
-            const int t = ((cz + oz) * TE + (cy + q / 3)) * TE + (cx + q % 3);
-            const int s = tile_slot(w, S.T, tcodes, t, k1, k2) - w0;
-            if (s >= 0 && s < TSCAP) {
-              S.tv[0][s] += a[q][0];
-              S.tv[1][s] += a[q][1];
-              S.tv[2][s] += a[q][2];
+      for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][tid] = a[q][f];
+    __syncthreads();
+    if (pbase >= 0)
+      for (int t = tid; t < TN; t += BT) {
+        const int n = S.T.cnt[t];
+        if (n == 0) continue;
+        const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
+        const size_t e0 = (size_t)pbase + S.T.lo[t];
+        for (int sl = 0; sl < n; ++sl) {
+          const uint2 code = n > 1 ? w.S.code[S.T.goff[t] + sl] : make_uint2(0u, 0u);
+          float acc[3] = {0.f, 0.f, 0.f};
+          for (int ozz = 0; ozz < 3; ++ozz) {
+            const int zz = tz - ozz;
+            if (zz < 0 || zz >= BR) continue;
+            for (int oyy = 0; oyy < 3; ++oyy) {
+              const int yy = ty - oyy;
+              if (yy < 0 || yy >= BR) continue;
+              for (int oxx = 0; oxx < 3; ++oxx) {
+                const int xx = tx - oxx;
+                if (xx < 0 || xx >= BR) continue;
+                const int cc = (zz * BR + yy) * BR + xx;
+                if (it >= S.ncode[cc]) continue;
+                if (n > 1 && (S.ccode[cc][it].x != code.x || S.ccode[cc][it].y != code.y)) continue;
+                const int src = ozz * BR3 + cc, q = oyy * 3 + oxx;
+                acc[0] += S.stage[q * 3 + 0][src];
+                acc[1] += S.stage[q * 3 + 1][src];
+                acc[2] += S.stage[q * 3 + 2][src];
+              }
             }
           }
-          __syncthreads();
+          const size_t e = e0 + sl;
+          if (it == 0) {
+            w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], 0.f);
+          } else {
+            const float4 pm = w.B.pm[e];
+            w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], 0.f);
+          }
         }
-    }
-    const int wn = min(TSCAP, total - w0);
-    if (pbase >= 0)
-      for (int j = tid; j < wn; j += BT)
-        w.B.pm[(size_t)pbase + w0 + j] = make_float4(S.tv[0][j], S.tv[1][j], S.tv[2][j], 0.f);
+      }
+    __syncthreads();
   }
 }
 
@@ -996,7 +1010,7 @@ __global__ void k_musl_node(World w, LaunchSet ls) {
         const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
         const int pb = w.B.poff[b];
         if (pb < 0) continue;
-        const size_t e = (size_t)pb + w.B.plo[(size_t)b * TN + tt];
+        const size_t e = (size_t)pb + (w.B.tdesc[(size_t)b * TN + tt] & 0xffff);
         for (int a = 0; a < ns; ++a) {
           const float4 q = w.B.pm[e + a];
           S[a][0] += q.x;
@@ -1054,7 +1068,7 @@ __global__ void __launch_bounds__(BT, 3) k_fupd(World w, LaunchSet ls) {
   int c0x, c0y, c0z;
   brick_coords(sc, lb, c0x, c0y, c0z);
   if (tid == 0) S.any = 0;
-  tile_load(w, sc, c0x, c0y, c0z, S.T);
+  tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
   const bool in_smem = S.T.total <= TSCAP;
   const uint2 *tcodes = in_smem ? S.codes : nullptr;
   if (in_smem) {
@@ -1596,24 +1610,26 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   if (threadIdx.x == 0) w.N.tile_sum[t.w] = total;
 }
 
-// slots in each brick's node tile (after the per-node counts are final)
-__global__ void k_brick_tot(World w, LaunchSet ls, int force) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ls.n_btiles) return;
-  const int4 bt = ls.btiles[i];
+// per brick: slot count and first tile slot of each tile node, and the
+// tile's slot total (after the per-node counts are final)
+__global__ void k_brick_tiles(World w, LaunchSet ls, int force) {
+  const int4 bt = ls.btiles[blockIdx.x];
   const DevScene &sc = w.scenes[bt.x];
   if (!force && !sc.need_rebuild) return;
+  __shared__ int sm[33];
   int c0x, c0y, c0z;
   brick_coords(sc, bt.y - sc.brick_begin, c0x, c0y, c0z);
-  int tot = 0;
-  for (int tz = 0; tz < TE; ++tz)
-    for (int ty = 0; ty < TE; ++ty)
-      for (int tx = 0; tx < TE; ++tx) {
-        const int nx = c0x + tx, ny = c0y + ty, nz = c0z + tz;
-        if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2])
-          tot += w.N.slot_cnt[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
-      }
-  w.B.ptot[bt.y] = tot;
+  const int t = threadIdx.x;
+  int cnt = 0;
+  if (t < TN) {
+    const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
+    if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2])
+      cnt = w.N.slot_cnt[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
+  }
+  int total;
+  const int ex = block_excl_scan(cnt, sm, total);
+  if (t < TN) w.B.tdesc[(size_t)bt.y * TN + t] = ex | (cnt << 16);
+  if (t == 0) w.B.ptot[bt.y] = total;
 }
 
 // per scene: slot offsets of the node tiles, and partial-sum ranges of the bricks
@@ -1756,9 +1772,9 @@ cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t 
 
 const char *const bm_kernel_names[BM_NUM_KERNELS] = {
     "k_p2g_brick", "k_p2g_node", "k_g2p_musl", "k_musl_node", "k_fupd",
-    "k_tool", "k_slot_count", "k_slot_scan", "k_slot_fill", "k_brick_tot",
+    "k_tool", "k_slot_count", "k_slot_scan", "k_slot_fill", "k_brick_tiles",
     "k_pair_clear", "k_pair_hash", "k_scan_local", "k_scan_top", "k_scan_add", "k_pair_fill",
-    "k_pair_sort", "k_pair"};
+    "k_pair_sort", "k_pair", "k_pre"};
 
 // ev (optional): 2 * BM_NUM_KERNELS events recorded around each launch
 static inline void rec(cudaEvent_t *ev, int k, int after, cudaStream_t st) {
@@ -1772,7 +1788,7 @@ static cudaError_t launch_rebuild(const World &w, const LaunchSet &ls, cudaStrea
   k_slot_count<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
   rec(ev, 6, 1, st);
   rec(ev, 9, 0, st);
-  k_brick_tot<<<(ls.n_btiles + 127) / 128, 128, 0, st>>>(w, ls, force);
+  k_brick_tiles<<<ls.n_btiles, 256, 0, st>>>(w, ls, force);
   rec(ev, 9, 1, st);
   rec(ev, 7, 0, st);
   k_slot_scan<<<ls.n_scenes, 256, 0, st>>>(w, ls, force);
@@ -1812,6 +1828,9 @@ cudaError_t bm_kernels_init() {
 
 template <int PPC>
 static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
+  rec(ev, 18, 0, st);
+  k_pre<<<ls.n_btiles, 256, 0, st>>>(w, ls);
+  rec(ev, 18, 1, st);
   rec(ev, 0, 0, st);
   k_p2g_brick<PPC><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
   rec(ev, 0, 1, st);

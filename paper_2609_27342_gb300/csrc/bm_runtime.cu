@@ -197,7 +197,10 @@ int world_alloc(WorldH *W) {
     F(pp.ut[a], P);
     F(pp.J[a], P);
   }
-  for (int k = 0; k < 9; ++k) F(pp.F[k], P);
+  for (int k = 0; k < 9; ++k) {
+    F(pp.F[k], P);
+    F(pp.A[k], P);
+  }
   F(pp.D, P);
   U(pp.base, P);
   U(pp.s1, P);
@@ -239,10 +242,10 @@ int world_alloc(WorldH *W) {
   BPool &bp = W->w.B;
   bp.pm = W->get<float4>(W->cap_ppool);
   bp.pd = W->get<float4>(W->cap_ppool);
-  bp.plo = W->get<uint16_t>(W->cap_brick * BM_TILE_NODES);
   bp.poff = W->get<int>(W->cap_brick);
   bp.ptot = W->get<int>(W->cap_brick);
-  ok &= bp.pm && bp.pd && bp.plo && bp.poff && bp.ptot;
+  bp.tdesc = W->get<int>(W->cap_brick * BM_TILE_NODES);
+  ok &= bp.pm && bp.pd && bp.poff && bp.ptot && bp.tdesc;
   W->w.scenes = W->get<DevScene>(W->cap_scenes);
   W->w.wpart = W->get<double>(W->cap_brick * 6);
   W->w.whist = W->get<double>(std::max<int64_t>(W->cap_hist, 1) * 6);
@@ -1289,6 +1292,8 @@ int bm_batch_profile(bm_batch_t b, int n_substeps, double *ms, int *launches, in
       if (cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
         ms[k] += t;
         if (launches) launches[k] += 1;
+      } else {
+        cudaGetLastError();  // kernel not launched this substep (its events never recorded)
       }
     }
   }
