@@ -1057,7 +1057,7 @@ struct K1S {
   int any;
 };
 
-__global__ void __launch_bounds__(BT, 3) k_fupd(World w, LaunchSet ls) {
+__global__ void __launch_bounds__(BT, 5) k_fupd(World w, LaunchSet ls) {
   __shared__ K1S S;
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
@@ -1132,6 +1132,8 @@ __global__ void __launch_bounds__(BT, 3) k_fupd(World w, LaunchSet ls) {
       if (pend == 1) P.s1[p] = s1 | (1u << cut);
       else P.s2[p] = s2 | (1u << cut);
       any = true;
+      // the nodes of this particle's stencil need their codes recounted
+      w.N.dirty[sc.cell_begin + cell_index(sc, bx, by, bz)] = 1;
     }
   }
   if (any) S.any = 1;
@@ -1573,10 +1575,26 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   __shared__ int sm[33];
   const int i = threadIdx.x;
   int cnt = 0;
+  const int node = t.y + i;
+  int ix = 0, iy = 0, iz = 0;
+  bool recount = force != 0;
   if (i < t.z) {
-    const int node = t.y + i;
-    int ix, iy, iz;
     node_coords(sc, node - sc.node_begin, ix, iy, iz);
+    // only nodes whose neighbourhood holds a newly labelled particle are
+    // recounted; the others keep their distinct codes from the last rebuild
+    for (int oz = 0; oz < 3 && !recount; ++oz)
+      for (int oy = 0; oy < 3 && !recount; ++oy)
+        for (int ox = 0; ox < 3; ++ox) {
+          const int bx = ix - ox, by = iy - oy, bz = iz - oz;
+          if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) continue;
+          if (w.N.dirty[sc.cell_begin + cell_index(sc, bx, by, bz)]) {
+            recount = true;
+            break;
+          }
+        }
+  }
+  if (i < t.z && !recount) cnt = w.N.ncodes[node];
+  else if (i < t.z) {
     const int *cs = w.N.cell_start + sc.cell_begin;
     unsigned long long keys[BM_MAXS];
     bool over = false;
@@ -1601,10 +1619,11 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
           }
         }
     if (over) atomicOr(&sc.err, BM_ERRBIT_SLOT_OVERFLOW);
-    w.N.slot_cnt[node] = (uint8_t)cnt;
+    w.N.ncodes[node] = (uint8_t)cnt;
     for (int a = 0; a < cnt; ++a)
       w.N.tmp_codes[(size_t)node * BM_MAXS + a] = make_uint2((uint32_t)keys[a], (uint32_t)(keys[a] >> 32));
   }
+  if (i < t.z) w.N.slot_cnt[node] = (uint8_t)cnt;
   int total;
   block_excl_scan(cnt, sm, total);
   if (threadIdx.x == 0) w.N.tile_sum[t.w] = total;
@@ -1630,6 +1649,7 @@ __global__ void k_brick_tiles(World w, LaunchSet ls, int force) {
   const int ex = block_excl_scan(cnt, sm, total);
   if (t < TN) w.B.tdesc[(size_t)bt.y * TN + t] = ex | (cnt << 16);
   if (t == 0) w.B.ptot[bt.y] = total;
+  if (t < BR3) w.N.dirty[sc.cell_begin + (bt.y - sc.brick_begin) * BR3 + t] = 0;  // recounted
 }
 
 // per scene: slot offsets of the node tiles, and partial-sum ranges of the bricks
