@@ -305,6 +305,26 @@ def run_native(args):
     wall = time.perf_counter() - t0
     e2e_value = world * n_particles * e2e_steps / wall
 
+    # continuous-batching server on a Poisson request stream (rollouts of
+    # 8k-500k particles, 200-2000 substeps, 1-3 cuts), admission by an HBM budget
+    serving = None
+    if args.serve_requests > 0:
+        from paper_2609_27342_gb300.serving import Server
+        reqs = bi.serving_requests(n_requests=args.serve_requests, seed=3)
+        budget = int(args.serve_budget_gb * (1 << 30))
+        srv = Server(budget_bytes=budget, max_scenes=args.serve_requests, max_chunk=16,
+                     max_particles=sum(r.scene.n for r in reqs))
+        for r in reqs:
+            srv.submit(r.scene, r.n_substeps, arrival_s=r.arrival_s)
+        st = srv.run(realtime=True, timeout_s=600)
+        srv.close()
+        serving = {"requests": st["requests"], "rate_hz": 50, "budget_gb": args.serve_budget_gb,
+                   "throughput": st["throughput"], "unit": UNIT, "wall_s": st["wall_s"],
+                   "step_ms_p50": st["step_ms_p50"], "step_ms_p99": st["step_ms_p99"],
+                   "request_latency_s_p50": st["request_latency_s_p50"],
+                   "request_latency_s_p99": st["request_latency_s_p99"]}
+        log(f"serving: {serving}")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = scenes[:16]
@@ -337,6 +357,7 @@ def run_native(args):
                       "launches_per_substep_per_scene": LAUNCHES_PER_SUBSTEP},
             "batched_over_plain": (value / world / plain_rate) if plain_rate else None,
             "clocks": clk,
+            "serving": serving,
             "cpu_baseline": cpu,
             "error_bits": err_bits,
         }
@@ -395,6 +416,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -232,6 +232,12 @@ typedef struct {
 
 int bm_batch_create(const bm_batch_desc *desc, const bm_alloc *alloc, void *stream,
                     bm_batch_t *out);
+/* Create a scene (and its blade, when blade != NULL) directly inside the
+ * batch pools: the same initial state as bm_scene_create + bm_add_blade,
+ * without device allocations of its own.  BM_E_CAPACITY when the pools have
+ * no room (nothing is created).  Batch members keep no wrench history. */
+int bm_batch_scene_create(bm_batch_t b, const bm_scene_desc *desc, const bm_blade_desc *blade,
+                          const float *X_ref, int64_t n, bm_scene_t *out);
 /* Move a scene's device state into the batch pools (BM_E_CAPACITY if it
  * does not fit).  The scene's own buffers are released. */
 int bm_batch_add(bm_batch_t b, bm_scene_t s);

@@ -104,6 +104,8 @@ SIGNATURES = {
     "bm_scene_info_get": (C.c_int, [VP, C.POINTER(SceneInfo)]),
     "bm_scene_destroy": (C.c_int, [VP]),
     "bm_batch_create": (C.c_int, [C.POINTER(BatchDesc), C.POINTER(Alloc), VP, PVP]),
+    "bm_batch_scene_create": (C.c_int, [VP, C.POINTER(SceneDesc), C.POINTER(BladeDesc),
+                                        C.POINTER(C.c_float), C.c_int64, PVP]),
     "bm_batch_add": (C.c_int, [VP, VP]),
     "bm_batch_remove": (C.c_int, [VP, VP]),
     "bm_batch_step": (C.c_int, [VP, C.c_int]),

@@ -1191,6 +1191,45 @@ int bm_batch_create(const bm_batch_desc *desc, const bm_alloc *alloc, void *stre
   return BM_OK;
 }
 
+int bm_batch_scene_create(bm_batch_t b, const bm_scene_desc *desc, const bm_blade_desc *blade,
+                          const float *X_ref, int64_t n, bm_scene_t *out) {
+  if (!b || !out) return fail(BM_E_INVALID, "null batch or output handle");
+  *out = nullptr;
+  int rc = validate_desc(desc);
+  if (rc) return rc;
+  if (n <= 0 || !X_ref) return fail(BM_E_INVALID, "need at least one particle");
+  if (blade) {
+    if (blade->n_segments < 0 || blade->n_segments > BM_MAX_SEGMENTS) return fail(BM_E_INVALID, "too many segments");
+    for (int i = 0; i < blade->n_segments; ++i)
+      if (blade->segments[i].cut_id >= BM_MAX_CUTS || blade->segments[i].cut_id < -1)
+        return fail(BM_E_TOO_MANY_CUTS, "cut id outside [-1, 32)");
+  }
+  WorldH *W = b->world;
+  bm_scene_s *s = new bm_scene_s();
+  s->desc = *desc;
+  s->desc.wrench_history = 0;  // batch pools keep no per-substep wrench history
+  s->home_stream = W->st;
+  s->n = n;
+  s->X.assign(X_ref, X_ref + 3 * n);
+  if (blade) {
+    s->blade = *blade;
+    s->has_blade = true;
+  }
+  rc = build_layout(s);
+  if (!rc) {
+    fill_template(s);
+    rc = place_fresh(W, s);
+  }
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  rc = finish_placement(W, s);
+  if (rc) return rc;
+  *out = s;
+  return BM_OK;
+}
+
 int bm_batch_add(bm_batch_t b, bm_scene_t s) {
   if (!b || !valid_scene(s)) return fail(BM_E_INVALID, "bad batch or scene");
   if (s->world == b->world) return BM_OK;

@@ -1,0 +1,175 @@
+"""Continuous-batching server for cutting rollouts.
+
+Requests (a scene and a substep count) arrive over time.  Every admitted
+scene lives in one device batch (packed pools) and is advanced with all other
+admitted scenes by CUDA-graph launches; a request that arrives while others
+run is admitted as soon as the HBM budget and the pools have room, between
+chunks of substeps, so its work overlaps with theirs on the device.  Finished
+scenes are read back and their pool ranges freed immediately.
+
+Because every sum in the substep is taken in a fixed order, a scene's result
+does not depend on which other scenes share the batch: a rollout served in a
+mix is bit-identical to the same rollout run alone.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import _abi as A
+from .sim import Batch, Scene, footprint
+
+
+@dataclasses.dataclass
+class Result:
+    request_id: int
+    n_particles: int
+    n_substeps: int
+    arrival_s: float
+    admitted_s: float
+    finished_s: float
+    x: np.ndarray          # final positions (caller order)
+    wrench: np.ndarray     # interval-averaged reaction wrench of the last substep
+    error_bits: int
+
+    @property
+    def latency_s(self) -> float:
+        return self.finished_s - self.arrival_s
+
+
+@dataclasses.dataclass
+class _Active:
+    rid: int
+    scene: Scene
+    remaining: int
+    total: int
+    bytes: int
+    arrival_s: float
+    admitted_s: float
+
+
+class Server:
+    """HBM-budgeted continuous batching over one GPU.
+
+    ``budget_bytes`` bounds the device memory of admitted scenes (footprints
+    from bm_scene_footprint); the batch pools are sized from it once.
+    ``max_chunk`` bounds the substeps run between admission points.
+    """
+
+    # pool capacity per budget byte (particles, nodes): a scene's footprint is
+    # roughly 190 B per particle and its node count under half its particles
+    BYTES_PER_PARTICLE = 190
+
+    def __init__(self, budget_bytes: int, max_scenes: int = 256, max_chunk: int = 16,
+                 stream=None, max_particles: Optional[int] = None):
+        import torch
+        self._torch = torch
+        self.budget = int(budget_bytes)
+        cap_p = int(max_particles or self.budget // self.BYTES_PER_PARTICLE)
+        cap_n = cap_p // 2 + 27 * max_scenes
+        self.stream = stream or torch.cuda.Stream()
+        self.batch = Batch(max_particles=cap_p, max_nodes=cap_n, max_scenes=max_scenes,
+                           graph_chunk=max_chunk, stream=self.stream)
+        self.max_chunk = max_chunk
+        self.queue: List[tuple] = []
+        self.active: List[_Active] = []
+        self.used = 0
+        self.results: Dict[int, Result] = {}
+        self.step_ms: List[float] = []      # ms per batched substep, one sample per chunk
+        self.step_weight: List[int] = []    # substeps in that chunk
+        self.particle_substeps = 0
+        self._next_id = 0
+
+    # -- requests ----------------------------------------------------------
+    def submit(self, scene, n_substeps: int, arrival_s: float = 0.0) -> int:
+        rid = self._next_id
+        self._next_id += 1
+        self.queue.append((arrival_s, rid, scene, int(n_substeps)))
+        self.queue.sort(key=lambda t: (t[0], t[1]))
+        return rid
+
+    def _admit(self, now: float) -> None:
+        while self.queue and self.queue[0][0] <= now:
+            arrival, rid, sc, n = self.queue[0]
+            nbytes = footprint(sc)[3]
+            if self.used + nbytes > self.budget:
+                return
+            try:
+                s = Scene.in_batch(self.batch, sc)
+            except A.BMError as e:
+                if e.code == A.E_CAPACITY:
+                    return
+                raise
+            self.queue.pop(0)
+            self.used += nbytes
+            self.active.append(_Active(rid, s, n, n, nbytes, arrival, now))
+
+    def _retire(self, now: float) -> None:
+        keep = []
+        for a in self.active:
+            if a.remaining > 0:
+                keep.append(a)
+                continue
+            # the no-allocation read keeps cudaMalloc/cudaFree (which would stall
+            # the other scenes' work) out of the serving loop
+            r = a.scene.read_noalloc("x") if a.scene.n * 12 <= (16 << 20) else a.scene.read("x")
+            info = a.scene.info()
+            self.results[a.rid] = Result(a.rid, a.scene.n, a.total, a.arrival_s, a.admitted_s, now,
+                                         r["x"], a.scene.tool_wrench() if a.scene.spec.blade else
+                                         np.zeros(6), int(info.error_bits))
+            a.scene.close()
+            self.used -= a.bytes
+        self.active = keep
+
+    # -- main loop -----------------------------------------------------------
+    def run(self, realtime: bool = True, timeout_s: float = 3600.0) -> dict:
+        """Serve until every submitted request has finished.  With realtime
+        the arrival times are honoured against the wall clock; otherwise every
+        request counts as already arrived."""
+        torch = self._torch
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        while self.queue or self.active:
+            now = time.perf_counter() - t0
+            if now > timeout_s:
+                raise TimeoutError("serving loop exceeded its time limit")
+            self._admit(now if realtime else float("inf"))
+            if not self.active:
+                if self.queue and realtime:
+                    time.sleep(max(0.0, min(0.05, self.queue[0][0] - now)))
+                    continue
+                if self.queue:
+                    raise RuntimeError("a request does not fit the budget or the pools")
+                break
+            k = min(self.max_chunk, min(a.remaining for a in self.active))
+            e0.record(self.stream)
+            self.batch.step(k)
+            e1.record(self.stream)
+            e1.synchronize()
+            self.step_ms.append(e0.elapsed_time(e1) / k)
+            self.step_weight.append(k)
+            self.particle_substeps += k * sum(a.scene.n for a in self.active)
+            for a in self.active:
+                a.remaining -= k
+            self._retire(time.perf_counter() - t0)
+        wall = time.perf_counter() - t0
+        return self.stats(wall)
+
+    def stats(self, wall_s: float) -> dict:
+        ms = np.repeat(np.array(self.step_ms), np.array(self.step_weight)) if self.step_ms else \
+            np.zeros(1)
+        lat = np.array([r.latency_s for r in self.results.values()]) if self.results else np.zeros(1)
+        return {"requests": len(self.results), "wall_s": wall_s,
+                "throughput": self.particle_substeps / wall_s if wall_s > 0 else 0.0,
+                "step_ms_p50": float(np.percentile(ms, 50)),
+                "step_ms_p99": float(np.percentile(ms, 99)),
+                "request_latency_s_p50": float(np.percentile(lat, 50)),
+                "request_latency_s_p99": float(np.percentile(lat, 99)),
+                "particle_substeps": self.particle_substeps}
+
+    def close(self):
+        self.batch.close()

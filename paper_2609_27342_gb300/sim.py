@@ -111,6 +111,28 @@ class Scene:
             bid = C.c_int()
             A.check(self._L.bm_add_blade(self._h, C.byref(self._blade), C.byref(bid)))
 
+    @classmethod
+    def in_batch(cls, batch: "Batch", sc) -> "Scene":
+        """Create the scene directly inside ``batch``'s pools (no device
+        allocation of its own); raises BMError(E_CAPACITY) when it does not fit."""
+        self = cls.__new__(cls)
+        self._L = A.load()
+        X = np.ascontiguousarray(np.asarray(sc.X, dtype=np.float32))
+        self.n = int(X.shape[0])
+        self.spec = sc
+        self._alloc = None
+        self._desc = scene_desc(sc, 0)
+        self._blade = blade_desc(sc.blade) if sc.blade is not None else None
+        h = C.c_void_p()
+        A.check(self._L.bm_batch_scene_create(
+            batch._h, C.byref(self._desc),
+            C.byref(self._blade) if self._blade is not None else None,
+            X.ctypes.data_as(C.POINTER(C.c_float)), self.n, C.byref(h)))
+        self._h = h
+        self.batch = batch
+        batch.scenes.append(self)
+        return self
+
     @property
     def handle(self):
         return self._h
@@ -119,6 +141,10 @@ class Scene:
         if getattr(self, "_h", None) is not None and self._h.value:
             self._L.bm_scene_destroy(self._h)
             self._h = None
+        b = getattr(self, "batch", None)
+        if b is not None and self in b.scenes:
+            b.scenes.remove(self)
+        self.batch = None
 
     def __del__(self):
         try:
@@ -293,7 +319,7 @@ class Batch:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            for s in self.scenes:
+            for s in list(self.scenes):
                 s.close()
             self.scenes = []
             self._L.bm_batch_destroy(self._h)
