@@ -294,8 +294,10 @@ def batched_scenes(n_scenes: int = 256, seed: int = 2, n_min: int = 4096,
                       half_length=float(max(size)),
                       pose_x=tuple(float(t) for t in edge0), pose_R=tuple(float(t) for t in R.ravel()),
                       segments=[Segment(n_substeps, v=tuple(float(t) for t in speed * d), cut_id=0)])
-        out.append(Scene(X=X, E=E, nu=nu, rho=rho, dx=dx, V0=dx ** 3 / 8, dt=dt,
-                         blade=blade, name=f"batch{i}"))
+        # reference grid offset by half a cell: each base cell (Eq. 1 stencil
+        # origin) then holds exactly one lattice cell's 2 x 2 x 2 particles
+        out.append(Scene(X=X, E=E, nu=nu, rho=rho, dx=dx, origin=(-dx / 2,) * 3,
+                         V0=dx ** 3 / 8, dt=dt, blade=blade, name=f"batch{i}"))
     return out
 
 
@@ -340,8 +342,8 @@ def serving_requests(n_requests: int = 64, rate_hz: float = 50.0, seed: int = 3,
         blade = Blade(pose_x=(size[0] / 2, size[1] / 2, size[2] + 0.002),
                       half_length=float(max(size)), segments=segs)
         out.append(Request(arrival_s=t, scene=Scene(X=X, E=E, nu=nu, rho=rho, dx=dx,
-                                                     V0=dx ** 3 / 8, dt=dt, blade=blade,
-                                                     name=f"req{i}"),
+                                                     origin=(-dx / 2,) * 3, V0=dx ** 3 / 8,
+                                                     dt=dt, blade=blade, name=f"req{i}"),
                            n_substeps=n_steps))
     return out
 

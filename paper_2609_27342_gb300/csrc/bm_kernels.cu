@@ -660,15 +660,13 @@ __global__ void __launch_bounds__(BT, 3) k_p2g_brick(World w, LaunchSet ls) {
         for (int sl = 0; sl < n; ++sl) {
           const uint2 code = n > 1 ? w.S.code[S.T.goff[t] + sl] : make_uint2(0u, 0u);
           float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int ozz = 0; ozz < 3; ++ozz) {
+          // offsets o with 0 <= t - o < 4 on every axis, in ascending order
+          for (int ozz = max(0, tz - (BR - 1)); ozz <= min(2, tz); ++ozz) {
             const int zz = tz - ozz;
-            if (zz < 0 || zz >= BR) continue;
-            for (int oyy = 0; oyy < 3; ++oyy) {
+            for (int oyy = max(0, ty - (BR - 1)); oyy <= min(2, ty); ++oyy) {
               const int yy = ty - oyy;
-              if (yy < 0 || yy >= BR) continue;
-              for (int oxx = 0; oxx < 3; ++oxx) {
+              for (int oxx = max(0, tx - (BR - 1)); oxx <= min(2, tx); ++oxx) {
                 const int xx = tx - oxx;
-                if (xx < 0 || xx >= BR) continue;
                 const int cc = (zz * BR + yy) * BR + xx;
                 if (it >= S.ncode[cc]) continue;
                 if (n > 1 && (S.ccode[cc][it].x != code.x || S.ccode[cc][it].y != code.y)) continue;
@@ -951,15 +949,12 @@ __global__ void __launch_bounds__(BT, 4) k_g2p_musl(World w, LaunchSet ls) {
         for (int sl = 0; sl < n; ++sl) {
           const uint2 code = n > 1 ? w.S.code[S.T.goff[t] + sl] : make_uint2(0u, 0u);
           float acc[3] = {0.f, 0.f, 0.f};
-          for (int ozz = 0; ozz < 3; ++ozz) {
+          for (int ozz = max(0, tz - (BR - 1)); ozz <= min(2, tz); ++ozz) {
             const int zz = tz - ozz;
-            if (zz < 0 || zz >= BR) continue;
-            for (int oyy = 0; oyy < 3; ++oyy) {
+            for (int oyy = max(0, ty - (BR - 1)); oyy <= min(2, ty); ++oyy) {
               const int yy = ty - oyy;
-              if (yy < 0 || yy >= BR) continue;
-              for (int oxx = 0; oxx < 3; ++oxx) {
+              for (int oxx = max(0, tx - (BR - 1)); oxx <= min(2, tx); ++oxx) {
                 const int xx = tx - oxx;
-                if (xx < 0 || xx >= BR) continue;
                 const int cc = (zz * BR + yy) * BR + xx;
                 if (it >= S.ncode[cc]) continue;
                 if (n > 1 && (S.ccode[cc][it].x != code.x || S.ccode[cc][it].y != code.y)) continue;
