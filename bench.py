@@ -220,11 +220,34 @@ def run_native(args):
         plain_rate = n_particles * plain_steps / (plain_ms * 1e-3)
         log(f"plain path: {plain_rate:.3e} p-s/s ({plain_ms:.1f} ms for {plain_steps} substeps)")
 
-    batch = pkg.Batch(max_particles=n_particles, max_nodes=sum(nodes), max_scenes=N_SCENES,
-                      max_bricks=n_bricks, graph_chunk=args.chunk, node_tile=args.ntile,
-                      stream=stream)
-    for o in plain_objs:
-        batch.add(o)
+    def make_batch(members):
+        b = pkg.Batch(max_particles=n_particles, max_nodes=sum(nodes), max_scenes=N_SCENES,
+                      max_bricks=n_bricks, stream=stream)
+        for o in members:
+            b.add(o)
+        return b
+
+    # launch shape: autotuned (untimed) on a throwaway copy of the workload, so
+    # that the timed substeps start from the scenes' initial state, unless
+    # given on the command line
+    if args.chunk and args.ntile and args.variant is not None:
+        shape = {"graph_chunk": args.chunk, "node_tile": args.ntile,
+                 "brick_variant": args.variant, "autotuned": False}
+    else:
+        from paper_2609_27342_gb300.autotune import autotune
+        probe = [pkg.Scene(s, stream=stream) for s in scenes]
+        tb = make_batch(probe)
+        tuned = autotune(tb, stream)
+        tb.close()
+        for o in probe:
+            o.close()
+        del probe, tb
+        shape = dict(tuned["best"], autotuned=True, candidates=len(tuned["trials"]))
+        for t in tuned["trials"]:
+            log(f"  autotune trial {t}")
+        log(f"autotune: {tuned['best']}")
+    batch = make_batch(plain_objs)
+    batch.set_tiles(shape["graph_chunk"], shape["node_tile"], shape["brick_variant"])
     # warm-up (also captures the graphs)
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -313,7 +336,8 @@ def run_native(args):
         reqs = bi.serving_requests(n_requests=args.serve_requests, seed=3)
         budget = int(args.serve_budget_gb * (1 << 30))
         srv = Server(budget_bytes=budget, max_scenes=args.serve_requests, max_chunk=16,
-                     max_particles=sum(r.scene.n for r in reqs))
+                     max_particles=sum(r.scene.n for r in reqs), node_tile=shape["node_tile"],
+                     brick_variant=shape["brick_variant"])
         for r in reqs:
             srv.submit(r.scene, r.n_substeps, arrival_s=r.arrival_s)
         st = srv.run(realtime=True, timeout_s=600)
@@ -342,7 +366,7 @@ def run_native(args):
             "config": {"workload": WORKLOAD, "scenes": N_SCENES, "particles": n_particles,
                        "nodes": n_nodes, "slots": n_slots, "seed": SEED,
                        "bricks": n_bricks, "substeps_timed": args.steps,
-                       "graph_chunk": args.chunk, "node_tile": args.ntile,
+                       "launch_shape": shape,
                        "parallelism": f"scene-sharded x{world} (each rank its own batch)",
                        "l2": "inputs larger than L2 (state ~1.2 GB vs 129 MB L2)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 18 * 8,
@@ -408,11 +432,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--chunk", type=int, default=16)
-    ap.add_argument("--ntile", type=int, default=128)
+    ap.add_argument("--chunk", type=int, default=0, help="fix the graph chunk (with --ntile, "
+                    "--variant; otherwise the launch shape is autotuned)")
+    ap.add_argument("--ntile", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=None)
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -269,11 +269,16 @@ int bm_batch_errors(bm_batch_t b, uint32_t *bits);
  * a bm_status.  Advances the simulation like bm_batch_step. */
 int bm_batch_profile(bm_batch_t b, int n_substeps, double *ms, int *launches, int cap);
 const char *bm_kernel_name(int i);
-/* Launch shape used by subsequent bm_batch_step calls (autotuner hook):
- * substeps per captured CUDA graph (1..256) and nodes per CTA of the
- * per-node kernels (multiple of 32 in 64..512).  Results do not depend on
- * either: every sum is taken in a fixed order. */
-int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile);
+/* Launch shape used by subsequent bm_batch_step calls (set by the
+ * autotuner): substeps per captured CUDA graph (1..256), nodes per CTA of the
+ * per-node kernels (multiple of 32 in 64..512) and the brick-kernel
+ * occupancy variant (0: 3/4/5 resident CTAs per SM for P2G, G2P+MUSL and the
+ * F update; 1: 2/3/4, more registers per thread; 2: 4/5/6).  Results do not
+ * depend on any of them: every sum is taken in a fixed order and the
+ * variants share their arithmetic.  Synchronises the batch stream; captured
+ * graphs are rebuilt on the next step.  BM_E_INVALID on an out-of-range
+ * argument (the previous shape stays). */
+int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile, int brick_variant);
 int bm_batch_destroy(bm_batch_t b);
 
 const char *bm_last_error(void);

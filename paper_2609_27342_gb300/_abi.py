@@ -116,7 +116,7 @@ SIGNATURES = {
     "bm_batch_tool_wrenches": (C.c_int, [VP, PD, C.c_int, C.c_int]),
     "bm_batch_members": (C.c_int, [VP, PVP, C.c_int]),
     "bm_batch_errors": (C.c_int, [VP, C.POINTER(C.c_uint32)]),
-    "bm_batch_set_tiles": (C.c_int, [VP, C.c_int, C.c_int]),
+    "bm_batch_set_tiles": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
     "bm_batch_destroy": (C.c_int, [VP]),
     "bm_batch_profile": (C.c_int, [VP, C.c_int, PD, C.POINTER(C.c_int), C.c_int]),
     "bm_kernel_name": (C.c_char_p, [C.c_int]),

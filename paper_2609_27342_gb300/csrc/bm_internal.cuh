@@ -152,6 +152,7 @@ struct LaunchSet {
   const int4 *ntiles;
   int n_ntiles;
   int ntile_size;
+  int variant;              // brick-kernel occupancy variant, 0..BM_NUM_VARIANTS-1
   const int *scene_ids;     // scenes in this set
   int n_scenes;
   int any_pair;             // some scene has pair contact
@@ -160,6 +161,7 @@ struct LaunchSet {
 
 // kernel launchers (bm_kernels.cu)
 #define BM_NUM_KERNELS 19
+#define BM_NUM_VARIANTS 3
 extern const char *const bm_kernel_names[BM_NUM_KERNELS];
 cudaError_t bm_kernels_init();  // per device: shared-memory limits of the brick kernels
 cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st);

@@ -573,8 +573,8 @@ __device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s
   atomicMax(maxcodes, cnt);
 }
 
-template <int PPC>
-__global__ void __launch_bounds__(BT, 3) k_p2g_brick(World w, LaunchSet ls) {
+template <int PPC, int MB>
+__global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K2S<PPC> &S = *reinterpret_cast<K2S<PPC> *>(smraw);
   const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
@@ -805,8 +805,8 @@ struct K4S {
   int maxcodes;
 };
 
-template <int PPC>
-__global__ void __launch_bounds__(BT, 4) k_g2p_musl(World w, LaunchSet ls) {
+template <int PPC, int MB>
+__global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K4S<PPC> &S = *reinterpret_cast<K4S<PPC> *>(smraw);
   const int4 bt = ls.btiles[blockIdx.x];
@@ -1052,7 +1052,8 @@ struct K1S {
   int any;
 };
 
-__global__ void __launch_bounds__(BT, 5) k_fupd(World w, LaunchSet ls) {
+template <int MB>
+__global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
   __shared__ K1S S;
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
@@ -1818,13 +1819,23 @@ cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t 
   return launch_rebuild(w, ls, st, force, nullptr);
 }
 
-template <int PPC>
+// Brick-kernel occupancy variants (minimum resident CTAs per SM of
+// k_p2g_brick, k_g2p_musl, k_fupd): fewer CTAs leave more registers per
+// thread, more CTAs hide more latency.  The arithmetic is the same in every
+// variant, so results are bit-identical; the batch autotuner picks one.
+template <int V> struct Occ;
+template <> struct Occ<0> { static constexpr int p2g = 3, g2p = 4, fupd = 5; };
+template <> struct Occ<1> { static constexpr int p2g = 2, g2p = 3, fupd = 4; };
+template <> struct Occ<2> { static constexpr int p2g = 4, g2p = 5, fupd = 6; };
+
+template <int PPC, int V>
 static cudaError_t set_smem_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC, Occ<V>::p2g>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(K2S<PPC>));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_g2p_musl<PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(K4S<PPC>));
+  return cudaFuncSetAttribute(k_g2p_musl<PPC, Occ<V>::g2p>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K4S<PPC>));
 }
 
 cudaError_t bm_kernels_init() {
@@ -1834,32 +1845,36 @@ cudaError_t bm_kernels_init() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (device == dev && status == cudaSuccess) return status;
-  e = set_smem_attrs<8>();
-  if (e == cudaSuccess) e = set_smem_attrs<16>();
+  if (e == cudaSuccess) e = set_smem_attrs<8, 0>();
+  if (e == cudaSuccess) e = set_smem_attrs<8, 1>();
+  if (e == cudaSuccess) e = set_smem_attrs<8, 2>();
+  if (e == cudaSuccess) e = set_smem_attrs<16, 0>();
+  if (e == cudaSuccess) e = set_smem_attrs<16, 1>();
+  if (e == cudaSuccess) e = set_smem_attrs<16, 2>();
   status = e;
   device = dev;
   return e;
 }
 
-template <int PPC>
+template <int PPC, int V>
 static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   rec(ev, 18, 0, st);
   k_pre<<<ls.n_btiles, 256, 0, st>>>(w, ls);
   rec(ev, 18, 1, st);
   rec(ev, 0, 0, st);
-  k_p2g_brick<PPC><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+  k_p2g_brick<PPC, Occ<V>::p2g><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
   rec(ev, 0, 1, st);
   rec(ev, 1, 0, st);
   k_p2g_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 1, 1, st);
   rec(ev, 2, 0, st);
-  k_g2p_musl<PPC><<<ls.n_btiles, BT, sizeof(K4S<PPC>), st>>>(w, ls);
+  k_g2p_musl<PPC, Occ<V>::g2p><<<ls.n_btiles, BT, sizeof(K4S<PPC>), st>>>(w, ls);
   rec(ev, 2, 1, st);
   rec(ev, 3, 0, st);
   k_musl_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 3, 1, st);
   rec(ev, 4, 0, st);
-  k_fupd<<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  k_fupd<Occ<V>::fupd><<<ls.n_btiles, BT, 0, st>>>(w, ls);
   rec(ev, 4, 1, st);
 }
 
@@ -1896,8 +1911,14 @@ static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, c
 cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   if (ls.n_btiles == 0) return cudaSuccess;
   if (ls.any_pair && w.H.n_buckets > 0) launch_pairs(w, ls, st, ev);
-  if (ls.ppc16) launch_bricks<16>(w, ls, st, ev);
-  else launch_bricks<8>(w, ls, st, ev);
+  switch (ls.variant * 2 + (ls.ppc16 ? 1 : 0)) {
+    case 0: launch_bricks<8, 0>(w, ls, st, ev); break;
+    case 1: launch_bricks<16, 0>(w, ls, st, ev); break;
+    case 2: launch_bricks<8, 1>(w, ls, st, ev); break;
+    case 3: launch_bricks<16, 1>(w, ls, st, ev); break;
+    case 4: launch_bricks<8, 2>(w, ls, st, ev); break;
+    default: launch_bricks<16, 2>(w, ls, st, ev); break;
+  }
   rec(ev, 5, 0, st);
   k_tool<<<ls.n_scenes, 256, 0, st>>>(w, ls);
   rec(ev, 5, 1, st);

@@ -142,6 +142,7 @@ struct WorldH {
   int *d_scene_ids = nullptr, *d_slot_ids = nullptr;
   double *d_stage = nullptr;
   int ntile_size = 128;
+  int variant = 0;          // brick-kernel occupancy variant
   int graph_chunk = 16;
   std::vector<bm_scene_s *> members;
   bool tiles_dirty = true;
@@ -330,6 +331,7 @@ LaunchSet scene_set(const WorldH *W, const bm_scene_s *s) {
   ls.ntiles = W->d_ntiles + s->ntile_begin;
   ls.n_ntiles = s->n_ntile;
   ls.ntile_size = W->ntile_size;
+  ls.variant = W->variant;
   ls.scene_ids = W->d_slot_ids + s->slot;
   ls.n_scenes = 1;
   ls.any_pair = s->desc.pair_contact;
@@ -343,6 +345,7 @@ LaunchSet world_set(const WorldH *W) {
   ls.ntiles = W->d_ntiles;
   ls.n_ntiles = W->n_ntiles;
   ls.ntile_size = W->ntile_size;
+  ls.variant = W->variant;
   ls.scene_ids = W->d_scene_ids;
   ls.n_scenes = (int)W->members.size();
   for (auto *s : W->members) {
@@ -1244,14 +1247,17 @@ int bm_batch_remove(bm_batch_t b, bm_scene_t s) {
   return BM_OK;
 }
 
-int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile) {
+int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile, int brick_variant) {
   if (!b) return fail(BM_E_INVALID, "bad batch");
-  if (graph_chunk < 1 || graph_chunk > 256 || node_tile < 64 || node_tile > 512 || node_tile % 32)
-    return fail(BM_E_INVALID, "graph chunk in [1, 256]; node tile a multiple of 32 in [64, 512]");
+  if (graph_chunk < 1 || graph_chunk > 256 || node_tile < 64 || node_tile > 512 || node_tile % 32 ||
+      brick_variant < 0 || brick_variant >= BM_NUM_VARIANTS)
+    return fail(BM_E_INVALID, "graph chunk in [1, 256]; node tile a multiple of 32 in [64, 512]; "
+                              "brick variant in [0, 2]");
   WorldH *W = b->world;
   CK(cudaStreamSynchronize(W->st));
   W->graph_chunk = graph_chunk;
   W->ntile_size = node_tile;
+  W->variant = brick_variant;
   W->tiles_dirty = true;
   return rebuild_tiles(W);
 }

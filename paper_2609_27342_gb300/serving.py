@@ -56,7 +56,9 @@ class Server:
 
     ``budget_bytes`` bounds the device memory of admitted scenes (footprints
     from bm_scene_footprint); the batch pools are sized from it once.
-    ``max_chunk`` bounds the substeps run between admission points.
+    ``max_chunk`` bounds the substeps run between admission points;
+    ``node_tile`` and ``brick_variant`` are the launch shape (for instance an
+    autotuned one; results do not depend on it).
     """
 
     # pool capacity per budget byte (particles, nodes): a scene's footprint is
@@ -64,7 +66,8 @@ class Server:
     BYTES_PER_PARTICLE = 190
 
     def __init__(self, budget_bytes: int, max_scenes: int = 256, max_chunk: int = 16,
-                 stream=None, max_particles: Optional[int] = None):
+                 stream=None, max_particles: Optional[int] = None, node_tile: int = 128,
+                 brick_variant: int = 0):
         import torch
         self._torch = torch
         self.budget = int(budget_bytes)
@@ -73,6 +76,7 @@ class Server:
         self.stream = stream or torch.cuda.Stream()
         self.batch = Batch(max_particles=cap_p, max_nodes=cap_n, max_scenes=max_scenes,
                            graph_chunk=max_chunk, stream=self.stream)
+        self.batch.set_tiles(max_chunk, node_tile, brick_variant)
         self.max_chunk = max_chunk
         self.queue: List[tuple] = []
         self.active: List[_Active] = []

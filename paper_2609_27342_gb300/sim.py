@@ -280,8 +280,11 @@ class Batch:
     def step(self, n: int = 1) -> None:
         A.check(self._L.bm_batch_step(self._h, int(n)))
 
-    def set_tiles(self, graph_chunk: int, node_tile: int) -> None:
-        A.check(self._L.bm_batch_set_tiles(self._h, int(graph_chunk), int(node_tile)))
+    def set_tiles(self, graph_chunk: int, node_tile: int, brick_variant: int = 0) -> None:
+        """Launch shape of later steps; see bm_batch_set_tiles (results do not
+        depend on it)."""
+        A.check(self._L.bm_batch_set_tiles(self._h, int(graph_chunk), int(node_tile),
+                                           int(brick_variant)))
 
     def members(self) -> list:
         n = self._L.bm_batch_members(self._h, None, 0)

@@ -202,18 +202,54 @@ def test_batched_equals_plain_bitwise(pkg):
     for p in plain:
         p.step(24)
     ref = [p.read("x", "v", "F", "mask1", "mask2") for p in plain]
-    for chunk, ntile in [(8, 128), (3, 64), (16, 256)]:
+    for chunk, ntile, variant in [(8, 128, 0), (3, 64, 1), (16, 256, 2), (5, 96, 1)]:
         b = pkg.Batch(max_particles=sum(s.n for s in scenes) + 1000, max_nodes=200000,
                       max_scenes=8, graph_chunk=chunk, node_tile=ntile)
+        b.set_tiles(chunk, ntile, variant)
         gs = [pkg.Scene(s) for s in scenes]
         for s in gs:
             b.add(s)
-        b.step(24)
+        b.step(10)
+        # a change of launch shape between steps keeps the trajectory
+        b.set_tiles(max(1, chunk // 2), 512 - ntile, (variant + 1) % 3)
+        b.step(14)
         for s, r in zip(gs, ref):
             got = s.read("x", "v", "F", "mask1", "mask2")
             for k in r:
-                assert np.array_equal(got[k], r[k]), (chunk, ntile, k)
+                assert np.array_equal(got[k], r[k]), (chunk, ntile, variant, k)
         b.close()
+
+
+def test_autotune_keeps_the_trajectory(pkg):
+    """The autotuner times real launch shapes on the batch and applies the
+    fastest; the probes are ordinary substeps, so the scenes end where plain
+    runs of the same length end, bit for bit."""
+    import torch
+    from paper_2609_27342_gb300.autotune import autotune
+    scenes = [_touching_block(size=(0.04, 0.02, 0.02)),
+              bi.single_cut_cuboid(size=(0.05, 0.02, 0.025), edge_z0=0.026, speed=0.8)]
+    st = torch.cuda.Stream()
+    b = pkg.Batch(max_particles=sum(s.n for s in scenes) + 1000, max_nodes=200000, max_scenes=4,
+                  stream=st)
+    gs = [pkg.Scene(s, stream=st) for s in scenes]
+    for s in gs:
+        b.add(s)
+    r = autotune(b, st, substeps=2, rounds=1, variants=(0, 2), node_tiles=(64, 256),
+                 graph_chunks=(2, 16), baseline=(4, 128, 0))
+    shapes = {(t["graph_chunk"], t["node_tile"], t["brick_variant"]) for t in r["trials"]}
+    # the baseline, the 2 x 2 grid at a 16-substep graph, then the winner's
+    # other graph chunks (one more shape when the baseline itself won the grid)
+    assert len(shapes) == len(r["trials"]) in (6, 7)
+    assert r["best"]["relative_to_baseline"] == min(t["relative"] for t in r["trials"])
+    assert all(t["ms"] > 0 for t in r["trials"])
+    b.step(3)
+    n = r["substeps_advanced"] + 3
+    for s, sc in zip(gs, scenes):
+        p = pkg.Scene(sc)
+        p.step(n)
+        assert np.array_equal(s.read("x")["x"], p.read("x")["x"])
+        p.close()
+    b.close()
 
 
 def test_batch_remove_keeps_state(pkg):

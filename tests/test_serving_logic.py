@@ -28,6 +28,9 @@ class FakeBatch:
     def step(self, n):
         self.steps.append(n)
 
+    def set_tiles(self, chunk, ntile, variant):
+        self.shape = (chunk, ntile, variant)
+
     def close(self):
         pass
 
