@@ -1095,3 +1095,530 @@ void or_momentum(const or_scene *s, double out[3]) {
   for (int64_t p = 0; p < s->n; ++p)
     for (int a = 0; a < 3; ++a) out[a] += s->mp * s->v[3 * p + a];
 }
+
+/* ======================================================================== */
+/* Adjoint of one substep (reverse mode), for calibration of E, nu and the  */
+/* blade velocity from reaction-force trajectories.                         */
+/*                                                                          */
+/* The substep is differentiated with every discrete decision of the       */
+/* forward substep held fixed: the codes (side labels), the contact active  */
+/* sets (Jn > 0 for the blade and the floor), the sign test of the normal   */
+/* velocity in phi_hat, stick or slip (Eq. 12), the front band and the D    */
+/* release (Eq. 5), and the face / clamp pattern of the box closest point.  */
+/* D itself enters only through those decisions and carries no adjoint.     */
+/* Scope: a kinematic blade that translates (no angular velocity), rigid    */
+/* interval 1, no material-material contact.                                */
+/*                                                                          */
+/* Given the scene at the state before substep n and the adjoints of the    */
+/* state after it (x, v, F, u_t), plus dL/dF_B^n of this substep's          */
+/* reaction force (Eq. 16), or_adj_substep replaces the state adjoints by   */
+/* those of the state before the substep and accumulates dL/dmu,            */
+/* dL/dlambda, and the adjoints of the tool position and segment velocity.  */
+/* ======================================================================== */
+
+typedef struct {
+  int64_t n;
+  double *xb, *vb, *Fb, *ub;  /* adjoints of x, v, F, u_t (n x 3, 3, 9, 3) */
+  double mub, lamb;           /* dL/dmu, dL/dlambda */
+  double xBb[3];              /* adjoint of the tool position at the current state */
+  double vsegb[OR_MAX_SEG][3];/* dL/d(segment linear velocity) */
+} or_adj;
+
+or_adj *or_adj_create(int64_t n) {
+  or_adj *a = (or_adj *)calloc(1, sizeof(or_adj));
+  a->n = n;
+  a->xb = (double *)calloc((size_t)n * 3, sizeof(double));
+  a->vb = (double *)calloc((size_t)n * 3, sizeof(double));
+  a->Fb = (double *)calloc((size_t)n * 9, sizeof(double));
+  a->ub = (double *)calloc((size_t)n * 3, sizeof(double));
+  return a;
+}
+
+void or_adj_destroy(or_adj *a) {
+  if (!a) return;
+  free(a->xb); free(a->vb); free(a->Fb); free(a->ub);
+  free(a);
+}
+
+/* 0: x, 1: v, 2: F, 3: u_t, 4: tool position (3) */
+double *or_adj_field(or_adj *a, int which) {
+  switch (which) {
+    case 0: return a->xb;
+    case 1: return a->vb;
+    case 2: return a->Fb;
+    case 3: return a->ub;
+    case 4: return a->xBb;
+  }
+  return NULL;
+}
+
+/* out: dL/dE, dL/dnu, dL/dmu, dL/dlambda, tool-position adjoint (3), then
+   the segment velocity adjoints (OR_MAX_SEG x 3) */
+void or_adj_theta(const or_adj *a, const or_scene *s, double *out) {
+  double E = s->P.E, nu = s->P.nu;
+  double Dn = (1.0 + nu) * (1.0 - 2.0 * nu);
+  double dmu_dE = 1.0 / (2.0 * (1.0 + nu)), dmu_dnu = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+  double dlam_dE = nu / Dn, dlam_dnu = E * (1.0 + 2.0 * nu * nu) / (Dn * Dn);
+  out[0] = a->mub * dmu_dE + a->lamb * dlam_dE;
+  out[1] = a->mub * dmu_dnu + a->lamb * dlam_dnu;
+  out[2] = a->mub;
+  out[3] = a->lamb;
+  memcpy(out + 4, a->xBb, sizeof(double) * 3);
+  memcpy(out + 7, a->vsegb, sizeof(double) * 3 * OR_MAX_SEG);
+}
+
+/* deep copy (a checkpoint); the grid is scratch and starts empty */
+or_scene *or_clone(const or_scene *s) {
+  or_scene *t = (or_scene *)malloc(sizeof(or_scene));
+  *t = *s;
+  size_t n = (size_t)s->n, n3 = n * 3;
+#define OR_DUP(f, cnt)                                      \
+  t->f = malloc(sizeof(*s->f) * (cnt) > 0 ? sizeof(*s->f) * (cnt) : 1); \
+  memcpy(t->f, s->f, sizeof(*s->f) * (cnt))
+  OR_DUP(X, n3); OR_DUP(x, n3); OR_DUP(v, n3); OR_DUP(F, n * 9); OR_DUP(D, n);
+  OR_DUP(ut, n3); OR_DUP(J, n3);
+  OR_DUP(digit, n * OR_MAX_CUTS); OR_DUP(digit_next, n * OR_MAX_CUTS);
+  OR_DUP(hist, n * OR_HIST); OR_DUP(hist_next, n * OR_HIST);
+  OR_DUP(hist_cnt, n); OR_DUP(hist_cnt_next, n);
+  OR_DUP(wrench_hist, (size_t)(s->wrench_cap > 0 ? s->wrench_cap : 1) * 6);
+#undef OR_DUP
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  t->nodes = (or_node *)calloc(nn, sizeof(or_node));
+  return t;
+}
+
+/* dP^T[Pb] of the neo-Hookean stress: Fb += ..., mub/lamb += ... */
+void or_piola_vjp(const double F[9], double mu, double lam, const double Pb[9], double Fb[9],
+                      double *mub, double *lamb) {
+  double c[9];
+  c[0] = F[4] * F[8] - F[5] * F[7];
+  c[1] = F[5] * F[6] - F[3] * F[8];
+  c[2] = F[3] * F[7] - F[4] * F[6];
+  c[3] = F[2] * F[7] - F[1] * F[8];
+  c[4] = F[0] * F[8] - F[2] * F[6];
+  c[5] = F[1] * F[6] - F[0] * F[7];
+  c[6] = F[1] * F[5] - F[2] * F[4];
+  c[7] = F[2] * F[3] - F[0] * F[5];
+  c[8] = F[0] * F[4] - F[1] * F[3];
+  double J = det3(F);
+  if (!(J > OR_JMIN)) J = OR_JMIN; /* clamped elements are flagged by the forward step */
+  double G[9];                     /* F^{-T} */
+  for (int k = 0; k < 9; ++k) G[k] = c[k] / J;
+  double lj = log(J);
+  /* P = mu F + (lam ln J - mu) G, dG = -G dF^T G, d ln J = G : dF */
+  double PG = 0, PF = 0;
+  for (int k = 0; k < 9; ++k) {
+    PG += Pb[k] * G[k];
+    PF += Pb[k] * F[k];
+  }
+  double GPtG[9]; /* (G Pb^T G)_lk = sum_ij G_lj Pb_ij G_ik */
+  for (int l = 0; l < 3; ++l)
+    for (int k = 0; k < 3; ++k) {
+      double acc = 0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) acc += G[3 * l + j] * Pb[3 * i + j] * G[3 * i + k];
+      GPtG[3 * l + k] = acc;
+    }
+  for (int k = 0; k < 9; ++k) Fb[k] += mu * Pb[k] - (lam * lj - mu) * GPtG[k] + lam * PG * G[k];
+  *mub += PF - PG;
+  *lamb += lj * PG;
+}
+
+/* (C^T S)^b = S^b + 1/M sum_{a != b, compatible} m^a (S^a - S^b): the
+   transpose of the linear map of Eq. 8 (masses and codes fixed) */
+void or_couple_T(int ns, const int64_t *codes, const double *m, int nc, double *S) {
+  double M = 0;
+  for (int a = 0; a < ns; ++a) M += m[a];
+  if (!(M > 0)) return;
+  double *out = (double *)malloc(sizeof(double) * (size_t)ns * (size_t)nc);
+  for (int b = 0; b < ns; ++b)
+    for (int c = 0; c < nc; ++c) {
+      double acc = 0;
+      for (int a = 0; a < ns; ++a) {
+        if (a == b || or_conflict(codes[a], codes[b])) continue;
+        acc += m[a] * (S[a * nc + c] - S[b * nc + c]);
+      }
+      out[b * nc + c] = S[b * nc + c] + acc / M;
+    }
+  memcpy(S, out, sizeof(double) * (size_t)ns * (size_t)nc);
+  free(out);
+}
+
+/* VJP of the blade contact of particle p (Eq. 12, 14, 15, 5 release).
+   Jb: adjoint of the particle's blade impulse J_pB (after release);
+   ub_new: adjoint of u_t after the substep.  Adds to xb, vb, xBb, vBb and
+   writes ub_old (adjoint of u_t before the substep). */
+static void contact_vjp(const or_scene *s, const or_frame *fr, int cut, int64_t p, double Dn,
+                        const double Jb_in[3], const double ub_new[3], double xb[3], double vb[3],
+                        double ub_old[3], double xBb[3], double vBb[3]) {
+  const or_params *P = &s->P;
+  const double dt = P->dt, mp = s->mp;
+  const double *xp = s->x + 3 * p, *vp = s->v + 3 * p, *uh = s->ut + 3 * p;
+  ub_old[0] = ub_old[1] = ub_old[2] = 0.0;
+  /* --- forward recomputation --- */
+  const double *ax[3] = {fr->n, fr->e, fr->d};
+  double y[3] = {xp[0] - fr->c[0], xp[1] - fr->c[1], xp[2] - fr->c[2]};
+  double q[3];
+  int outside = 0, clampd[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) {
+    q[a] = dot3(y, ax[a]);
+    if (fabs(q[a]) > fr->hext[a]) outside = clampd[a] = 1;
+  }
+  double xc[3], nB[3], phi;
+  or_box_closest(fr->c, fr->n, fr->e, fr->d, fr->hext, xp, s->Rp, xc, nB, &phi);
+  double diff[3] = {0, 0, 0}, dist = 0, nl[3] = {0, 0, 0};
+  int best = 0;
+  double sg = 1.0;
+  if (outside) {
+    for (int a = 0; a < 3; ++a) {
+      double qc = q[a] < -fr->hext[a] ? -fr->hext[a] : (q[a] > fr->hext[a] ? fr->hext[a] : q[a]);
+      diff[a] = q[a] - qc;
+    }
+    dist = norm3(diff);
+    for (int a = 0; a < 3; ++a) nl[a] = diff[a] / dist;
+  } else {
+    double bd = fr->hext[0] - fabs(q[0]);
+    for (int a = 1; a < 3; ++a) {
+      double dd = fr->hext[a] - fabs(q[a]);
+      if (dd < bd) {
+        bd = dd;
+        best = a;
+      }
+    }
+    sg = q[best] < 0 ? -1.0 : 1.0;
+  }
+  double vrel[3] = {vp[0] - s->vB[0], vp[1] - s->vB[1], vp[2] - s->vB[2]};
+  double vn = dot3(vrel, nB);
+  int neg = vn < 0;
+  double phihat = phi + dt * (neg ? vn : 0.0);
+  double meff = 1.0 / (1.0 / mp + 0.0);
+  double kn = P->s_n * meff / dt;
+  double Jn = kn * (phihat < 0 ? -phihat : 0.0);
+  if (!(Jn > 0)) return; /* no contact: u_t is reset to zero, nothing flows back */
+  double fn = Jn / dt;
+  /* friction, Eq. 12 */
+  double udn = dot3(uh, nB), ul = norm3(uh);
+  double tu[3] = {uh[0] - udn * nB[0], uh[1] - udn * nB[1], uh[2] - udn * nB[2]};
+  double tl = norm3(tu);
+  double sc = tl > 0 ? ul / tl : 0.0;
+  double ut[3] = {tu[0] * sc, tu[1] * sc, tu[2] * sc};
+  double vnn = dot3(vrel, nB);
+  double vt[3] = {vrel[0] - vnn * nB[0], vrel[1] - vnn * nB[1], vrel[2] - vnn * nB[2]};
+  double kt = P->gamma_k * meff / (dt * dt);
+  double ct = 2.0 * P->gamma_c * sqrt(meff * kt);
+  double ftr[3];
+  for (int i = 0; i < 3; ++i) ftr[i] = -kt * ut[i] - ct * vt[i];
+  double fl = norm3(ftr);
+  int stick = fl <= s->B.mu_s * fn;
+  double ft[3];
+  for (int i = 0; i < 3; ++i) ft[i] = stick ? ftr[i] : s->B.mu_d * fn * ftr[i] / fl;
+  double JpB[3];
+  for (int i = 0; i < 3; ++i) JpB[i] = Jn * nB[i] + dt * ft[i];
+  int rel = 0;
+  if (cut >= 0) {
+    double r[3] = {xp[0] - fr->xe[0], xp[1] - fr->xe[1], xp[2] - fr->xe[2]};
+    double sp = dot3(r, fr->n), lp = dot3(r, fr->e), fp = dot3(r, fr->d);
+    double dv[3] = {fr->ve[0] - vp[0], fr->ve[1] - vp[1], fr->ve[2] - vp[2]};
+    double uc = dot3(dv, fr->d);
+    int front = fabs(sp) <= P->h && fabs(lp) <= s->B.half_len && fp >= 0.0 && fp <= P->b_lead &&
+                uc > P->u_min;
+    if (front && !(Dn < 1.0) && dot3(JpB, fr->d) > 0) rel = 1;
+  }
+  /* --- reverse --- */
+  double Jb[3] = {Jb_in[0], Jb_in[1], Jb_in[2]};
+  if (rel) { /* J' = (I - d d^T) J */
+    double t = dot3(Jb, fr->d);
+    for (int i = 0; i < 3; ++i) Jb[i] -= t * fr->d[i];
+  }
+  double Jnb = dot3(Jb, nB);
+  double nBb[3] = {Jn * Jb[0], Jn * Jb[1], Jn * Jb[2]};
+  double ftb[3] = {dt * Jb[0], dt * Jb[1], dt * Jb[2]};
+  double utb[3] = {0, 0, 0}, vtb[3] = {0, 0, 0}, ftrb[3], fnb = 0;
+  if (stick) { /* ft = ftr, u' = ut + dt vt */
+    for (int i = 0; i < 3; ++i) {
+      ftrb[i] = ftb[i];
+      utb[i] += ub_new[i];
+      vtb[i] += dt * ub_new[i];
+    }
+  } else { /* ft = mu_d fn ftr/|ftr|, u' = -(ft + ct vt)/kt */
+    double g[3], hh[3], hb[3];
+    for (int i = 0; i < 3; ++i) {
+      g[i] = ftb[i] - ub_new[i] / kt;
+      vtb[i] += -ct * ub_new[i] / kt;
+      hh[i] = ftr[i] / fl;
+    }
+    fnb += s->B.mu_d * dot3(g, hh);
+    for (int i = 0; i < 3; ++i) hb[i] = s->B.mu_d * fn * g[i];
+    double t = dot3(hb, hh);
+    for (int i = 0; i < 3; ++i) ftrb[i] = (hb[i] - t * hh[i]) / fl;
+  }
+  for (int i = 0; i < 3; ++i) { /* ftr = -kt ut - ct vt */
+    utb[i] += -kt * ftrb[i];
+    vtb[i] += -ct * ftrb[i];
+  }
+  double vrelb[3];
+  { /* vt = vrel - (vrel.nB) nB */
+    double t = dot3(vtb, nB);
+    for (int i = 0; i < 3; ++i) {
+      vrelb[i] = vtb[i] - t * nB[i];
+      nBb[i] += -vnn * vtb[i] - t * vrel[i];
+    }
+  }
+  double uhb[3] = {0, 0, 0};
+  if (tl > 0) { /* ut = tu ul/tl; tu = uh - (uh.nB) nB */
+    double scb = dot3(utb, tu);
+    double ulb = scb / tl, tlb = -scb * ul / (tl * tl);
+    double tub[3];
+    for (int i = 0; i < 3; ++i) tub[i] = sc * utb[i] + tlb * tu[i] / tl;
+    for (int i = 0; i < 3; ++i) uhb[i] += ulb * uh[i] / ul;
+    double t = dot3(tub, nB);
+    for (int i = 0; i < 3; ++i) {
+      uhb[i] += tub[i] - t * nB[i];
+      nBb[i] += -udn * tub[i] - t * uh[i];
+    }
+  }
+  Jnb += fnb / dt;
+  double phihatb = -kn * Jnb;
+  double phib = phihatb, vnb = neg ? dt * phihatb : 0.0;
+  for (int i = 0; i < 3; ++i) {
+    vrelb[i] += vnb * nB[i];
+    nBb[i] += vnb * vrel[i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    vb[i] += vrelb[i];
+    vBb[i] -= vrelb[i];
+  }
+  double qb[3] = {0, 0, 0};
+  if (outside) { /* nB = sum_a nl_a ax_a, nl = diff/dist, phi = dist - R */
+    double nlb[3], t = 0;
+    for (int a = 0; a < 3; ++a) {
+      nlb[a] = dot3(nBb, ax[a]);
+      t += nlb[a] * nl[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (clampd[a]) qb[a] = (nlb[a] - t * nl[a]) / dist + phib * nl[a];
+  } else {
+    qb[best] = sg * phib; /* phi = sg q_best - h_best - R; nB fixed */
+  }
+  for (int i = 0; i < 3; ++i) {
+    double yb = qb[0] * ax[0][i] + qb[1] * ax[1][i] + qb[2] * ax[2][i];
+    xb[i] += yb;
+    xBb[i] -= yb; /* box centre = tool position + a fixed offset */
+  }
+  memcpy(ub_old, uhb, sizeof uhb);
+}
+
+int or_adj_substep(const or_scene *s0, or_adj *A, const double Fbar[3]) {
+  if (s0->P.pair_on) return -1;
+  if (s0->has_blade) {
+    if (s0->B.mass > 0 || s0->B.rigid_interval != 1) return -1;
+    for (int k = 0; k < s0->B.nseg; ++k)
+      if (s0->B.seg[k].w[0] != 0 || s0->B.seg[k].w[1] != 0 || s0->B.seg[k].w[2] != 0) return -1;
+    if (s0->wB[0] != 0 || s0->wB[1] != 0 || s0->wB[2] != 0) return -1;
+  }
+  or_scene *s = or_clone(s0); /* the substep's own set-up is replayed on a copy */
+  const or_params *P = &s->P;
+  int64_t n = s->n;
+  double dt = P->dt, mp = s->mp, V0 = P->V0, beta = P->beta;
+  const or_seg *sg = s->has_blade ? seg_at(s, s->step) : NULL;
+  int seg_idx = -1;
+  if (s->has_blade) { /* segment whose velocity the tool carries this substep */
+    int64_t acc = 0;
+    for (int k = 0; k < s->B.nseg; ++k) {
+      acc += s->B.seg[k].n_steps;
+      if (s->step < acc) {
+        seg_idx = k;
+        break;
+      }
+    }
+    if (seg_idx < 0) seg_idx = s->B.nseg - 1; /* program ended: the last twist holds */
+  }
+  int cut = sg ? sg->cut_id : -1;
+  or_frame fr;
+  memset(&fr, 0, sizeof fr);
+  if (s->has_blade) {
+    if (sg)
+      for (int i = 0; i < 3; ++i) {
+        s->vB[i] = sg->v[i];
+        s->wB[i] = sg->w[i];
+      }
+    if (cut >= 0 && cut != s->cur_cut) {
+      for (int64_t p = 0; p < n; ++p) s->D[p] = 0.0;
+      s->cur_cut = cut;
+    }
+    or_make_frame(s, &fr);
+  }
+  /* logical grids and their masses (fixed by the codes) */
+  clear_grid(s);
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          or_lgrid *g = lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 1);
+          g->m += w[0][i] * w[1][j] * w[2][k] * mp;
+        }
+  }
+  size_t nn = (size_t)s->dim[0] * s->dim[1] * s->dim[2];
+  /* (a) F' = F + dt sum_i v*_i (x) grad0 N: adjoint of v* per logical grid (in vstar) */
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    const double *Fb = A->Fb + 9 * p;
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double gN[3] = {dw[0][i] * w[1][j] * w[2][k], w[0][i] * dw[1][j] * w[2][k],
+                          w[0][i] * w[1][j] * dw[2][k]};
+          or_lgrid *g = lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          for (int a = 0; a < 3; ++a)
+            g->vstar[a] += dt * (Fb[3 * a] * gN[0] + Fb[3 * a + 1] * gN[1] + Fb[3 * a + 2] * gN[2]);
+        }
+  }
+  /* (b) v* = C p* / m (coupled MUSL momentum over mass): adjoint of p* per
+     logical grid (in pstar) */
+  for (size_t i = 0; i < nn; ++i) {
+    or_node *nd = &s->nodes[i];
+    int ns = nd->cnt;
+    if (ns == 0) continue;
+    int64_t *codes = (int64_t *)malloc(sizeof(int64_t) * ns);
+    double *m = (double *)malloc(sizeof(double) * ns);
+    double *S = (double *)malloc(sizeof(double) * ns * 3);
+    for (int a = 0; a < ns; ++a) {
+      codes[a] = nd->g[a].code;
+      m[a] = nd->g[a].m;
+      for (int c = 0; c < 3; ++c) S[a * 3 + c] = nd->g[a].m > 0 ? nd->g[a].vstar[c] / nd->g[a].m : 0.0;
+    }
+    or_couple_T(ns, codes, m, 3, S);
+    for (int a = 0; a < ns; ++a)
+      for (int c = 0; c < 3; ++c) nd->g[a].pstar[c] = S[a * 3 + c];
+    free(codes); free(m); free(S);
+  }
+  /* (c) p* = sum N m_p v'_p: adjoint of v' (the G2P velocity) */
+  double *v1b = (double *)malloc(sizeof(double) * (size_t)n * 3);
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    double acc[3] = {A->vb[3 * p], A->vb[3 * p + 1], A->vb[3 * p + 2]};
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double N = w[0][i] * w[1][j] * w[2][k];
+          or_lgrid *g = lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          for (int a = 0; a < 3; ++a) acc[a] += N * mp * g->pstar[a];
+        }
+    memcpy(v1b + 3 * p, acc, sizeof acc);
+  }
+  /* (d) G2P (Eq. 17) and x' = x + dt sum N vnew: adjoints of the coupled
+     momentum and momentum change per logical grid (in p and dp) */
+  for (size_t i = 0; i < nn; ++i)
+    for (int a = 0; a < s->nodes[i].cnt; ++a) {
+      memset(s->nodes[i].g[a].p, 0, sizeof(double) * 3);
+      memset(s->nodes[i].g[a].dp, 0, sizeof(double) * 3);
+    }
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double N = w[0][i] * w[1][j] * w[2][k];
+          or_lgrid *g = lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          if (!(g->m > 0)) continue;
+          for (int a = 0; a < 3; ++a) {
+            g->p[a] += N / g->m * ((1.0 - beta) * v1b[3 * p + a] + dt * A->xb[3 * p + a]);
+            g->dp[a] += N / g->m * (v1b[3 * p + a] + dt * A->xb[3 * p + a]);
+          }
+        }
+  }
+  for (size_t i = 0; i < nn; ++i) {
+    or_node *nd = &s->nodes[i];
+    int ns = nd->cnt;
+    if (ns == 0) continue;
+    int64_t *codes = (int64_t *)malloc(sizeof(int64_t) * ns);
+    double *m = (double *)malloc(sizeof(double) * ns);
+    double *S = (double *)malloc(sizeof(double) * ns * 6);
+    for (int a = 0; a < ns; ++a) {
+      codes[a] = nd->g[a].code;
+      m[a] = nd->g[a].m;
+      for (int c = 0; c < 3; ++c) {
+        S[a * 6 + c] = nd->g[a].p[c];
+        S[a * 6 + 3 + c] = nd->g[a].dp[c];
+      }
+    }
+    or_couple_T(ns, codes, m, 6, S);
+    for (int a = 0; a < ns; ++a)
+      for (int c = 0; c < 3; ++c) {
+        nd->g[a].p[c] = S[a * 6 + c];
+        nd->g[a].dp[c] = S[a * 6 + 3 + c];
+      }
+    free(codes); free(m); free(S);
+  }
+  /* (e) P2G (Eq. 2), stress and contact, per particle */
+  double vBb[3] = {0, 0, 0}, xBd[3] = {0, 0, 0};
+  for (int64_t p = 0; p < n; ++p) {
+    int b[3];
+    double w[3][3], dw[3][3];
+    base_of(s, s->X + 3 * p, b, w, dw);
+    int64_t c = pcode(s, p, s->digit);
+    double vb[3], Jbar[3] = {0, 0, 0}, Pb[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < 3; ++a) vb[a] = beta * v1b[3 * p + a];
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          double N = w[0][i] * w[1][j] * w[2][k];
+          double gN[3] = {dw[0][i] * w[1][j] * w[2][k], w[0][i] * dw[1][j] * w[2][k],
+                          w[0][i] * w[1][j] * dw[2][k]};
+          or_lgrid *g = lgrid_find(&s->nodes[node_index(s, b[0] + i, b[1] + j, b[2] + k)], c, 0);
+          for (int a = 0; a < 3; ++a) {
+            vb[a] += N * mp * g->p[a];
+            Jbar[a] += N * g->dp[a];
+            for (int d = 0; d < 3; ++d) Pb[3 * a + d] += -dt * V0 * g->dp[a] * gN[d];
+          }
+        }
+    double *Fb = A->Fb + 9 * p; /* F' = F + ...: dF'/dF = I */
+    or_piola_vjp(s->F + 9 * p, s->mu, s->lam, Pb, Fb, &A->mub, &A->lamb);
+    double *xb = A->xb + 3 * p;  /* x' = x + ...: dx'/dx = I */
+    double ub_new[3] = {A->ub[3 * p], A->ub[3 * p + 1], A->ub[3 * p + 2]};
+    double ub_old[3] = {0, 0, 0};
+    if (s->has_blade && P->tool_contact_on) {
+      /* J_p = J_pB + floor; F_B^n = -sum_p J_pB / dt (Eq. 16) */
+      double JbB[3] = {Jbar[0] - Fbar[0] / dt, Jbar[1] - Fbar[1] / dt, Jbar[2] - Fbar[2] / dt};
+      contact_vjp(s, &fr, cut, p, s->D[p], JbB, ub_new, xb, vb, ub_old, xBd, vBb);
+    }
+    if (P->floor_on) {
+      const double *xp = s->x + 3 * p, *vp = s->v + 3 * p;
+      double phi = xp[2] - P->floor_z - s->Rp;
+      int neg = vp[2] < 0;
+      double phihat = phi + dt * (neg ? vp[2] : 0.0);
+      double kn = P->s_n * mp / dt;
+      if (kn * (phihat < 0 ? -phihat : 0.0) > 0) {
+        double phihatb = -kn * Jbar[2];
+        xb[2] += phihatb;
+        if (neg) vb[2] += dt * phihatb;
+      }
+    }
+    memcpy(A->vb + 3 * p, vb, sizeof vb);
+    memcpy(A->ub + 3 * p, ub_old, sizeof ub_old);
+  }
+  free(v1b);
+  /* tool: x_B^{n+1} = x_B^n + dt v_B^n, v_B^n = segment velocity */
+  if (s->has_blade) {
+    for (int i = 0; i < 3; ++i) {
+      double vtot = vBb[i] + dt * A->xBb[i];
+      A->xBb[i] += xBd[i];
+      if (seg_idx >= 0) A->vsegb[seg_idx][i] += vtot;
+    }
+  }
+  or_destroy(s);
+  return 0;
+}

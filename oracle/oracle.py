@@ -113,6 +113,18 @@ def lib():
             L.or_side_label.restype = C.c_int
             L.or_cut_progress.argtypes = [C.c_double] * 4
             L.or_cut_progress.restype = C.c_double
+            L.or_clone.argtypes = [C.c_void_p]
+            L.or_clone.restype = C.c_void_p
+            L.or_adj_create.argtypes = [C.c_int64]
+            L.or_adj_create.restype = C.c_void_p
+            L.or_adj_destroy.argtypes = [C.c_void_p]
+            L.or_adj_field.argtypes = [C.c_void_p, C.c_int]
+            L.or_adj_field.restype = dp
+            L.or_adj_theta.argtypes = [C.c_void_p, C.c_void_p, dp]
+            L.or_adj_substep.argtypes = [C.c_void_p, C.c_void_p, dp]
+            L.or_adj_substep.restype = C.c_int
+            L.or_piola_vjp.argtypes = [dp, C.c_double, C.c_double, dp, dp, dp, dp]
+            L.or_couple_T.argtypes = [C.c_int, C.POINTER(C.c_int64), dp, C.c_int, dp]
             _lib = L
     return _lib
 
@@ -172,6 +184,27 @@ def couple(codes, m, S):
     ns, nc = S.shape
     lib().or_couple(ns, codes.ctypes.data_as(C.POINTER(C.c_int64)), _dp(m), nc, _dp(S))
     return S
+
+
+def couple_T(codes, m, S):
+    """Transpose of the Eq. 8 coupling map (masses and codes fixed)."""
+    codes = np.ascontiguousarray(np.asarray(codes, dtype=np.int64))
+    m = _arr(m)
+    S = np.ascontiguousarray(np.asarray(S, dtype=np.float64)).copy()
+    ns, nc = S.shape
+    lib().or_couple_T(ns, codes.ctypes.data_as(C.POINTER(C.c_int64)), _dp(m), nc, _dp(S))
+    return S
+
+
+def piola_vjp(F, mu, lam, Pb):
+    """(dP/dF)^T Pb, dP/dmu : Pb, dP/dlambda : Pb of the neo-Hookean stress."""
+    F = _arr(F, 9)
+    Pb = _arr(Pb, 9)
+    Fb = np.zeros(9)
+    mub = np.zeros(1)
+    lamb = np.zeros(1)
+    lib().or_piola_vjp(_dp(F), mu, lam, _dp(Pb), _dp(Fb), _dp(mub), _dp(lamb))
+    return Fb.reshape(3, 3), float(mub[0]), float(lamb[0])
 
 
 def friction(u_hist, n, vrel, fn, meff, dt, gk, gc, mus, mud):
@@ -251,8 +284,15 @@ class OracleScene:
     FIELDS = {"X": (0, 3), "x": (1, 3), "v": (2, 3), "F": (3, 9), "D": (4, 1),
               "ut": (5, 3), "code": (6, 1), "J": (7, 3), "digits": (8, MAX_CUTS)}
 
-    def __init__(self, sc, single_field: bool = False, wrench_capacity: int = 0):
+    def __init__(self, sc, single_field: bool = False, wrench_capacity: int = 0,
+                 _handle=None):
         self._L = lib()
+        if _handle is not None:  # a clone of another scene (see clone())
+            self.n = sc.n
+            self.params, self._blade = sc.params, sc._blade
+            self.wrench_capacity = sc.wrench_capacity
+            self._h = _handle
+            return
         X = _arr(sc.X)
         self.n = sc.n
         self.params = _params(sc, single_field)
@@ -272,6 +312,10 @@ class OracleScene:
 
     def step(self, n: int = 1) -> int:
         return self._L.or_step(self._h, int(n))
+
+    def clone(self) -> "OracleScene":
+        """Deep copy of the whole state (a checkpoint)."""
+        return OracleScene(self, _handle=self._L.or_clone(self._h))
 
     def get(self, name: str) -> np.ndarray:
         fid, w = self.FIELDS[name]
@@ -340,3 +384,81 @@ class OracleScene:
         out = np.zeros(3)
         self._L.or_momentum(self._h, _dp(out))
         return out
+
+
+# ---------------------------------------------------------------------------
+# adjoint (reverse mode) with checkpoints
+# ---------------------------------------------------------------------------
+
+class OracleAdjoint:
+    """Adjoint state of one scene: x, v, F, u_t adjoints plus the parameter
+    accumulators (dL/dmu, dL/dlambda, tool position, segment velocities)."""
+
+    def __init__(self, n: int):
+        self._L = lib()
+        self.n = n
+        self._h = self._L.or_adj_create(n)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.or_adj_destroy(h)
+            self._h = None
+
+    def field(self, name: str) -> np.ndarray:
+        which, w = {"x": (0, 3), "v": (1, 3), "F": (2, 9), "ut": (3, 3), "xB": (4, 3)}[name]
+        ptr = self._L.or_adj_field(self._h, which)
+        return np.ctypeslib.as_array(ptr, shape=(1 if name == "xB" else self.n, w))
+
+    def substep(self, scene: "OracleScene", force_bar) -> None:
+        fb = _arr(force_bar, 3)
+        if self._L.or_adj_substep(scene._h, self._h, _dp(fb)) != 0:
+            raise ValueError("adjoint needs a kinematic translating blade, rigid interval 1 "
+                             "and no pair contact")
+
+    def theta(self, scene: "OracleScene") -> dict:
+        out = np.zeros(7 + 3 * MAX_SEG)
+        self._L.or_adj_theta(self._h, scene._h, _dp(out))
+        return {"E": out[0], "nu": out[1], "mu": out[2], "lam": out[3], "xB": out[4:7],
+                "v_seg": out[7:].reshape(MAX_SEG, 3)}
+
+
+def force_loss(forces: np.ndarray, target: np.ndarray) -> float:
+    """L = sum_n |F_B^n - F_target^n|^2 over the reaction-force trajectory."""
+    return float(np.sum((np.asarray(forces) - np.asarray(target)) ** 2))
+
+
+def forces(sc, n_steps: int) -> np.ndarray:
+    """Reaction-force trajectory F_B^n (Eq. 16), n_steps x 3."""
+    o = OracleScene(sc, wrench_capacity=n_steps)
+    o.step(n_steps)
+    return o.wrench_history(0, n_steps)[:, :3].copy()
+
+
+def gradient(sc, target: np.ndarray, n_steps: int, every: int = 20) -> dict:
+    """Loss and its gradient w.r.t. E, nu and the blade's segment
+    velocities, by the FP64 adjoint with a checkpoint every ``every``
+    substeps (each checkpoint interval is recomputed forward once)."""
+    o = OracleScene(sc, wrench_capacity=n_steps)
+    ck = {}
+    for k in range(n_steps):
+        if k % every == 0:
+            ck[k] = o.clone()
+        o.step(1)
+    F = o.wrench_history(0, n_steps)[:, :3].copy()
+    fbar = 2.0 * (F - np.asarray(target))
+    adj = OracleAdjoint(sc.n)
+    for k0 in sorted(ck, reverse=True):
+        k1 = min(k0 + every, n_steps)
+        states = []
+        t = ck[k0].clone()
+        for _ in range(k0, k1):
+            states.append(t.clone())
+            t.step(1)
+        for k in range(k1 - 1, k0 - 1, -1):
+            adj.substep(states[k - k0], fbar[k])
+        del states, t
+    th = adj.theta(o)
+    return {"loss": force_loss(F, target), "forces": F, "dE": th["E"], "dnu": th["nu"],
+            "dv_seg": th["v_seg"][:len(sc.blade.segments)] if sc.blade else None,
+            "dxB0": th["xB"], "adjoint": adj}
