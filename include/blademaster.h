@@ -214,6 +214,65 @@ int bm_read_state_noalloc(bm_scene_t s, uint32_t field_mask, void *const *dst);
 int bm_scene_info_get(bm_scene_t s, bm_scene_info *out);
 int bm_scene_destroy(bm_scene_t s);
 
+/* ---- checkpoints ---------------------------------------------------------
+ * A checkpoint is the scene's complete simulation state in one flat buffer:
+ * particle state (x, v, F, D, u_t, side masks; pair-contact history when the
+ * scene has pair contact), the tool's pose, twist and rigid-interval
+ * accumulators, the current cut, the substep counter, the frame of the next
+ * substep, the per-substep wrench history and the sticky error word.
+ * Restoring it makes the next substeps reproduce, bit for bit, the ones that
+ * followed the save (resume after a failure, and the recomputation between
+ * the checkpoints of the adjoint).  The buffer is caller-owned;
+ * bm_checkpoint_size gives its size.  It may be restored into the same scene
+ * only (same handle, any world: a scene moved into or out of a batch keeps
+ * its checkpoints valid).  dst/src are device pointers when *_on_device != 0,
+ * else host memory.  Both calls synchronise the scene's stream.  Restore
+ * rejects (BM_E_INVALID) a buffer whose header does not match the scene and
+ * rebuilds the logical-grid slots for the restored side masks. */
+int bm_checkpoint_size(bm_scene_t s, int64_t *bytes);
+int bm_checkpoint_save(bm_scene_t s, void *dst, int dst_on_device);
+int bm_checkpoint_restore(bm_scene_t s, const void *src, int src_on_device);
+
+/* ---- adjoint of the substep (calibration) ---------------------------------
+ * Reverse mode of one substep for gradients of a loss on the per-substep
+ * reaction force F_B^n (Eq. 16) with respect to the material (E, nu) and the
+ * blade's segment velocities, used with checkpoints: restore the state before
+ * substep n (bm_checkpoint_restore) and call bm_adjoint_substep for n in
+ * decreasing order.  The discrete decisions of the forward substep are held
+ * fixed: codes (Eq. 6-7), contact active sets (Eq. 14-15), stick or slip
+ * (Eq. 12), the front band and D release (Eq. 5) and the blade-box face;
+ * they are re-taken from the restored state with the forward float32
+ * expressions.  With the codes fixed, P2G, the coupling of Eq. 8, the grid
+ * update (Eq. 9), G2P (Eq. 17), the MUSL re-scatter and the F update form a
+ * fixed linear map; its transpose is applied by per-node gathers in a fixed
+ * order (no atomics).  float32 arithmetic, float64 parameter accumulators.
+ * Scope: a kinematic blade (mass 0) whose segments and current twist have no
+ * angular velocity, rigid interval 1, no material-material contact;
+ * anything else is BM_E_INVALID.  Device memory for the adjoint (about 84
+ * bytes per particle and 40 per logical-grid slot) comes from the scene's
+ * allocator; calls are ordered on the scene's stream. */
+typedef struct bm_adjoint_s *bm_adjoint_t;
+int bm_adjoint_create(bm_scene_t s, bm_adjoint_t *out);
+/* zero the state adjoints and every accumulator */
+int bm_adjoint_reset(bm_adjoint_t a);
+/* The scene holds the state before substep n (its substep counter says n).
+ * force_bar = dL/dF_B^n (host, 3 doubles).  Replaces the state adjoints of
+ * the state after the substep by those of the state before it and adds this
+ * substep's terms to the parameter accumulators.  Does not change the scene. */
+int bm_adjoint_substep(bm_adjoint_t a, const double force_bar[3]);
+/* Read (write != 0: overwrite) state adjoints in caller particle order,
+ * fields BM_FIELD_x, BM_FIELD_v, BM_FIELD_F, BM_FIELD_UT in increasing bit
+ * order (float32, n*3 / n*9 / n*3); buf are device pointers when
+ * on_device != 0.  Synchronises. */
+int bm_adjoint_state(bm_adjoint_t a, uint32_t field_mask, void *const *buf, int on_device, int write);
+/* Accumulated gradients (host, cap >= 7 + 3 * BM_MAX_SEGMENTS doubles):
+ * dL/dE, dL/dnu, dL/dmu, dL/dlambda, the adjoint of the tool position at the
+ * earliest substep processed (3), then dL/dv of each trajectory segment's
+ * linear velocity (3 per segment, BM_MAX_SEGMENTS segments).  Returns the
+ * count written.  Synchronises. */
+int bm_adjoint_params(bm_adjoint_t a, double *out, int cap);
+int bm_adjoint_destroy(bm_adjoint_t a);
+
 /* ---- batches of uneven scenes -------------------------------------------
  * A batch owns packed device pools (particles, nodes, slots) with a fixed
  * capacity.  Scenes moved into it keep their handles; bm_batch_step advances

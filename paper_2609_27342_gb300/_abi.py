@@ -102,6 +102,15 @@ SIGNATURES = {
     "bm_tool_wrench": (C.c_int, [VP, C.c_int, PD]),
     "bm_wrench_history": (C.c_int, [VP, C.c_int, C.c_int64, C.c_int64, PD]),
     "bm_scene_info_get": (C.c_int, [VP, C.POINTER(SceneInfo)]),
+    "bm_checkpoint_size": (C.c_int, [VP, C.POINTER(C.c_int64)]),
+    "bm_checkpoint_save": (C.c_int, [VP, VP, C.c_int]),
+    "bm_checkpoint_restore": (C.c_int, [VP, VP, C.c_int]),
+    "bm_adjoint_create": (C.c_int, [VP, PVP]),
+    "bm_adjoint_reset": (C.c_int, [VP]),
+    "bm_adjoint_substep": (C.c_int, [VP, PD]),
+    "bm_adjoint_state": (C.c_int, [VP, C.c_uint32, PVP, C.c_int, C.c_int]),
+    "bm_adjoint_params": (C.c_int, [VP, PD, C.c_int]),
+    "bm_adjoint_destroy": (C.c_int, [VP]),
     "bm_scene_destroy": (C.c_int, [VP]),
     "bm_batch_create": (C.c_int, [C.POINTER(BatchDesc), C.POINTER(Alloc), VP, PVP]),
     "bm_batch_scene_create": (C.c_int, [VP, C.POINTER(SceneDesc), C.POINTER(BladeDesc),

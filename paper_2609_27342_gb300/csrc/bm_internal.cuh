@@ -164,6 +164,17 @@ struct LaunchSet {
 #define BM_NUM_VARIANTS 3
 extern const char *const bm_kernel_names[BM_NUM_KERNELS];
 cudaError_t bm_kernels_init();  // per device: shared-memory limits of the brick kernels
+
+// adjoint of the substep (bm_adjoint.cu); the work record is opaque here
+size_t bm_adj_work_struct_size();
+size_t bm_adj_work_alloc_bytes(int64_t n_p, int64_t slot_cap);
+void *bm_adj_carve(void *base, int64_t n_p, int64_t slot_cap, int scene_slot, void *out_work);
+void bm_adj_set_slot(void *work, int scene_slot);
+double *bm_adj_acc(void *work);
+cudaError_t bm_launch_adjoint_substep(const World &w, const void *work, const double fbar[3], int n_p,
+                                      int n_node, cudaStream_t st);
+cudaError_t bm_launch_adjoint_io(const World &w, const void *work, int field, float *buf, int to_work,
+                                 int n_p, cudaStream_t st);
 cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t st);
 cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev);
 cudaError_t bm_launch_prepare(const World &w, const LaunchSet &ls, cudaStream_t st);

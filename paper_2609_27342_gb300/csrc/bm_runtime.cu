@@ -1035,6 +1035,243 @@ int bm_write_state(bm_scene_t s, uint32_t field_mask, const void *const *src, in
   return BM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// checkpoints: a flat buffer with a header, the device scene record and the
+// scene's pool ranges, each section 256-byte aligned
+// ---------------------------------------------------------------------------
+namespace {
+const uint64_t kCkMagic = 0x31304b434d4c4242ull;  // "BBLMCK01"
+struct CkHeader {
+  uint64_t magic;
+  int64_t n, p_begin, hist_cap, bytes;
+  int32_t pair, pad;
+};
+size_t ck_align(size_t b) { return (b + 255) & ~size_t(255); }
+
+// (destination offset, pool pointer, bytes) of every section after the scene record
+struct CkSection {
+  size_t off;
+  void *pool;
+  size_t bytes;
+};
+
+std::vector<CkSection> ck_layout(const bm_scene_s *s, size_t *total) {
+  const PPool &P = s->world->w.P;
+  const int64_t n = s->n, pb = s->p_begin;
+  std::vector<CkSection> v;
+  size_t off = ck_align(sizeof(CkHeader)) + ck_align(sizeof(DevScene));
+  auto add = [&](void *pool, size_t bytes) {
+    v.push_back({off, pool, bytes});
+    off += ck_align(bytes);
+  };
+  for (int a = 0; a < 3; ++a) add(P.x[a] + pb, sizeof(float) * n);
+  for (int a = 0; a < 3; ++a) add(P.v[a] + pb, sizeof(float) * n);
+  for (int k = 0; k < 9; ++k) add(P.F[k] + pb, sizeof(float) * n);
+  add(P.D + pb, sizeof(float) * n);
+  for (int a = 0; a < 3; ++a) add(P.ut[a] + pb, sizeof(float) * n);
+  add(P.s1 + pb, sizeof(uint32_t) * n);
+  add(P.s2 + pb, sizeof(uint32_t) * n);
+  if (s->desc.pair_contact)
+    for (int b = 0; b < 2; ++b) {
+      add(P.hist_partner[b] + pb * BM_HIST, sizeof(int) * n * BM_HIST);
+      add(P.hist_u[b] + pb * BM_HIST * 3, sizeof(float) * n * BM_HIST * 3);
+    }
+  if (s->hist_cap) add(s->world->w.whist + s->hist_begin * 6, sizeof(double) * 6 * s->hist_cap);
+  *total = off;
+  return v;
+}
+}  // namespace
+
+int bm_checkpoint_size(bm_scene_t s, int64_t *bytes) {
+  if (!valid_scene(s) || !bytes) return fail(BM_E_INVALID, "bad scene or output");
+  size_t total = 0;
+  ck_layout(s, &total);
+  *bytes = (int64_t)total;
+  return BM_OK;
+}
+
+int bm_checkpoint_save(bm_scene_t s, void *dst, int dst_on_device) {
+  if (!valid_scene(s) || !dst) return fail(BM_E_INVALID, "bad scene or destination");
+  (void)dst_on_device;  // unified addressing: one copy kind serves both
+  WorldH *W = s->world;
+  size_t total = 0;
+  std::vector<CkSection> secs = ck_layout(s, &total);
+  CK(cudaStreamSynchronize(W->st));
+  CkHeader h{kCkMagic, s->n, s->p_begin, s->hist_cap, (int64_t)total, s->desc.pair_contact ? 1 : 0, 0};
+  char *d = (char *)dst;
+  CK(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyDefault, W->st));
+  CK(cudaMemcpyAsync(d + ck_align(sizeof h), W->w.scenes + s->slot, sizeof(DevScene), cudaMemcpyDefault,
+                     W->st));
+  for (const CkSection &c : secs) CK(cudaMemcpyAsync(d + c.off, c.pool, c.bytes, cudaMemcpyDefault, W->st));
+  CK(cudaStreamSynchronize(W->st));
+  return BM_OK;
+}
+
+int bm_checkpoint_restore(bm_scene_t s, const void *src, int src_on_device) {
+  if (!valid_scene(s) || !src) return fail(BM_E_INVALID, "bad scene or source");
+  (void)src_on_device;
+  WorldH *W = s->world;
+  size_t total = 0;
+  std::vector<CkSection> secs = ck_layout(s, &total);
+  CK(cudaStreamSynchronize(W->st));
+  const char *d = (const char *)src;
+  CkHeader h{};
+  CK(cudaMemcpy(&h, d, sizeof h, cudaMemcpyDefault));
+  if (h.magic != kCkMagic || h.n != s->n || h.hist_cap != s->hist_cap || h.bytes != (int64_t)total ||
+      h.pair != (s->desc.pair_contact ? 1 : 0))
+    return fail(BM_E_INVALID, "checkpoint does not belong to this scene");
+  DevScene sv, cur;
+  CK(cudaMemcpy(&sv, d + ck_align(sizeof h), sizeof sv, cudaMemcpyDefault));
+  CK(cudaMemcpy(&cur, W->w.scenes + s->slot, sizeof cur, cudaMemcpyDeviceToHost));
+  for (const CkSection &c : secs) CK(cudaMemcpyAsync(c.pool, d + c.off, c.bytes, cudaMemcpyDefault, W->st));
+  const PPool &P = W->w.P;
+  CK(cudaMemsetAsync(P.pend + s->p_begin, 0, s->n, W->st));
+  CK(cudaStreamSynchronize(W->st));
+  // pair-history partners are pool indices of the world the save was made in
+  if (s->desc.pair_contact && h.p_begin != s->p_begin) {
+    std::vector<int> q((size_t)s->n * BM_HIST);
+    for (int b = 0; b < 2; ++b) {
+      int *ptr = P.hist_partner[b] + s->p_begin * BM_HIST;
+      CK(cudaMemcpy(q.data(), ptr, sizeof(int) * q.size(), cudaMemcpyDeviceToHost));
+      for (auto &v : q)
+        if (v >= 0) v = v - (int)h.p_begin + (int)s->p_begin;
+      CK(cudaMemcpy(ptr, q.data(), sizeof(int) * q.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  set_ranges(s, sv);
+  sv.slot_cap = cur.slot_cap;
+  sv.label_pending = 0;
+  sv.need_rebuild = 0;
+  CK(cudaMemcpy(W->w.scenes + s->slot, &sv, sizeof sv, cudaMemcpyHostToDevice));
+  CK(bm_launch_rebuild(W->w, scene_set(W, s), W->st, 1));
+  CK(cudaStreamSynchronize(W->st));
+  return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the substep
+// ---------------------------------------------------------------------------
+struct bm_adjoint_s {
+  bm_scene_s *s = nullptr;
+  Allocator al;
+  void *mem = nullptr;
+  size_t bytes = 0;
+  std::vector<unsigned char> work;  // the kernels' work record (pointers into mem)
+};
+
+namespace {
+int adjoint_scope(const bm_scene_s *s) {
+  if (s->desc.pair_contact) return fail(BM_E_INVALID, "adjoint: material-material contact is not supported");
+  if (s->has_blade) {
+    if (s->blade.mass > 0) return fail(BM_E_INVALID, "adjoint: the blade must be kinematic (mass 0)");
+    if (s->blade.rigid_interval > 1) return fail(BM_E_INVALID, "adjoint: rigid interval must be 1");
+    for (int k = 0; k < s->blade.n_segments; ++k)
+      for (int r = 0; r < 3; ++r)
+        if (s->blade.segments[k].omega[r] != 0.0)
+          return fail(BM_E_INVALID, "adjoint: blade segments must not rotate");
+  }
+  return BM_OK;
+}
+}  // namespace
+
+int bm_adjoint_create(bm_scene_t s, bm_adjoint_t *out) {
+  if (!valid_scene(s) || !out) return fail(BM_E_INVALID, "bad scene or output");
+  int rc = adjoint_scope(s);
+  if (rc) return rc;
+  bm_adjoint_s *a = new bm_adjoint_s();
+  a->s = s;
+  a->al.a = s->home_alloc;
+  a->al.has = s->has_home_alloc;
+  a->al.st = s->world->st;
+  a->bytes = bm_adj_work_alloc_bytes(s->n, s->slot_cap);
+  a->mem = a->al.alloc(a->bytes);
+  if (!a->mem) {
+    delete a;
+    return fail(BM_E_OOM, "adjoint: device allocation failed");
+  }
+  a->work.resize(bm_adj_work_struct_size());
+  bm_adj_carve(a->mem, s->n, s->slot_cap, s->slot, a->work.data());
+  *out = a;
+  return bm_adjoint_reset(a);
+}
+
+int bm_adjoint_reset(bm_adjoint_t a) {
+  if (!a || !valid_scene(a->s)) return fail(BM_E_INVALID, "bad adjoint");
+  WorldH *W = a->s->world;
+  CK(cudaMemsetAsync(a->mem, 0, a->bytes, W->st));
+  CK(cudaStreamSynchronize(W->st));
+  return BM_OK;
+}
+
+int bm_adjoint_substep(bm_adjoint_t a, const double force_bar[3]) {
+  if (!a || !valid_scene(a->s) || !force_bar) return fail(BM_E_INVALID, "bad adjoint or force adjoint");
+  bm_scene_s *s = a->s;
+  int rc = adjoint_scope(s);
+  if (rc) return rc;
+  WorldH *W = s->world;
+  bm_adj_set_slot(a->work.data(), s->slot);
+  CK(bm_launch_adjoint_substep(W->w, a->work.data(), force_bar, (int)s->n, (int)s->n_node, W->st));
+  return BM_OK;
+}
+
+int bm_adjoint_state(bm_adjoint_t a, uint32_t field_mask, void *const *buf, int on_device, int write) {
+  if (!a || !valid_scene(a->s) || !buf) return fail(BM_E_INVALID, "bad adjoint or buffers");
+  const uint32_t ok = BM_FIELD_x | BM_FIELD_v | BM_FIELD_F | BM_FIELD_UT;
+  if (field_mask & ~ok) return fail(BM_E_INVALID, "adjoint fields: x, v, F, UT");
+  bm_scene_s *s = a->s;
+  WorldH *W = s->world;
+  bm_adj_set_slot(a->work.data(), s->slot);
+  CK(cudaStreamSynchronize(W->st));
+  const uint32_t bits[4] = {BM_FIELD_x, BM_FIELD_v, BM_FIELD_F, BM_FIELD_UT};
+  int j = 0;
+  for (int f = 0; f < 4; ++f) {
+    if (!(field_mask & bits[f])) continue;
+    void *d = buf[j++];
+    if (!d) return fail(BM_E_INVALID, "null buffer");
+    const size_t bytes = sizeof(float) * (size_t)s->n * (f == 2 ? 9 : 3);
+    void *dev = d, *tmp = nullptr;
+    if (!on_device) {
+      CK(cudaMalloc(&tmp, bytes ? bytes : 16));
+      if (write) CK(cudaMemcpy(tmp, d, bytes, cudaMemcpyHostToDevice));
+      dev = tmp;
+    }
+    cudaError_t e = bm_launch_adjoint_io(W->w, a->work.data(), f, (float *)dev, write, (int)s->n, W->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(W->st);
+    if (e == cudaSuccess && tmp && !write) e = cudaMemcpy(d, tmp, bytes, cudaMemcpyDeviceToHost);
+    if (tmp) cudaFree(tmp);
+    CK(e);
+  }
+  return BM_OK;
+}
+
+int bm_adjoint_params(bm_adjoint_t a, double *out, int cap) {
+  const int need = 7 + 3 * BM_MAX_SEGMENTS;
+  if (!a || !valid_scene(a->s) || !out || cap < need) return fail(BM_E_INVALID, "bad adjoint or output");
+  bm_scene_s *s = a->s;
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  double acc[5 + 3 * BM_MAX_SEGMENTS];
+  CK(cudaMemcpy(acc, bm_adj_acc(a->work.data()), sizeof acc, cudaMemcpyDeviceToHost));
+  const double E = s->desc.E, nu = s->desc.nu, Dn = (1.0 + nu) * (1.0 - 2.0 * nu);
+  // mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu))
+  out[0] = acc[0] / (2.0 * (1.0 + nu)) + acc[1] * nu / Dn;
+  out[1] = -acc[0] * E / (2.0 * (1.0 + nu) * (1.0 + nu)) + acc[1] * E * (1.0 + 2.0 * nu * nu) / (Dn * Dn);
+  out[2] = acc[0];
+  out[3] = acc[1];
+  for (int k = 0; k < 3 + 3 * BM_MAX_SEGMENTS; ++k) out[4 + k] = acc[2 + k];
+  return need;
+}
+
+int bm_adjoint_destroy(bm_adjoint_t a) {
+  if (!a) return BM_OK;
+  if (a->mem) {
+    if (a->s && a->s->world) cudaStreamSynchronize(a->s->world->st);
+    a->al.release(a->mem);
+  }
+  delete a;
+  return BM_OK;
+}
+
 int bm_read_state_noalloc(bm_scene_t s, uint32_t field_mask, void *const *dst) {
   if (!valid_scene(s) || !dst) return fail(BM_E_INVALID, "bad scene or destination");
   WorldH *W = s->world;

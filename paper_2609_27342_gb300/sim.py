@@ -88,6 +88,18 @@ def _stream_handle(stream) -> Optional[int]:
     return int(h) if h else None
 
 
+def _buffer_ptr(buf, nbytes: int):
+    """(address, on_device) of a contiguous torch tensor or numpy array of at
+    least nbytes bytes."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"] or buf.nbytes < nbytes:
+            raise ValueError("buffer must be contiguous and hold the checkpoint")
+        return buf.ctypes.data, 0
+    if not buf.is_contiguous() or buf.numel() * buf.element_size() < nbytes:
+        raise ValueError("buffer must be contiguous and hold the checkpoint")
+    return buf.data_ptr(), int(buf.is_cuda)
+
+
 class Scene:
     """One simulation scene on the GPU (C handle ``bm_scene_t``)."""
 
@@ -136,6 +148,32 @@ class Scene:
     @property
     def handle(self):
         return self._h
+
+    # -- checkpoints -------------------------------------------------------
+    def checkpoint_size(self) -> int:
+        n = C.c_int64()
+        A.check(self._L.bm_checkpoint_size(self._h, C.byref(n)))
+        return int(n.value)
+
+    def checkpoint(self, out=None, device: bool = True):
+        """Complete simulation state in one buffer (bm_checkpoint_save): a
+        uint8 torch tensor on the current device, or a host numpy array with
+        ``device=False``; ``out`` reuses a buffer of checkpoint_size bytes."""
+        nbytes = self.checkpoint_size()
+        if out is None:
+            if device:
+                import torch
+                out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            else:
+                out = np.empty(nbytes, dtype=np.uint8)
+        ptr, on_dev = _buffer_ptr(out, nbytes)
+        A.check(self._L.bm_checkpoint_save(self._h, C.c_void_p(ptr), on_dev))
+        return out
+
+    def restore(self, buf) -> None:
+        """Restore a checkpoint of this scene (bm_checkpoint_restore)."""
+        ptr, on_dev = _buffer_ptr(buf, self.checkpoint_size())
+        A.check(self._L.bm_checkpoint_restore(self._h, C.c_void_p(ptr), on_dev))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -247,6 +285,72 @@ def footprint(sc) -> tuple:
     A.check(L.bm_scene_footprint(C.byref(d), X.ctypes.data_as(C.POINTER(C.c_float)), X.shape[0],
                                  C.byref(p), C.byref(nd), C.byref(br), C.byref(b)))
     return p.value, nd.value, br.value, b.value
+
+
+class Adjoint:
+    """Adjoint of the substep for one scene (bm_adjoint_*): state adjoints
+    plus accumulated parameter gradients."""
+
+    FIELDS = {"x": (A.FIELD_x, 3), "v": (A.FIELD_v, 3), "F": (A.FIELD_F, 9), "ut": (A.FIELD_UT, 3)}
+
+    def __init__(self, scene: "Scene"):
+        self._L = A.load()
+        self.scene = scene
+        h = C.c_void_p()
+        A.check(self._L.bm_adjoint_create(scene.handle, C.byref(h)))
+        self._h = h
+
+    def reset(self) -> None:
+        A.check(self._L.bm_adjoint_reset(self._h))
+
+    def substep(self, force_bar) -> None:
+        """Adjoint of the substep the scene is about to take; force_bar =
+        dL/dF_B of that substep's reaction force."""
+        fb = (C.c_double * 3)(*[float(t) for t in force_bar])
+        A.check(self._L.bm_adjoint_substep(self._h, fb))
+
+    def state(self, *names: str) -> Dict[str, np.ndarray]:
+        names = sorted(names, key=lambda k: self.FIELDS[k][0])
+        mask, bufs, out = 0, [], {}
+        n = self.scene.n
+        for k in names:
+            bit, w = self.FIELDS[k]
+            mask |= bit
+            out[k] = np.zeros((n, w), np.float32)
+            bufs.append(out[k].ctypes.data)
+        arr = (C.c_void_p * len(bufs))(*bufs)
+        A.check(self._L.bm_adjoint_state(self._h, mask, arr, 0, 0))
+        return out
+
+    def set_state(self, **fields) -> None:
+        names = sorted(fields, key=lambda k: self.FIELDS[k][0])
+        mask, bufs, keep = 0, [], []
+        for k in names:
+            bit, w = self.FIELDS[k]
+            a = np.ascontiguousarray(np.asarray(fields[k], np.float32).reshape(self.scene.n, w))
+            keep.append(a)
+            mask |= bit
+            bufs.append(a.ctypes.data)
+        arr = (C.c_void_p * len(bufs))(*bufs)
+        A.check(self._L.bm_adjoint_state(self._h, mask, arr, 0, 1))
+
+    def params(self) -> dict:
+        out = (C.c_double * (7 + 3 * A.MAX_SEGMENTS))()
+        A.check(self._L.bm_adjoint_params(self._h, out, len(out)))
+        a = np.array(out[:])
+        return {"E": a[0], "nu": a[1], "mu": a[2], "lam": a[3], "xB": a[4:7],
+                "v_seg": a[7:].reshape(A.MAX_SEGMENTS, 3)}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.bm_adjoint_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
