@@ -328,6 +328,41 @@ def run_native(args):
     wall = time.perf_counter() - t0
     e2e_value = world * n_particles * e2e_steps / wall
 
+    # adjoint calibration workload: 32,000 particles, 200 substeps, checkpoint
+    # every 20, loss on the reaction-force trajectory against a target made at
+    # E = 1.5e5 Pa; gradient vs central differences (relative step 1e-3)
+    adjoint = None
+    if args.adjoint:
+        from paper_2609_27342_gb300.calibration import force_loss_and_grad, forces
+        na = 200
+        target = forces(bi.calibration_scene(E=1.5e5), na)
+        spec = bi.calibration_scene()
+        force_loss_and_grad(spec, target, na, every=20)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, g = force_loss_and_grad(spec, target, na, every=20)
+        torch.cuda.synchronize()
+        t_fb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        forces(spec, na)
+        torch.cuda.synchronize()
+        t_f = time.perf_counter() - t0
+
+        def lossf(**kw):
+            return float(np.sum((forces(bi.calibration_scene(**kw), na) - target) ** 2))
+
+        fd = {"E": (lossf(E=1.001e5) - lossf(E=0.999e5)) / 200.0,
+              "nu": (lossf(nu=0.3003) - lossf(nu=0.2997)) / 6e-4,
+              "speed": (lossf(speed=0.2002) - lossf(speed=0.1998)) / 4e-4}
+        grad = {"E": g["E"], "nu": g["nu"], "speed": -float(g["v_seg"][0, 2])}
+        adjoint = {"workload": "calibration cuboid, 32,000 particles, 200 substeps, "
+                               "checkpoint every 20", "loss": loss, "grad": grad,
+                   "fd_rel_step_1e-3": fd,
+                   "rel_err_vs_fd": {k: abs(grad[k] - fd[k]) / abs(fd[k]) for k in fd},
+                   "forward_s": t_f, "forward_backward_s": t_fb,
+                   "particle_substeps_per_s_fwd_bwd": spec.n * na / t_fb}
+        log(f"adjoint: {adjoint}")
+
     # continuous-batching server on a Poisson request stream (rollouts of
     # 8k-500k particles, 200-2000 substeps, 1-3 cuts), admission by an HBM budget
     serving = None
@@ -382,6 +417,7 @@ def run_native(args):
             "batched_over_plain": (value / world / plain_rate) if plain_rate else None,
             "clocks": clk,
             "serving": serving,
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
             "error_bits": err_bits,
         }
@@ -444,6 +480,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -345,9 +345,12 @@ __device__ __forceinline__ void brick_coords(const DevScene &sc, int lb, int &c0
 // Cooperative load of a brick's tile (all threads; ends with a barrier).  The
 // per-node slot counts and first tile slots come from the descriptor the
 // slot rebuild wrote for this brick; the nodes' first pool slots from the
-// slot table.
-__device__ void tile_load(const World &w, const DevScene &sc, int brick, int c0x, int c0y, int c0z,
+// slot table.  Returns (in every thread) whether every tile node holds at
+// most one logical grid; the kernels then keep the tile's values by node
+// (entry t for tile node t) instead of by tile slot.
+__device__ bool tile_load(const World &w, const DevScene &sc, int brick, int c0x, int c0y, int c0z,
                           Tile &T) {
+  bool single = true;
   for (int t = threadIdx.x; t < TN; t += blockDim.x) {
     const int d = w.B.tdesc[(size_t)brick * TN + t];
     const int cnt = d >> 16;
@@ -359,9 +362,10 @@ __device__ void tile_load(const World &w, const DevScene &sc, int brick, int c0x
     T.lo[t] = (uint16_t)(d & 0xffff);
     T.cnt[t] = (uint8_t)cnt;
     T.goff[t] = off;
+    single &= cnt <= 1;
   }
   if (threadIdx.x == 0) T.total = w.B.ptot[brick];
-  __syncthreads();
+  return __syncthreads_and(single) != 0;
 }
 
 // tile slot holding code (s1, s2) at tile node t, or -1.  Nodes with several
@@ -537,15 +541,106 @@ __global__ void __launch_bounds__(256) k_pre(World w, LaunchSet ls) {
 // k_p2g_brick: the brick's share of P2G (Eq. 2) into its node tile, per
 // logical grid, from the particles' A, J, v staged in shared memory.
 // --------------------------------------------------------------------------
+// Sums of the staged (cell, z-offset) values of tile node t for each of its
+// logical grids (pass `it` over the cells' codes), handed to put(slot
+// entry, sums).  Sources are visited in ascending offset order, so every sum
+// is taken in the same order wherever it is computed.  With `uniform` (one
+// code in the whole brick, one logical grid at every tile node) no source
+// needs a code test: cells without particles staged zeros.
+template <int PPC, int NV, class Put>
+__device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, const float (*stage)[BT],
+                                                 const int *ncode, const uint2 (*ccode)[PPC], int it,
+                                                 int t, bool uniform, int pbase, Put put) {
+  const int n = T.cnt[t];
+  if (n == 0) return;
+  const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
+  const size_t e0 = (size_t)pbase + T.lo[t];
+  const int x0 = max(0, tx - (BR - 1)), x1 = min(2, tx), y0 = max(0, ty - (BR - 1)), y1 = min(2, ty);
+  const int z0 = max(0, tz - (BR - 1)), z1 = min(2, tz);
+  if (uniform) {
+    float acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.f;
+    for (int ozz = z0; ozz <= z1; ++ozz)
+      for (int oyy = y0; oyy <= y1; ++oyy)
+        for (int oxx = x0; oxx <= x1; ++oxx) {
+          const int src = ozz * BR3 + ((tz - ozz) * BR + (ty - oyy)) * BR + (tx - oxx);
+          const int q = (oyy * 3 + oxx) * NV;
+#pragma unroll
+          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][src];
+        }
+    put(e0, acc);
+    return;
+  }
+  for (int sl = 0; sl < n; ++sl) {
+    const uint2 code = n > 1 ? w.S.code[T.goff[t] + sl] : make_uint2(0u, 0u);
+    float acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.f;
+    // offsets o with 0 <= t - o < 4 on every axis, in ascending order
+    for (int ozz = z0; ozz <= z1; ++ozz) {
+      const int zz = tz - ozz;
+      for (int oyy = y0; oyy <= y1; ++oyy) {
+        const int yy = ty - oyy;
+        for (int oxx = x0; oxx <= x1; ++oxx) {
+          const int xx = tx - oxx;
+          const int cc = (zz * BR + yy) * BR + xx;
+          if (it >= ncode[cc]) continue;
+          if (n > 1 && (ccode[cc][it].x != code.x || ccode[cc][it].y != code.y)) continue;
+          const int src = ozz * BR3 + cc, q = (oyy * 3 + oxx) * NV;
+#pragma unroll
+          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][src];
+        }
+      }
+    }
+    put(e0 + sl, acc);
+  }
+}
+
 template <int PPC>
 struct K2S {
   Tile T;
-  float stage[9 * 7][BT];  // per (cell, z-offset) thread: sums for its 9 nodes
+  union {
+    float stage[9 * 7][BT];      // per (cell, z-offset) thread: sums for its 9 nodes
+    float part[18][PPC * BR3];   // the brick's particles (fx, v, A, J), [particle-in-cell][cell]
+  };
+  uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
   uint2 ccode[BR3][PPC];   // distinct codes of each cell (first-occurrence order)
   int ncode[BR3];
   int cs[BR3 + 1];
   int maxcodes;
 };
+
+// Coalesced load of a brick's particles into shared memory, transposed to
+// [particle-in-cell][cell] so that the (cell, z-offset) threads read
+// consecutive words.  Ends with a barrier.
+template <int PPC>
+__device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y, int c0z, K2S<PPC> &S,
+                                bool codes) {
+  for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
+    const int p = bt.z + i;
+    int bx, by, bz;
+    particle_base(P.base[p], bx, by, bz);
+    const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
+    const int si = (i - S.cs[c]) * BR3 + c;
+    S.part[0][si] = P.fx[0][p];
+    S.part[1][si] = P.fx[1][p];
+    S.part[2][si] = P.fx[2][p];
+    S.part[3][si] = P.v[0][p];
+    S.part[4][si] = P.v[1][p];
+    S.part[5][si] = P.v[2][p];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.part[6 + k][si] = P.A[k][p];
+    S.part[15][si] = P.J[0][p];
+    S.part[16][si] = P.J[1][p];
+    S.part[17][si] = P.J[2][p];
+    if (codes) {
+      S.ps1[si] = P.s1[p];
+      S.ps2[si] = P.s2[p];
+    }
+  }
+  __syncthreads();
+}
 
 // distinct codes of each cell, once per cell (threads of z-offset 0).
 // s1/s2 point at particle 0 of the brick's first cell (pool order) when
@@ -578,8 +673,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K2S<PPC> &S = *reinterpret_cast<K2S<PPC> *>(smraw);
   const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
-  DevScene &scm = w.scenes[bt.x];
-  const DevScene &sc = scm;
+  const DevScene &sc = w.scenes[bt.x];
   const PPool &P = w.P;
   const int tid = threadIdx.x;
   const int lb = bt.y - sc.brick_begin;
@@ -588,21 +682,28 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
   for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
   if (tid == 0) S.maxcodes = 0;
-  tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
-  cell_codes<PPC>(P.s1 + bt.z, P.s2 + bt.z, S.cs, true, S.ccode, S.ncode, &S.maxcodes);
+  const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
+  stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, true);
+  cell_codes<PPC>(S.ps1, S.ps2, S.cs, false, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
+  // every tile node holds one logical grid (so all the brick's particles
+  // share one code): the gather needs no code tests
+  const bool uniform_brick = single && S.maxcodes <= 1;
 
-  // ---- phase 1: per (cell, z-offset) sums over the cell's particles ----
+  // ---- per (cell, z-offset) sums over the cell's particles ----
   // Each thread sums, for its cell and one z-offset, m N, m v N and
   // A grad N + N J over the cell's particles of one code (one pass per code
   // present in the cell) into a staging area; then each tile node adds the
   // <= 27 staged sums of the cells around it, in a fixed order, and writes
-  // its slots' partials.  Every float sum has one owner: no atomics.
+  // its slots' partials.  Every float sum has one owner: no atomics.  The
+  // staging area shares its memory with the particle copy, so a brick with
+  // several codes in a cell copies its particles again for each pass.
   const int c = tid % BR3, oz = tid / BR3;
   const int n_c = S.cs[c + 1] - S.cs[c];
   const int iters = S.maxcodes > 0 ? S.maxcodes : 1;  // one pass writes zeros for empty bricks
   const int pbase = w.B.poff[bt.y];  // this brick's partial-sum range (negative: pool overflow)
   for (int it = 0; it < iters; ++it) {
+    if (it > 0) stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, false);
     const bool has = it < S.ncode[c];
     const uint32_t k1 = has ? S.ccode[c][it].x : 0u, k2 = has ? S.ccode[c][it].y : 0u;
     const bool uniform = S.ncode[c] == 1;
@@ -612,81 +713,66 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
 #pragma unroll
       for (int f = 0; f < 7; ++f) a[q][f] = 0.f;
     if (has) {
-      const int p0 = bt.z + S.cs[c];
       for (int j = 0; j < n_c; ++j) {
-        const int p = p0 + j;  // the brick's particles, read through L1
-        if (!uniform && (P.s1[p] != k1 || P.s2[p] != k2)) continue;
+        const int si = j * BR3 + c;
+        if (!uniform && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
         float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
-        const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
+        const float f0 = S.part[0][si], f1 = S.part[1][si], f2 = S.part[2][si];
         bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
         bs<0>(f1, wy[0], dwy[0]); bs<1>(f1, wy[1], dwy[1]); bs<2>(f1, wy[2], dwy[2]);
         bs_rt(oz, f2, wz, dwz);
-        const float v0 = P.v[0][p], v1 = P.v[1][p], v2 = P.v[2][p];
+        const float v0 = S.part[3][si], v1 = S.part[4][si], v2 = S.part[5][si];
         float A[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) A[k] = P.A[k][p];
-        const float J0 = P.J[0][p], J1 = P.J[1][p], J2 = P.J[2][p];
+        for (int k = 0; k < 9; ++k) A[k] = S.part[6 + k][si];
+        const float J0 = S.part[15][si], J1 = S.part[16][si], J2 = S.part[17][si];
 #pragma unroll
         for (int oy = 0; oy < 3; ++oy) {
+          // with N = wx wyz and grad N = (dwx wyz, wx dyz, wx wyd):
+          // A grad N + N J = wx (A_:1 dyz + A_:2 wyd + J wyz) + dwx (A_:0 wyz)
           const float wyz = wy[oy] * wz, dyz = dwy[oy] * wz, wyd = wy[oy] * dwz;
+          const float U0 = A[1] * dyz + A[2] * wyd + J0 * wyz;
+          const float U1 = A[4] * dyz + A[5] * wyd + J1 * wyz;
+          const float U2 = A[7] * dyz + A[8] * wyd + J2 * wyz;
+          const float V0 = A[0] * wyz, V1 = A[3] * wyz, V2 = A[6] * wyz;
+          const float M0 = v0 * wyz, M1 = v1 * wyz, M2 = v2 * wyz;
 #pragma unroll
           for (int ox = 0; ox < 3; ++ox) {
-            const float N = wx[ox] * wyz;
-            const float g0 = dwx[ox] * wyz, g1 = wx[ox] * dyz, g2 = wx[ox] * wyd;
             float *q = a[oy * 3 + ox];
-            q[0] += N;
-            q[1] += N * v0;
-            q[2] += N * v1;
-            q[3] += N * v2;
-            q[4] += A[0] * g0 + A[1] * g1 + A[2] * g2 + N * J0;
-            q[5] += A[3] * g0 + A[4] * g1 + A[5] * g2 + N * J1;
-            q[6] += A[6] * g0 + A[7] * g1 + A[8] * g2 + N * J2;
+            const float wxx = wx[ox], dxx = dwx[ox];
+            q[0] += wxx * wyz;
+            q[1] += wxx * M0;
+            q[2] += wxx * M1;
+            q[3] += wxx * M2;
+            q[4] += wxx * U0 + dxx * V0;
+            q[5] += wxx * U1 + dxx * V1;
+            q[6] += wxx * U2 + dxx * V2;
           }
         }
       }
     }
+    __syncthreads();  // the particle copy is read: the staging area may overwrite it
 #pragma unroll
     for (int q = 0; q < 9; ++q)
 #pragma unroll
       for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][tid] = a[q][f];
     __syncthreads();
-    // tile nodes gather the staged sums of the cells around them
-    if (pbase >= 0)
-      for (int t = tid; t < TN; t += BT) {
-        const int n = S.T.cnt[t];
-        if (n == 0) continue;
-        const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
-        const size_t e0 = (size_t)pbase + S.T.lo[t];
-        for (int sl = 0; sl < n; ++sl) {
-          const uint2 code = n > 1 ? w.S.code[S.T.goff[t] + sl] : make_uint2(0u, 0u);
-          float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          // offsets o with 0 <= t - o < 4 on every axis, in ascending order
-          for (int ozz = max(0, tz - (BR - 1)); ozz <= min(2, tz); ++ozz) {
-            const int zz = tz - ozz;
-            for (int oyy = max(0, ty - (BR - 1)); oyy <= min(2, ty); ++oyy) {
-              const int yy = ty - oyy;
-              for (int oxx = max(0, tx - (BR - 1)); oxx <= min(2, tx); ++oxx) {
-                const int xx = tx - oxx;
-                const int cc = (zz * BR + yy) * BR + xx;
-                if (it >= S.ncode[cc]) continue;
-                if (n > 1 && (S.ccode[cc][it].x != code.x || S.ccode[cc][it].y != code.y)) continue;
-                const int src = ozz * BR3 + cc, q = oyy * 3 + oxx;
-#pragma unroll
-                for (int f = 0; f < 7; ++f) acc[f] += S.stage[q * 7 + f][src];
-              }
-            }
-          }
-          const size_t e = e0 + sl;
-          if (it == 0) {
-            w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            w.B.pd[e] = make_float4(acc[4], acc[5], acc[6], 0.f);
-          } else {
-            const float4 pm = w.B.pm[e], pd = w.B.pd[e];
-            w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], pm.w + acc[3]);
-            w.B.pd[e] = make_float4(pd.x + acc[4], pd.y + acc[5], pd.z + acc[6], 0.f);
-          }
+    // tile nodes gather the staged sums of the cells around them: nodes
+    // 0..191 one per thread, the last 24 one (node, value) per thread
+    if (pbase >= 0) {
+      auto put = [&](size_t e, const float *acc) {  // pm = (m, m v), pd = force sums
+        if (it == 0) {
+          w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+          w.B.pd[e] = make_float4(acc[4], acc[5], acc[6], 0.f);
+        } else {
+          const float4 pm = w.B.pm[e], pd = w.B.pd[e];
+          w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], pm.w + acc[3]);
+          w.B.pd[e] = make_float4(pd.x + acc[4], pd.y + acc[5], pd.z + acc[6], 0.f);
         }
-      }
+      };
+      for (int t = tid; t < TN; t += BT)
+        gather_tile_node<PPC, 7>(w, S.T, S.stage, S.ncode, S.ccode, it, t, uniform_brick, pbase, put);
+    }
     __syncthreads();
   }
 }
@@ -793,7 +879,10 @@ struct K4S {
   Tile T;
   uint2 codes[TSCAP];
   union {
-    float tv[7][TSCAP];       // v_old xyz, m, v_new xyz of the tile slots (G2P)
+    struct {
+      float4 tvo[TSCAP];      // v_old xyz, m of the tile slots (G2P)
+      float4 tvn[TSCAP];      // v_new xyz
+    };
     float stage[9 * 3][BT];   // then: per (cell, z-offset) MUSL sums for 9 nodes
   };
   float pf[3][PPC * BR3];
@@ -820,18 +909,24 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
   for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
   if (tid == 0) S.maxcodes = 0;
-  tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
+  const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
   const int total = S.T.total;
   const bool in_smem = total <= TSCAP;  // otherwise G2P reads the pool slots directly
   const uint2 *tcodes = in_smem ? S.codes : nullptr;
-  if (in_smem) {
+  if (single) {  // by node: a particle's node t holds its (only) logical grid
+    for (int t = tid; t < TN; t += BT) {
+      const bool has = S.T.cnt[t] != 0;
+      const int g = S.T.goff[t];
+      S.tvo[t] = has ? w.S.vold[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      S.tvn[t] = has ? w.S.vnew[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else if (in_smem) {
     for (int t = tid; t < TN; t += BT) {
       const int n = S.T.cnt[t], lo = S.T.lo[t], g = S.T.goff[t];
       for (int a = 0; a < n; ++a) {
         if (n > 1) S.codes[lo + a] = w.S.code[g + a];
-        const float4 o = w.S.vold[g + a], nv = w.S.vnew[g + a];
-        S.tv[0][lo + a] = o.x; S.tv[1][lo + a] = o.y; S.tv[2][lo + a] = o.z; S.tv[3][lo + a] = o.w;
-        S.tv[4][lo + a] = nv.x; S.tv[5][lo + a] = nv.y; S.tv[6][lo + a] = nv.z;
+        S.tvo[lo + a] = w.S.vold[g + a];
+        S.tvn[lo + a] = w.S.vnew[g + a];
       }
     }
   }
@@ -853,6 +948,29 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
     bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
     bs<0>(f2, wz[0], d); bs<1>(f2, wz[1], d); bs<2>(f2, wz[2], d);
     float sn[3] = {0.f, 0.f, 0.f}, so[3] = {0.f, 0.f, 0.f};
+    if (single) {
+      // one logical grid per node, values by node; a node without mass holds
+      // zero velocities, so it needs no test
+      const int t0 = (lz * TE + ly) * TE + lx;
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+          const float wyz = wy[oy] * wz[oz];
+#pragma unroll
+          for (int ox = 0; ox < 3; ++ox) {
+            const int t = t0 + (oz * TE + oy) * TE + ox;
+            const float4 vo = S.tvo[t], vn = S.tvn[t];
+            const float N = wx[ox] * wyz;
+            sn[0] += N * vn.x;
+            sn[1] += N * vn.y;
+            sn[2] += N * vn.z;
+            so[0] += N * vo.x;
+            so[1] += N * vo.y;
+            so[2] += N * vo.z;
+          }
+        }
+    } else
 #pragma unroll
     for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
@@ -864,8 +982,8 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
           if (s < 0) continue;
           float4 vo, vn;
           if (in_smem) {
-            vo = make_float4(S.tv[0][s], S.tv[1][s], S.tv[2][s], S.tv[3][s]);
-            vn = make_float4(S.tv[4][s], S.tv[5][s], S.tv[6][s], 0.f);
+            vo = S.tvo[s];
+            vn = S.tvn[s];
           } else {
             const int g = S.T.goff[t] + s - S.T.lo[t];
             vo = w.S.vold[g];
@@ -903,6 +1021,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   __syncthreads();  // G2P reads of the tile velocities are done: stage may reuse them
   cell_codes<PPC>(S.ps1, S.ps2, S.cs, false, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
+  const bool uniform_brick = single && S.maxcodes <= 1;
   const int iters = S.maxcodes > 0 ? S.maxcodes : 1;
   const int pbase = w.B.poff[bt.y];
   for (int it = 0; it < iters; ++it) {
@@ -940,40 +1059,18 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][tid] = a[q][f];
     __syncthreads();
-    if (pbase >= 0)
-      for (int t = tid; t < TN; t += BT) {
-        const int n = S.T.cnt[t];
-        if (n == 0) continue;
-        const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
-        const size_t e0 = (size_t)pbase + S.T.lo[t];
-        for (int sl = 0; sl < n; ++sl) {
-          const uint2 code = n > 1 ? w.S.code[S.T.goff[t] + sl] : make_uint2(0u, 0u);
-          float acc[3] = {0.f, 0.f, 0.f};
-          for (int ozz = max(0, tz - (BR - 1)); ozz <= min(2, tz); ++ozz) {
-            const int zz = tz - ozz;
-            for (int oyy = max(0, ty - (BR - 1)); oyy <= min(2, ty); ++oyy) {
-              const int yy = ty - oyy;
-              for (int oxx = max(0, tx - (BR - 1)); oxx <= min(2, tx); ++oxx) {
-                const int xx = tx - oxx;
-                const int cc = (zz * BR + yy) * BR + xx;
-                if (it >= S.ncode[cc]) continue;
-                if (n > 1 && (S.ccode[cc][it].x != code.x || S.ccode[cc][it].y != code.y)) continue;
-                const int src = ozz * BR3 + cc, q = oyy * 3 + oxx;
-                acc[0] += S.stage[q * 3 + 0][src];
-                acc[1] += S.stage[q * 3 + 1][src];
-                acc[2] += S.stage[q * 3 + 2][src];
-              }
-            }
-          }
-          const size_t e = e0 + sl;
-          if (it == 0) {
-            w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], 0.f);
-          } else {
-            const float4 pm = w.B.pm[e];
-            w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], 0.f);
-          }
+    if (pbase >= 0) {
+      auto put = [&](size_t e, const float *acc) {  // pm = MUSL momentum sums
+        if (it == 0) {
+          w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], 0.f);
+        } else {
+          const float4 pm = w.B.pm[e];
+          w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], 0.f);
         }
-      }
+      };
+      for (int t = tid; t < TN; t += BT)
+        gather_tile_node<PPC, 3>(w, S.T, S.stage, S.ncode, S.ccode, it, t, uniform_brick, pbase, put);
+    }
     __syncthreads();
   }
 }
@@ -1048,7 +1145,7 @@ __global__ void k_musl_node(World w, LaunchSet ls) {
 struct K1S {
   Tile T;
   uint2 codes[TSCAP];
-  float tvs[3][TSCAP];
+  float4 tvs[TSCAP];
   int any;
 };
 
@@ -1064,18 +1161,18 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
   int c0x, c0y, c0z;
   brick_coords(sc, lb, c0x, c0y, c0z);
   if (tid == 0) S.any = 0;
-  tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
+  const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
   const bool in_smem = S.T.total <= TSCAP;
   const uint2 *tcodes = in_smem ? S.codes : nullptr;
-  if (in_smem) {
+  if (single) {  // by node
+    for (int t = tid; t < TN; t += BT)
+      S.tvs[t] = S.T.cnt[t] ? w.S.vstar[S.T.goff[t]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else if (in_smem) {
     for (int t = tid; t < TN; t += BT) {
       const int n = S.T.cnt[t], lo = S.T.lo[t], g = S.T.goff[t];
       for (int a = 0; a < n; ++a) {
         if (n > 1) S.codes[lo + a] = w.S.code[g + a];
-        const float4 v = w.S.vstar[g + a];
-        S.tvs[0][lo + a] = v.x;
-        S.tvs[1][lo + a] = v.y;
-        S.tvs[2][lo + a] = v.z;
+        S.tvs[lo + a] = w.S.vstar[g + a];
       }
     }
   }
@@ -1095,32 +1192,40 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
     bs<0>(f1, wy[0], gy[0]); bs<1>(f1, wy[1], gy[1]); bs<2>(f1, wy[2], gy[2]);
     bs<0>(f2, wz[0], gz[0]); bs<1>(f2, wz[1], gz[1]); bs<2>(f2, wz[2], gz[2]);
     float G[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int t0 = (lz * TE + ly) * TE + lx;
 #pragma unroll
     for (int oz = 0; oz < 3; ++oz)
 #pragma unroll
-      for (int oy = 0; oy < 3; ++oy)
+      for (int oy = 0; oy < 3; ++oy) {
+        // grad N = (gx wyz, wx gyz, wx wgz): sum v* gx and v* wx along the
+        // row of three nodes first, then scale by the row's y-z factors
+        const float wyz = wy[oy] * wz[oz], gyz = gy[oy] * wz[oz], wgz = wy[oy] * gz[oz];
+        float sx[3] = {0.f, 0.f, 0.f}, sw[3] = {0.f, 0.f, 0.f};
+        if (single) {  // by node; nodes without mass hold v* = 0
 #pragma unroll
-        for (int ox = 0; ox < 3; ++ox) {
-          const int t = ((lz + oz) * TE + (ly + oy)) * TE + (lx + ox);
-          const int s = tile_slot(w, S.T, tcodes, t, s1, s2);
-          if (s < 0) continue;
-          float v0, v1, v2;
-          if (in_smem) {
-            v0 = S.tvs[0][s];
-            v1 = S.tvs[1][s];
-            v2 = S.tvs[2][s];
-          } else {
-            const float4 v = w.S.vstar[S.T.goff[t] + s - S.T.lo[t]];
-            v0 = v.x;
-            v1 = v.y;
-            v2 = v.z;
+          for (int ox = 0; ox < 3; ++ox) {
+            const float4 v = S.tvs[t0 + (oz * TE + oy) * TE + ox];
+            sx[0] += v.x * gx[ox]; sx[1] += v.y * gx[ox]; sx[2] += v.z * gx[ox];
+            sw[0] += v.x * wx[ox]; sw[1] += v.y * wx[ox]; sw[2] += v.z * wx[ox];
           }
-          const float g0 = gx[ox] * wy[oy] * wz[oz], g1 = wx[ox] * gy[oy] * wz[oz],
-                      g2 = wx[ox] * wy[oy] * gz[oz];
-          G[0] += v0 * g0; G[1] += v0 * g1; G[2] += v0 * g2;
-          G[3] += v1 * g0; G[4] += v1 * g1; G[5] += v1 * g2;
-          G[6] += v2 * g0; G[7] += v2 * g1; G[8] += v2 * g2;
+        } else {
+#pragma unroll
+          for (int ox = 0; ox < 3; ++ox) {
+            const int t = t0 + (oz * TE + oy) * TE + ox;
+            const int s = tile_slot(w, S.T, tcodes, t, s1, s2);
+            if (s < 0) continue;
+            const float4 v = in_smem ? S.tvs[s] : w.S.vstar[S.T.goff[t] + s - S.T.lo[t]];
+            sx[0] += v.x * gx[ox]; sx[1] += v.y * gx[ox]; sx[2] += v.z * gx[ox];
+            sw[0] += v.x * wx[ox]; sw[1] += v.y * wx[ox]; sw[2] += v.z * wx[ox];
+          }
         }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          G[3 * a] += sx[a] * wyz;
+          G[3 * a + 1] += sw[a] * gyz;
+          G[3 * a + 2] += sw[a] * wgz;
+        }
+      }
 #pragma unroll
     for (int k = 0; k < 9; ++k) P.F[k][p] += c * G[k];
     const uint8_t pend = P.pend[p];
