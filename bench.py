@@ -49,7 +49,8 @@ FALLBACK_HBM_GBS = 6800.0
 # and writes of each kernel's own inputs and outputs, with brick-tile
 # partials counted at 3.375 tiles per slot (6^3 tile nodes per 4^3 cells).
 KERNEL_MODEL = {
-    "k_p2g_brick": {"bytes": (117, 0, 108, 480), "flops": (1050, 0, 0, 0)},
+    "k_pre": {"bytes": (149, 0, 0, 0), "flops": (420, 0, 0, 0)},
+    "k_p2g_brick": {"bytes": (84, 0, 108, 2000), "flops": (1050, 0, 0, 0)},
     "k_p2g_node": {"bytes": (0, 12, 140, 0), "flops": (0, 0, 40, 0)},
     "k_g2p_musl": {"bytes": (72, 0, 162, 1080), "flops": (570, 0, 0, 0)},
     "k_musl_node": {"bytes": (0, 12, 86, 0), "flops": (0, 0, 20, 0)},

@@ -613,7 +613,7 @@ struct K2S {
 
 // Coalesced load of a brick's particles into shared memory, transposed to
 // [particle-in-cell][cell] so that the (cell, z-offset) threads read
-// consecutive words.  Ends with a barrier.
+// consecutive words.  The caller provides the barrier that publishes it.
 template <int PPC>
 __device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y, int c0z, K2S<PPC> &S,
                                 bool codes) {
@@ -639,7 +639,6 @@ __device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y
       S.ps2[si] = P.s2[p];
     }
   }
-  __syncthreads();
 }
 
 // distinct codes of each cell, once per cell (threads of z-offset 0).
@@ -682,8 +681,10 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   const int *csg = w.N.cell_start + sc.cell_begin + lb * BR3;
   for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
   if (tid == 0) S.maxcodes = 0;
-  const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
+  __syncthreads();
+  // the particle copy and the tile descriptors load together (one barrier)
   stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, true);
+  const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
   cell_codes<PPC>(S.ps1, S.ps2, S.cs, false, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
   // every tile node holds one logical grid (so all the brick's particles
@@ -703,7 +704,10 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   const int iters = S.maxcodes > 0 ? S.maxcodes : 1;  // one pass writes zeros for empty bricks
   const int pbase = w.B.poff[bt.y];  // this brick's partial-sum range (negative: pool overflow)
   for (int it = 0; it < iters; ++it) {
-    if (it > 0) stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, false);
+    if (it > 0) {
+      stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, false);
+      __syncthreads();
+    }
     const bool has = it < S.ncode[c];
     const uint32_t k1 = has ? S.ccode[c][it].x : 0u, k2 = has ? S.ccode[c][it].y : 0u;
     const bool uniform = S.ncode[c] == 1;
