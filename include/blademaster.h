@@ -331,8 +331,8 @@ const char *bm_kernel_name(int i);
 /* Launch shape used by subsequent bm_batch_step calls (set by the
  * autotuner): substeps per captured CUDA graph (1..256), nodes per CTA of the
  * per-node kernels (multiple of 32 in 64..512) and the brick-kernel
- * occupancy variant (0: 3/4/5 resident CTAs per SM for P2G, G2P+MUSL and the
- * F update; 1: 2/3/4, more registers per thread; 2: 4/5/6).  Results do not
+ * occupancy variant (0: 3/5/7 resident CTAs per SM for P2G, G2P+MUSL and the
+ * F update; 1: 2/4/5, more registers per thread; 2: 4/6/8).  Results do not
  * depend on any of them: every sum is taken in a fixed order and the
  * variants share their arithmetic.  Synchronises the batch stream; captured
  * graphs are rebuilt on the next step.  BM_E_INVALID on an out-of-range

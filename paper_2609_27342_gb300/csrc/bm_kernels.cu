@@ -397,8 +397,8 @@ __device__ __forceinline__ int tile_slot(const World &w, const Tile &T, const ui
 // reaction wrench (Eq. 16), side label for the next substep (Eq. 3, 4, 6),
 // and A = -dt V0 P(F) / dx with the total impulse J for P2G.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pre(World w, LaunchSet ls) {
-  __shared__ float red[6][8];
+__global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
+  __shared__ float red[6][4];
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
   const DevScene &sc = scm;
@@ -1933,9 +1933,9 @@ cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t 
 // thread, more CTAs hide more latency.  The arithmetic is the same in every
 // variant, so results are bit-identical; the batch autotuner picks one.
 template <int V> struct Occ;
-template <> struct Occ<0> { static constexpr int p2g = 3, g2p = 4, fupd = 5; };
-template <> struct Occ<1> { static constexpr int p2g = 2, g2p = 3, fupd = 4; };
-template <> struct Occ<2> { static constexpr int p2g = 4, g2p = 5, fupd = 6; };
+template <> struct Occ<0> { static constexpr int p2g = 3, g2p = 5, fupd = 7; };
+template <> struct Occ<1> { static constexpr int p2g = 2, g2p = 4, fupd = 5; };
+template <> struct Occ<2> { static constexpr int p2g = 4, g2p = 6, fupd = 8; };
 
 template <int PPC, int V>
 static cudaError_t set_smem_attrs() {
@@ -1968,7 +1968,7 @@ cudaError_t bm_kernels_init() {
 template <int PPC, int V>
 static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   rec(ev, 18, 0, st);
-  k_pre<<<ls.n_btiles, 256, 0, st>>>(w, ls);
+  k_pre<<<ls.n_btiles, 128, 0, st>>>(w, ls);
   rec(ev, 18, 1, st);
   rec(ev, 0, 0, st);
   k_p2g_brick<PPC, Occ<V>::p2g><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
