@@ -18,7 +18,7 @@
 #include "../../include/blademaster.h"
 
 #define BM_MAXS 16           // logical grids (distinct codes) per node
-#define BM_TILE_SLOTS 648    // tile slots cached in shared memory (3 per tile node); more use the pool
+#define BM_TILE_SLOTS 512    // tile slots cached in shared memory; tiles with more read the pool
 #define BM_TILE_NODES 216    // 6 x 6 x 6 nodes touched by a brick of 4 x 4 x 4 base cells
 #define BM_BRICK_CELLS 64
 #define BM_HIST 16           // pair-contact history entries per particle

@@ -549,7 +549,8 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
 // needs a code test: cells without particles staged zeros.
 template <int PPC, int NV, class Put>
 __device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, const float (*stage)[BT],
-                                                 const int *ncode, const uint2 (*ccode)[PPC], int it,
+                                                 const uint8_t *ncode, const uint8_t (*ccode)[PPC],
+                                                 const uint32_t *ps1, const uint32_t *ps2, int it,
                                                  int t, bool uniform, int pbase, Put put) {
   const int n = T.cnt[t];
   if (n == 0) return;
@@ -586,7 +587,10 @@ __device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, 
           const int xx = tx - oxx;
           const int cc = (zz * BR + yy) * BR + xx;
           if (it >= ncode[cc]) continue;
-          if (n > 1 && (ccode[cc][it].x != code.x || ccode[cc][it].y != code.y)) continue;
+          if (n > 1) {
+            const int k = ccode[cc][it] * BR3 + cc;
+            if (ps1[k] != code.x || ps2[k] != code.y) continue;
+          }
           const int src = ozz * BR3 + cc, q = (oyy * 3 + oxx) * NV;
 #pragma unroll
           for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][src];
@@ -605,8 +609,9 @@ struct K2S {
     float part[18][PPC * BR3];   // the brick's particles (fx, v, A, J), [particle-in-cell][cell]
   };
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
-  uint2 ccode[BR3][PPC];   // distinct codes of each cell (first-occurrence order)
-  int ncode[BR3];
+  uint8_t ccode[BR3][PPC];  // distinct codes of each cell: particle-in-cell index of the
+                            // first particle with each code (first-occurrence order)
+  uint8_t ncode[BR3];
   int cs[BR3 + 1];
   int maxcodes;
 };
@@ -641,9 +646,33 @@ __device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y
   }
 }
 
-// distinct codes of each cell, once per cell (threads of z-offset 0).
-// s1/s2 point at particle 0 of the brick's first cell (pool order) when
-// stride == 1, or at the [particle-in-cell][cell] staging when stride == 0.
+// distinct codes of each cell, once per cell (threads of z-offset 0), from
+// the [particle-in-cell][cell] staging of the codes: each code is kept as the
+// particle-in-cell index of its first particle.
+template <int PPC>
+__device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s2, const int *cs,
+                                           uint8_t (*ccode)[PPC], uint8_t *ncode, int *maxcodes) {
+  const int c = threadIdx.x;
+  if (c >= BR3) return;
+  const int n = cs[c + 1] - cs[c];
+  int cnt = 0;
+  for (int j = 0; j < n; ++j) {
+    const int k = j * BR3 + c;
+    const uint32_t a = s1[k], b = s2[k];
+    bool seen = false;
+    for (int q = 0; q < cnt; ++q) {
+      const int kq = ccode[c][q] * BR3 + c;
+      if (s1[kq] == a && s2[kq] == b) {
+        seen = true;
+        break;
+      }
+    }
+    if (!seen) ccode[c][cnt++] = (uint8_t)j;
+  }
+  ncode[c] = (uint8_t)cnt;
+  atomicMax(maxcodes, cnt);
+}
+
 template <int PPC>
 __device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s2, const int *cs,
                                            bool pool_order, uint2 (*ccode)[PPC], int *ncode,
@@ -685,7 +714,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   // the particle copy and the tile descriptors load together (one barrier)
   stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, true);
   const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
-  cell_codes<PPC>(S.ps1, S.ps2, S.cs, false, S.ccode, S.ncode, &S.maxcodes);
+  cell_codes<PPC>(S.ps1, S.ps2, S.cs, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
   // every tile node holds one logical grid (so all the brick's particles
   // share one code): the gather needs no code tests
@@ -709,7 +738,8 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
       __syncthreads();
     }
     const bool has = it < S.ncode[c];
-    const uint32_t k1 = has ? S.ccode[c][it].x : 0u, k2 = has ? S.ccode[c][it].y : 0u;
+    const int kc = has ? S.ccode[c][it] * BR3 + c : 0;
+    const uint32_t k1 = has ? S.ps1[kc] : 0u, k2 = has ? S.ps2[kc] : 0u;
     const bool uniform = S.ncode[c] == 1;
     float a[9][7];
 #pragma unroll
@@ -775,7 +805,8 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
         }
       };
       for (int t = tid; t < TN; t += BT)
-        gather_tile_node<PPC, 7>(w, S.T, S.stage, S.ncode, S.ccode, it, t, uniform_brick, pbase, put);
+        gather_tile_node<PPC, 7>(w, S.T, S.stage, S.ncode, S.ccode, S.ps1, S.ps2, it, t, uniform_brick,
+                                 pbase, put);
     }
     __syncthreads();
   }
@@ -892,8 +923,8 @@ struct K4S {
   float pf[3][PPC * BR3];
   float pv[3][PPC * BR3];
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
-  uint2 ccode[BR3][PPC];
-  int ncode[BR3];
+  uint8_t ccode[BR3][PPC];  // as in K2S
+  uint8_t ncode[BR3];
   int cs[BR3 + 1];
   int maxcodes;
 };
@@ -1023,14 +1054,15 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   const int c = tid % BR3, oz = tid / BR3;
   const int n_c = S.cs[c + 1] - S.cs[c];
   __syncthreads();  // G2P reads of the tile velocities are done: stage may reuse them
-  cell_codes<PPC>(S.ps1, S.ps2, S.cs, false, S.ccode, S.ncode, &S.maxcodes);
+  cell_codes<PPC>(S.ps1, S.ps2, S.cs, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
   const bool uniform_brick = single && S.maxcodes <= 1;
   const int iters = S.maxcodes > 0 ? S.maxcodes : 1;
   const int pbase = w.B.poff[bt.y];
   for (int it = 0; it < iters; ++it) {
     const bool has = it < S.ncode[c];
-    const uint32_t k1 = has ? S.ccode[c][it].x : 0u, k2 = has ? S.ccode[c][it].y : 0u;
+    const int kc = has ? S.ccode[c][it] * BR3 + c : 0;
+    const uint32_t k1 = has ? S.ps1[kc] : 0u, k2 = has ? S.ps2[kc] : 0u;
     const bool uniform = S.ncode[c] == 1;
     float a[9][3];
 #pragma unroll
@@ -1073,7 +1105,8 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
         }
       };
       for (int t = tid; t < TN; t += BT)
-        gather_tile_node<PPC, 3>(w, S.T, S.stage, S.ncode, S.ccode, it, t, uniform_brick, pbase, put);
+        gather_tile_node<PPC, 3>(w, S.T, S.stage, S.ncode, S.ccode, S.ps1, S.ps2, it, t, uniform_brick,
+                                 pbase, put);
     }
     __syncthreads();
   }
