@@ -105,7 +105,7 @@ struct NPool {
   int *slot_off;            // first slot of each node (pool slot index)
   uint8_t *slot_cnt;        // logical grids at each node
   uint8_t *ncodes;          // distinct codes found at each node by the last recount
-  uint8_t *dirty;           // per base cell: a particle gained a label since the last recount
+  uint8_t *dirty;           // per node: a particle of its stencil gained a label since the last recount
   uint2 *tmp_codes;         // [node * BM_MAXS] scratch for the rebuild
   int *tile_sum;            // per node tile: slots in the tile (scan scratch)
 };

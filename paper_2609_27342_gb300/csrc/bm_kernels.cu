@@ -553,7 +553,9 @@ __device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, 
                                                  const uint32_t *ps1, const uint32_t *ps2, int it,
                                                  int t, bool uniform, int pbase, Put put) {
   const int n = T.cnt[t];
-  if (n == 0) return;
+  // a node with one logical grid sees one code in every source cell (each
+  // particle of a source cell touches it), so passes after the first add nothing
+  if (n == 0 || (it > 0 && n == 1)) return;
   const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
   const size_t e0 = (size_t)pbase + T.lo[t];
   const int x0 = max(0, tx - (BR - 1)), x1 = min(2, tx), y0 = max(0, ty - (BR - 1)), y1 = min(2, ty);
@@ -619,14 +621,17 @@ struct K2S {
 // Coalesced load of a brick's particles into shared memory, transposed to
 // [particle-in-cell][cell] so that the (cell, z-offset) threads read
 // consecutive words.  The caller provides the barrier that publishes it.
+// With pass > 0 only the particles of cells holding more than `pass` codes
+// are copied (the only ones that pass reads).
 template <int PPC>
 __device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y, int c0z, K2S<PPC> &S,
-                                bool codes) {
+                                bool codes, int pass = 0) {
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
     int bx, by, bz;
     particle_base(P.base[p], bx, by, bz);
     const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
+    if (pass > 0 && S.ncode[c] <= pass) continue;
     const int si = (i - S.cs[c]) * BR3 + c;
     S.part[0][si] = P.fx[0][p];
     S.part[1][si] = P.fx[1][p];
@@ -734,7 +739,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   const int pbase = w.B.poff[bt.y];  // this brick's partial-sum range (negative: pool overflow)
   for (int it = 0; it < iters; ++it) {
     if (it > 0) {
-      stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, false);
+      stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, false, it);
       __syncthreads();
     }
     const bool has = it < S.ncode[c];
@@ -786,10 +791,13 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
       }
     }
     __syncthreads();  // the particle copy is read: the staging area may overwrite it
+    // the gather reads a cell's sums only when the cell holds an it-th code
+    // (pass 0 also reads the zeros of empty cells)
+    if (it == 0 || has)
 #pragma unroll
-    for (int q = 0; q < 9; ++q)
+      for (int q = 0; q < 9; ++q)
 #pragma unroll
-      for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][tid] = a[q][f];
+        for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][tid] = a[q][f];
     __syncthreads();
     // tile nodes gather the staged sums of the cells around them: nodes
     // 0..191 one per thread, the last 24 one (node, value) per thread
@@ -1090,10 +1098,11 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
         }
       }
     }
+    if (it == 0 || has)
 #pragma unroll
-    for (int q = 0; q < 9; ++q)
+      for (int q = 0; q < 9; ++q)
 #pragma unroll
-      for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][tid] = a[q][f];
+        for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][tid] = a[q][f];
     __syncthreads();
     if (pbase >= 0) {
       auto put = [&](size_t e, const float *acc) {  // pm = MUSL momentum sums
@@ -1271,7 +1280,10 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
       else P.s2[p] = s2 | (1u << cut);
       any = true;
       // the nodes of this particle's stencil need their codes recounted
-      w.N.dirty[sc.cell_begin + cell_index(sc, bx, by, bz)] = 1;
+      for (int oz = 0; oz < 3; ++oz)
+        for (int oy = 0; oy < 3; ++oy)
+          for (int ox = 0; ox < 3; ++ox)
+            w.N.dirty[sc.node_begin + ((bz + oz) * sc.nn[1] + (by + oy)) * sc.nn[0] + (bx + ox)] = 1;
     }
   }
   if (any) S.any = 1;
@@ -1718,18 +1730,9 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   bool recount = force != 0;
   if (i < t.z) {
     node_coords(sc, node - sc.node_begin, ix, iy, iz);
-    // only nodes whose neighbourhood holds a newly labelled particle are
-    // recounted; the others keep their distinct codes from the last rebuild
-    for (int oz = 0; oz < 3 && !recount; ++oz)
-      for (int oy = 0; oy < 3 && !recount; ++oy)
-        for (int ox = 0; ox < 3; ++ox) {
-          const int bx = ix - ox, by = iy - oy, bz = iz - oz;
-          if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) continue;
-          if (w.N.dirty[sc.cell_begin + cell_index(sc, bx, by, bz)]) {
-            recount = true;
-            break;
-          }
-        }
+    // only nodes next to a newly labelled particle are recounted; the others
+    // keep their distinct codes from the last rebuild
+    recount |= w.N.dirty[node] != 0;
   }
   if (i < t.z && !recount) cnt = w.N.ncodes[node];
   else if (i < t.z) {
@@ -1758,6 +1761,7 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
         }
     if (over) atomicOr(&sc.err, BM_ERRBIT_SLOT_OVERFLOW);
     w.N.ncodes[node] = (uint8_t)cnt;
+    w.N.dirty[node] = 0;
     for (int a = 0; a < cnt; ++a)
       w.N.tmp_codes[(size_t)node * BM_MAXS + a] = make_uint2((uint32_t)keys[a], (uint32_t)(keys[a] >> 32));
   }
@@ -1787,7 +1791,6 @@ __global__ void k_brick_tiles(World w, LaunchSet ls, int force) {
   const int ex = block_excl_scan(cnt, sm, total);
   if (t < TN) w.B.tdesc[(size_t)bt.y * TN + t] = ex | (cnt << 16);
   if (t == 0) w.B.ptot[bt.y] = total;
-  if (t < BR3) w.N.dirty[sc.cell_begin + (bt.y - sc.brick_begin) * BR3 + t] = 0;  // recounted
 }
 
 // per scene: slot offsets of the node tiles, and partial-sum ranges of the bricks

@@ -231,7 +231,7 @@ int world_alloc(WorldH *W) {
   I(np.slot_off, W->cap_node);
   np.slot_cnt = W->get<uint8_t>(W->cap_node);
   np.ncodes = W->get<uint8_t>(W->cap_node);
-  np.dirty = W->get<uint8_t>(W->cap_cell);
+  np.dirty = W->get<uint8_t>(W->cap_node);
   ok &= np.slot_cnt && np.ncodes && np.dirty;
   np.tmp_codes = W->get<uint2>(W->cap_node * BM_MAXS);
   ok &= np.tmp_codes != nullptr;
