@@ -364,6 +364,42 @@ def run_native(args):
                    "particle_substeps_per_s_fwd_bwd": spec.n * na / t_fb}
         log(f"adjoint: {adjoint}")
 
+    # single-cut cuboid (16,000 particles, plain path) and the cylinder with
+    # two intersecting cuts, a push, a two-way tool and pair contact (about
+    # 251k particles, plain path), timed once the blade is in the material
+    configs = None
+    if args.configs and rank == 0:
+        configs = {}
+        sc0 = bi.single_cut_cuboid()
+        g0 = pkg.Scene(sc0, stream=stream)
+        g0.step(10)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g0.step(100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r0 = sc0.n * 100 / (e0.elapsed_time(e1) * 1e-3)
+        g0.close()
+        configs["single_cut"] = {"workload": "single-cut neo-Hookean cuboid, 16,000 particles",
+                                 "path": "plain (one scene per launch)", "value": r0, "unit": UNIT,
+                                 "substeps_timed": 100}
+        sc1 = bi.cylinder_cuts_push()
+        g1 = pkg.Scene(sc1, stream=stream)
+        g1.step(100)  # the blade reaches the top of the cylinder
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g1.step(200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r1 = sc1.n * 200 / (e0.elapsed_time(e1) * 1e-3)
+        configs["cylinder"] = {"workload": "cylinder 0.2 m x r 0.02 m, dx 2 mm, two intersecting "
+                                           "cuts and a push, 0.2 kg two-way tool, pair contact",
+                               "particles": sc1.n, "path": "plain (one scene per launch)",
+                               "value": r1, "unit": UNIT, "substeps_timed": 200,
+                               "first_substep": 100, "error_bits": int(g1.info().error_bits)}
+        g1.close()
+        log(f"configs: {configs}")
+
     # continuous-batching server on a Poisson request stream (rollouts of
     # 8k-500k particles, 200-2000 substeps, 1-3 cuts), admission by an HBM budget
     serving = None
@@ -393,6 +429,14 @@ def run_native(args):
                "sample": f"first 16 of the 256 scenes ({sum(s.n for s in sample)} particles), "
                          f"{rounds} substeps each, FP64 C oracle, one scene per thread, "
                          f"{wall_c:.1f} s wall"}
+        # the single-cut cuboid (16,000 particles) on one host core
+        from oracle import oracle as O
+        o0 = O.OracleScene(bi.single_cut_cuboid())
+        t0 = time.perf_counter()
+        o0.step(10)
+        cpu["single_cut_1_core"] = {"value": o0.n * 10 / (time.perf_counter() - t0), "unit": UNIT,
+                                    "sample": "substeps 0-9 of the 16,000-particle single-cut "
+                                              "cuboid, FP64 oracle, one thread"}
 
     if rank == 0:
         line = {
@@ -419,6 +463,7 @@ def run_native(args):
             "clocks": clk,
             "serving": serving,
             "adjoint": adjoint,
+            "configs": configs,
             "cpu_baseline": cpu,
             "error_bits": err_bits,
         }
@@ -482,6 +527,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
+    ap.add_argument("--no-configs", dest="configs", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
