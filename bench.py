@@ -181,6 +181,25 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_scenes(rank: int):
+    """The batch of one rank: 256 uneven scenes seeded per rank (rank 0 uses
+    the workload's seed), so ranks hold independent shards of the work."""
+    return bi.batched_scenes(N_SCENES, seed=SEED + rank, n_substeps=100000)
+
+
+def reduce_over_ranks(dist, ms: float, particles: int, device="cuda"):
+    """(max of the timed milliseconds, sum of the particles) over all ranks;
+    the job's throughput is the summed work over the slowest rank's time."""
+    if dist is None:
+        return ms, particles
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(particles)], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(n.item()))
+
+
 def run_native(args):
     import torch
     world, rank, local = dist_setup()
@@ -194,7 +213,7 @@ def run_native(args):
     import paper_2609_27342_gb300 as pkg
     pkg.load()
 
-    scenes = bi.batched_scenes(N_SCENES, seed=SEED, n_substeps=100000)
+    scenes = rank_scenes(rank)
     n_particles = sum(s.n for s in scenes)
     stream = torch.cuda.Stream()
     fps = [pkg.footprint(s) for s in scenes]
@@ -271,12 +290,8 @@ def run_native(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_particles * args.steps / (ms * 1e-3)
+    ms, job_particles = reduce_over_ranks(dist, e0.elapsed_time(e1), n_particles)
+    value = job_particles * args.steps / (ms * 1e-3)
     err_bits = batch.errors()
 
     # per-kernel device times over the same number of substeps (live events)
@@ -326,14 +341,14 @@ def run_native(args):
         batch.set_tool_states_ptr(h_states.data_ptr(), n, False)
         batch.step(1)
         batch.tool_wrenches_ptr(h_wr.data_ptr(), n, False)
-    wall = time.perf_counter() - t0
-    e2e_value = world * n_particles * e2e_steps / wall
+    wall, _ = reduce_over_ranks(dist, (time.perf_counter() - t0) * 1e3, n_particles)
+    e2e_value = job_particles * e2e_steps / (wall * 1e-3)
 
     # adjoint calibration workload: 32,000 particles, 200 substeps, checkpoint
     # every 20, loss on the reaction-force trajectory against a target made at
     # E = 1.5e5 Pa; gradient vs central differences (relative step 1e-3)
     adjoint = None
-    if args.adjoint:
+    if args.adjoint and rank == 0:
         from paper_2609_27342_gb300.calibration import force_loss_and_grad, forces
         na = 200
         target = forces(bi.calibration_scene(E=1.5e5), na)
@@ -444,6 +459,7 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "scenes": N_SCENES, "particles": n_particles,
+                       "job_particles": job_particles, "seeds": f"{SEED}..{SEED + world - 1} (one per rank)",
                        "nodes": n_nodes, "slots": n_slots, "seed": SEED,
                        "bricks": n_bricks, "substeps_timed": args.steps,
                        "launch_shape": shape,
