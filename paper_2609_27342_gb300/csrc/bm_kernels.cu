@@ -827,6 +827,31 @@ __device__ __forceinline__ void covering(int i, int nbr, int &first, int &last) 
   if (i - (TE - 1) < 0) first = 0;
 }
 
+// First partial-sum entry of a node in each of the (up to 8) brick tiles that
+// cover it, in brick order (k = dz*4 + dy*2 + dx over the covering bricks'
+// offsets); -1 where no brick or where the brick's partials overflowed.  All
+// loads of the eight candidates are issued together.
+__device__ __forceinline__ void covering_entries(const World &w, const DevScene &sc, int ix, int iy, int iz,
+                                                 long long e[8]) {
+  int x0, x1, y0, y1, z0, z1;
+  covering(ix, sc.nbr[0], x0, x1);
+  covering(iy, sc.nbr[1], y0, y1);
+  covering(iz, sc.nbr[2], z0, z1);
+  int b[8], tt[8], pb[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int Bx = x0 + (k & 1), By = y0 + ((k >> 1) & 1), Bz = z0 + (k >> 2);
+    const bool ok = Bx <= x1 && By <= y1 && Bz <= z1;
+    b[k] = ok ? sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx : -1;
+    tt[k] = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) pb[k] = b[k] >= 0 ? w.B.poff[b[k]] : -1;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    e[k] = pb[k] >= 0 ? (long long)pb[k] + (w.B.tdesc[(size_t)b[k] * TN + tt[k]] & 0xffff) : -1;
+}
+
 // --------------------------------------------------------------------------
 // k_p2g_node: per node, sum the tile partials of the bricks covering it (in
 // brick order), couple compatible logical grids (Eq. 8), grid update (Eq. 9)
@@ -842,25 +867,22 @@ __global__ void k_p2g_node(World w, LaunchSet ls) {
   const int off = w.N.slot_off[node];
   int ix, iy, iz;
   node_coords(sc, node - sc.node_begin, ix, iy, iz);
-  int x0, x1, y0, y1, z0, z1;
-  covering(ix, sc.nbr[0], x0, x1);
-  covering(iy, sc.nbr[1], y0, y1);
-  covering(iz, sc.nbr[2], z0, z1);
+  long long ent[8];
+  covering_entries(w, sc, ix, iy, iz, ent);
   if (ns == 1) {
     float4 sm = make_float4(0.f, 0.f, 0.f, 0.f), sd = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int Bz = z0; Bz <= z1; ++Bz)
-      for (int By = y0; By <= y1; ++By)
-        for (int Bx = x0; Bx <= x1; ++Bx) {
-          const int b = sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx;
-          const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
-          const int pb = w.B.poff[b];
-          if (pb < 0) continue;
-          const size_t e = (size_t)pb + (w.B.tdesc[(size_t)b * TN + tt] & 0xffff);
-          const float4 a = w.B.pm[e];
-          const float4 d = w.B.pd[e];
-          sm.x += a.x; sm.y += a.y; sm.z += a.z; sm.w += a.w;
-          sd.x += d.x; sd.y += d.y; sd.z += d.z;
-        }
+    float4 a[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      a[k] = ent[k] >= 0 ? w.B.pm[ent[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      d[k] = ent[k] >= 0 ? w.B.pd[ent[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (ent[k] < 0) continue;
+      sm.x += a[k].x; sm.y += a[k].y; sm.z += a[k].z; sm.w += a[k].w;
+      sd.x += d[k].x; sd.y += d[k].y; sd.z += d[k].z;
+    }
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f), nw = make_float4(0.f, 0.f, 0.f, 0.f);
     if (sm.x > 0.f) {
       const float im = 1.0f / sm.x, imm = 1.0f / (sc.mp * sm.x);
@@ -879,22 +901,17 @@ __global__ void k_p2g_node(World w, LaunchSet ls) {
     m[a] = 0.f;
     for (int c = 0; c < 6; ++c) S[a][c] = 0.f;
   }
-  for (int Bz = z0; Bz <= z1; ++Bz)
-    for (int By = y0; By <= y1; ++By)
-      for (int Bx = x0; Bx <= x1; ++Bx) {
-        const int b = sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx;
-        const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
-        const int pb = w.B.poff[b];
-        if (pb < 0) continue;
-        const size_t e = (size_t)pb + (w.B.tdesc[(size_t)b * TN + tt] & 0xffff);
-        for (int a = 0; a < ns; ++a) {
-          const float4 q = w.B.pm[e + a];
-          const float4 d = w.B.pd[e + a];
-          m[a] += q.x;
-          S[a][0] += q.y; S[a][1] += q.z; S[a][2] += q.w;
-          S[a][3] += d.x; S[a][4] += d.y; S[a][5] += d.z;
-        }
-      }
+  for (int k = 0; k < 8; ++k) {
+    if (ent[k] < 0) continue;
+    const size_t e = (size_t)ent[k];
+    for (int a = 0; a < ns; ++a) {
+      const float4 q = w.B.pm[e + a];
+      const float4 d = w.B.pd[e + a];
+      m[a] += q.x;
+      S[a][0] += q.y; S[a][1] += q.z; S[a][2] += q.w;
+      S[a][3] += d.x; S[a][4] += d.y; S[a][5] += d.z;
+    }
+  }
   for (int a = 0; a < ns; ++a) {
     m[a] *= sc.mp;
     for (int c = 0; c < 3; ++c) S[a][c] *= sc.mp;
