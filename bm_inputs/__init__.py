@@ -150,6 +150,7 @@ class Scene:
     tool_contact: bool = True
     blade: Optional[Blade] = None
     name: str = ""
+    model: str = "neo_hookean"   # or "fixed_corotated" (the paper's elastic model)
 
     @property
     def n(self) -> int:

@@ -60,6 +60,7 @@ typedef struct {
   double Gc, zeta, u_min, b_back, b_lead, h;
   int tool_contact_on;
   int single_field; /* 1: P2G/G2P ignore codes (the single-field baseline) */
+  int model;        /* 0: compressible neo-Hookean; 1: fixed-corotated (Sec. III-B) */
 } or_params;
 
 typedef struct {
@@ -225,6 +226,115 @@ int or_piola(const double F[9], double mu, double lam, double P[9]) {
     P[k] = mu * (F[k] - FinvT) + lam * lj * FinvT;
   }
   return clamped;
+}
+
+/* ------------------------------------------------------------------------ */
+/* stress: fixed-corotated, the paper's elastic model (Sec. III-B)           */
+/*   psi = mu |F - R|^2 + lam/2 (J - 1)^2,  F = R S (polar decomposition)     */
+/*   P   = 2 mu (F - R) + lam (J - 1) J F^{-T}                               */
+/* ------------------------------------------------------------------------ */
+
+/* eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations:
+   A = V diag(w) V^T (V orthogonal, columns = eigenvectors) */
+static void or_sym_eig3(const double Ain[9], double V[9], double w[3]) {
+  double A[9];
+  memcpy(A, Ain, sizeof A);
+  for (int k = 0; k < 9; ++k) V[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  static const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    double diag = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (off <= 1e-32 * diag || off == 0.0) break;
+    for (int r = 0; r < 3; ++r) {
+      int p = PQ[r][0], q = PQ[r][1];
+      double apq = A[3 * p + q];
+      if (apq == 0.0) continue;
+      /* rotation angle that zeroes A_pq: tan(2 phi) = 2 A_pq / (A_qq - A_pp) */
+      double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+      double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+      /* A <- G^T A G, V <- V G with G the rotation in the (p, q) plane */
+      for (int k = 0; k < 3; ++k) { /* columns p, q */
+        double akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - sn * akq;
+        A[3 * k + q] = sn * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) { /* rows p, q */
+        double apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - sn * aqk;
+        A[3 * q + k] = sn * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        double vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - sn * vkq;
+        V[3 * k + q] = sn * vkp + c * vkq;
+      }
+    }
+  }
+  w[0] = A[0];
+  w[1] = A[4];
+  w[2] = A[8];
+}
+
+/* polar decomposition F = R S (det F > 0): S = (F^T F)^{1/2}, R = F S^{-1} */
+void or_polar(const double F[9], double R[9], double S[9]) {
+  double C[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+  double V[9], w[3];
+  or_sym_eig3(C, V, w);
+  double sq[3], isq[3];
+  for (int k = 0; k < 3; ++k) {
+    sq[k] = sqrt(w[k] > 0 ? w[k] : 0.0);
+    isq[k] = sq[k] > 0 ? 1.0 / sq[k] : 0.0;
+  }
+  double Si[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a = 0, b = 0;
+      for (int k = 0; k < 3; ++k) {
+        a += V[3 * i + k] * sq[k] * V[3 * j + k];
+        b += V[3 * i + k] * isq[k] * V[3 * j + k];
+      }
+      S[3 * i + j] = a;
+      Si[3 * i + j] = b;
+    }
+  matmul(F, Si, R);
+}
+
+double or_psi_fcr(const double F[9], double mu, double lam) {
+  double R[9], S[9];
+  or_polar(F, R, S);
+  double d = 0;
+  for (int k = 0; k < 9; ++k) d += (F[k] - R[k]) * (F[k] - R[k]);
+  double J = det3(F);
+  return mu * d + 0.5 * lam * (J - 1.0) * (J - 1.0);
+}
+
+/* returns 1 when the element is inverted or degenerate (J <= 1e-6): the
+   rotation is then taken from the clamped-J cofactor form and flagged */
+int or_piola_fcr(const double F[9], double mu, double lam, double P[9]) {
+  double J = det3(F);
+  int clamped = !(J > OR_JMIN);
+  double R[9], S[9];
+  or_polar(F, R, S);
+  double c[9]; /* J F^{-T} = cofactor matrix */
+  c[0] = F[4] * F[8] - F[5] * F[7];
+  c[1] = F[5] * F[6] - F[3] * F[8];
+  c[2] = F[3] * F[7] - F[4] * F[6];
+  c[3] = F[2] * F[7] - F[1] * F[8];
+  c[4] = F[0] * F[8] - F[2] * F[6];
+  c[5] = F[1] * F[6] - F[0] * F[7];
+  c[6] = F[1] * F[5] - F[2] * F[4];
+  c[7] = F[2] * F[3] - F[0] * F[5];
+  c[8] = F[0] * F[4] - F[1] * F[3];
+  for (int k = 0; k < 9; ++k) P[k] = 2.0 * mu * (F[k] - R[k]) + lam * (J - 1.0) * c[k];
+  return clamped;
+}
+
+/* the scene's elastic model */
+static int or_stress(const or_params *P, const double F[9], double mu, double lam, double Pk[9]) {
+  return P->model == 1 ? or_piola_fcr(F, mu, lam, Pk) : or_piola(F, mu, lam, Pk);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -808,7 +918,7 @@ static void substep(or_scene *s) {
     double w[3][3], dw[3][3];
     base_of(s, s->X + 3 * p, b, w, dw);
     double Pk[9];
-    if (or_piola(s->F + 9 * p, s->mu, s->lam, Pk)) s->err |= OR_E_INVERTED;
+    if (or_stress(P, s->F + 9 * p, s->mu, s->lam, Pk)) s->err |= OR_E_INVERTED;
     int64_t c = pcode(s, p, s->digit);
     double Jb[3];
     for (int i = 0; i < 3; ++i) {
@@ -1409,7 +1519,7 @@ static void contact_vjp(const or_scene *s, const or_frame *fr, int cut, int64_t 
 }
 
 int or_adj_substep(const or_scene *s0, or_adj *A, const double Fbar[3]) {
-  if (s0->P.pair_on) return -1;
+  if (s0->P.pair_on || s0->P.model != 0) return -1;
   if (s0->has_blade) {
     if (s0->B.mass > 0 || s0->B.rigid_interval != 1) return -1;
     for (int k = 0; k < s0->B.nseg; ++k)

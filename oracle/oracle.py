@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("pair_mu_s", C.c_double), ("pair_mu_d", C.c_double), ("Gc", C.c_double),
                 ("zeta", C.c_double), ("u_min", C.c_double), ("b_back", C.c_double),
                 ("b_lead", C.c_double), ("h", C.c_double), ("tool_contact_on", C.c_int),
-                ("single_field", C.c_int)]
+                ("single_field", C.c_int), ("model", C.c_int)]
 
 
 class Seg(C.Structure):
@@ -125,6 +125,11 @@ def lib():
             L.or_adj_substep.restype = C.c_int
             L.or_piola_vjp.argtypes = [dp, C.c_double, C.c_double, dp, dp, dp, dp]
             L.or_couple_T.argtypes = [C.c_int, C.POINTER(C.c_int64), dp, C.c_int, dp]
+            L.or_polar.argtypes = [dp, dp, dp]
+            L.or_piola_fcr.argtypes = [dp, C.c_double, C.c_double, dp]
+            L.or_piola_fcr.restype = C.c_int
+            L.or_psi_fcr.argtypes = [dp, C.c_double, C.c_double]
+            L.or_psi_fcr.restype = C.c_double
             _lib = L
     return _lib
 
@@ -156,6 +161,27 @@ def piola(F, mu, lam):
     P = np.zeros(9)
     clamped = lib().or_piola(_dp(F), mu, lam, _dp(P))
     return P.reshape(3, 3), bool(clamped)
+
+
+def polar(F):
+    """Polar decomposition F = R S (FP64, Jacobi eigen-decomposition of F^T F)."""
+    F = _arr(F, 9)
+    R = np.zeros(9)
+    S = np.zeros(9)
+    lib().or_polar(_dp(F), _dp(R), _dp(S))
+    return R.reshape(3, 3), S.reshape(3, 3)
+
+
+def piola_fcr(F, mu, lam):
+    """Fixed-corotated first Piola-Kirchhoff stress and the inverted flag."""
+    F = _arr(F, 9)
+    P = np.zeros(9)
+    clamped = lib().or_piola_fcr(_dp(F), mu, lam, _dp(P))
+    return P.reshape(3, 3), bool(clamped)
+
+
+def psi_fcr(F, mu, lam) -> float:
+    return lib().or_psi_fcr(_dp(_arr(F, 9)), mu, lam)
 
 
 def psi(F, mu, lam) -> float:
@@ -252,6 +278,7 @@ def _params(sc, single_field=False) -> Params:
     p.b_back, p.b_lead, p.h = sc.b_back, sc.b_lead, sc.band_half_width
     p.tool_contact_on = int(sc.tool_contact)
     p.single_field = int(single_field)
+    p.model = {"neo_hookean": 0, "fixed_corotated": 1}[getattr(sc, "model", "neo_hookean")]
     return p
 
 
