@@ -81,7 +81,7 @@ typedef struct {
  * (Sec. III-E) are uniform over the scene.  Fields marked "<=0 -> default"
  * take the default when non-positive. */
 typedef struct {
-  double E, nu, rho;         /* neo-Hookean: mu = E/(2(1+nu)), lambda = E nu/((1+nu)(1-2nu)) */
+  double E, nu, rho;         /* Lame: mu = E/(2(1+nu)), lambda = E nu/((1+nu)(1-2nu)) */
   double dx;                 /* reference-grid spacing; node i sits at origin + i dx (Eq. 1) */
   double origin[3];
   double V0;                 /* reference volume per particle V_p^0 */
@@ -100,7 +100,15 @@ typedef struct {
   double band_half_width;    /* h_k, <=0 -> 6 dx (Sec. III-D) */
   int tool_contact;          /* 0: the blade only assigns labels */
   int wrench_history;        /* substeps of per-substep wrench kept on device */
+  int model;                 /* elastic model: BM_MODEL_NEO_HOOKEAN or BM_MODEL_FIXED_COROTATED */
 } bm_scene_desc;
+
+/* Elastic models (first Piola-Kirchhoff stress P(F), Sec. III-B):
+ * compressible neo-Hookean, P = mu (F - F^-T) + lambda ln J F^-T;
+ * fixed-corotated (the paper's model), P = 2 mu (F - R) + lambda (J - 1) J F^-T
+ * with F = R S the polar decomposition.  J <= 1e-6 is clamped and flagged
+ * (BM_ERRBIT_INVERTED). */
+enum { BM_MODEL_NEO_HOOKEAN = 0, BM_MODEL_FIXED_COROTATED = 1 };
 
 /* A piece of blade trajectory: a world-frame twist (about the tool-frame
  * origin x_B) held for n_steps substeps.  Kinematic tool: the prescribed

@@ -25,6 +25,8 @@ ERRBIT_NONFINITE = 4
 ERRBIT_CONTACT_OVERFLOW = 8
 ERRBIT_TOO_MANY_CUTS = 16
 
+MODEL_NEO_HOOKEAN, MODEL_FIXED_COROTATED = 0, 1
+
 FIELD_X, FIELD_x, FIELD_v, FIELD_F, FIELD_D = 1, 2, 4, 8, 16
 FIELD_UT, FIELD_CODE, FIELD_MASK1, FIELD_MASK2 = 32, 64, 128, 256
 
@@ -49,7 +51,7 @@ class SceneDesc(C.Structure):
                 ("pair_mu_d", C.c_double), ("G_c", C.c_double), ("zeta", C.c_double),
                 ("u_min", C.c_double), ("b_back", C.c_double), ("b_lead", C.c_double),
                 ("band_half_width", C.c_double), ("tool_contact", C.c_int),
-                ("wrench_history", C.c_int)]
+                ("wrench_history", C.c_int), ("model", C.c_int)]
 
 
 class Segment(C.Structure):

@@ -48,6 +48,7 @@ struct DevScene {
   // material / discretisation (float32 for the particle kernels)
   float dx, inv_dx;
   float mp, V0, Rp, dt, beta, g[3], mu, lam;
+  int model;                // BM_MODEL_*
   float Wth, u_min, b_back, b_lead, h;
   float s_n, gamma_k, gamma_c;
   float pair_mu_s, pair_mu_d;

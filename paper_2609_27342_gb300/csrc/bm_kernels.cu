@@ -92,6 +92,62 @@ __device__ __forceinline__ bool piola(const float F[9], float mu, float lam, flo
 }
 
 // --------------------------------------------------------------------------
+// fixed-corotated stress, P = 2 mu (F - R) + lam (J - 1) J F^-T, with the
+// rotation R of the polar decomposition F = R S from Newton's iteration
+// R <- (g R + R^-T / g) / 2 (g = (|R^-1| / |R|)^(1/2), Frobenius norms),
+// which converges quadratically to R for det F > 0.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void cof3(const float F[9], float c[9]) {
+  c[0] = F[4] * F[8] - F[5] * F[7];
+  c[1] = F[5] * F[6] - F[3] * F[8];
+  c[2] = F[3] * F[7] - F[4] * F[6];
+  c[3] = F[2] * F[7] - F[1] * F[8];
+  c[4] = F[0] * F[8] - F[2] * F[6];
+  c[5] = F[1] * F[6] - F[0] * F[7];
+  c[6] = F[1] * F[5] - F[2] * F[4];
+  c[7] = F[2] * F[3] - F[0] * F[5];
+  c[8] = F[0] * F[4] - F[1] * F[3];
+}
+
+__device__ bool piola_fcr(const float F[9], float mu, float lam, float P[9]) {
+  float c[9];
+  cof3(F, c);
+  const float J = F[0] * c[0] + F[1] * c[1] + F[2] * c[2];
+  const bool clamped = !(J > 1e-6f);
+  float R[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = F[k];
+  for (int it = 0; it < 16; ++it) {
+    float q[9];
+    cof3(R, q);
+    const float d = R[0] * q[0] + R[1] * q[1] + R[2] * q[2];  // R^-T = cof(R) / det R
+    if (d == 0.0f) break;
+    const float id = 1.0f / d;
+    float nr = 0.f, ni = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      q[k] *= id;
+      nr += R[k] * R[k];
+      ni += q[k] * q[k];
+    }
+    const float g = sqrtf(sqrtf(ni / nr));
+    const float ig = 1.0f / g;
+    float dif = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float r = 0.5f * (g * R[k] + ig * q[k]);
+      dif += (r - R[k]) * (r - R[k]);
+      R[k] = r;
+    }
+    if (dif <= 1e-13f) break;
+  }
+  const float jl = lam * (J - 1.0f);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) P[k] = 2.0f * mu * (F[k] - R[k]) + jl * c[k];
+  return clamped;
+}
+
+// --------------------------------------------------------------------------
 // Eq. 12: spring-history Coulomb friction (float32)
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void friction(const float uh[3], const float n[3], const float vrel[3],
@@ -499,7 +555,8 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
     float Pk[9];
-    clamped |= piola(F, sc.mu, sc.lam, Pk);
+    clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk)
+                                                    : piola(F, sc.mu, sc.lam, Pk);
     const float cA = -dt * sc.V0 * sc.inv_dx;  // grad N is applied per axis in units of 1/dx
 #pragma unroll
     for (int k = 0; k < 9; ++k) P.A[k][p] = cA * Pk[k];

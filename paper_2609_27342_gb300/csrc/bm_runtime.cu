@@ -377,6 +377,7 @@ void fill_template(bm_scene_s *s) {
   t.dt = (float)d.dt;
   t.beta = (float)d.beta;
   for (int a = 0; a < 3; ++a) t.g[a] = (float)d.gravity[a];
+  t.model = d.model;
   t.mu = (float)(d.E / (2.0 * (1.0 + d.nu)));
   t.lam = (float)(d.E * d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
   t.Wth = (float)(d.G_c * std::pow(d.V0, 2.0 / 3.0) * (1.0 - d.zeta) / d.zeta);
@@ -697,6 +698,8 @@ int validate_desc(const bm_scene_desc *d) {
   if (!(d->nu > -1.0 && d->nu < 0.5)) return fail(BM_E_INVALID, "nu must lie in (-1, 0.5)");
   if (!(d->beta >= 0 && d->beta <= 1)) return fail(BM_E_INVALID, "beta must lie in [0, 1]");
   if (!(d->zeta > 0 && d->zeta < 1)) return fail(BM_E_INVALID, "zeta must lie in (0, 1)");
+  if (d->model != BM_MODEL_NEO_HOOKEAN && d->model != BM_MODEL_FIXED_COROTATED)
+    return fail(BM_E_INVALID, "unknown elastic model");
   return BM_OK;
 }
 
@@ -1162,6 +1165,7 @@ struct bm_adjoint_s {
 namespace {
 int adjoint_scope(const bm_scene_s *s) {
   if (s->desc.pair_contact) return fail(BM_E_INVALID, "adjoint: material-material contact is not supported");
+  if (s->desc.model != BM_MODEL_NEO_HOOKEAN) return fail(BM_E_INVALID, "adjoint: neo-Hookean scenes only");
   if (s->has_blade) {
     if (s->blade.mass > 0) return fail(BM_E_INVALID, "adjoint: the blade must be kinematic (mass 0)");
     if (s->blade.rigid_interval > 1) return fail(BM_E_INVALID, "adjoint: rigid interval must be 1");

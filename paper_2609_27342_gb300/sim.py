@@ -32,6 +32,8 @@ def scene_desc(sc, wrench_history: int = 0) -> A.SceneDesc:
     d.b_back, d.b_lead, d.band_half_width = sc.b_back, sc.b_lead, sc.band_half_width
     d.tool_contact = int(sc.tool_contact)
     d.wrench_history = int(wrench_history)
+    d.model = {"neo_hookean": A.MODEL_NEO_HOOKEAN, "fixed_corotated": A.MODEL_FIXED_COROTATED}[
+        getattr(sc, "model", "neo_hookean")]
     return d
 
 

@@ -349,3 +349,25 @@ def test_momentum_balance_on_gpu(pkg):
     dP = np.diff(np.array(P), axis=0)
     # the only impulse is the tool's: dP = -dt * F_B
     assert np.max(np.abs(dP + sc.dt * W[:, :3])) <= 1e-4 * np.max(np.abs(sc.dt * W[:, :3]))
+
+
+def test_fixed_corotated_matches_oracle(pkg):
+    """The paper's fixed-corotated model (Sec. III-B) on the single-cut cuboid
+    at a large cutting speed: positions and the wrench history after 100
+    substeps against the FP64 oracle, and different from neo-Hookean."""
+    import dataclasses
+    sc = dataclasses.replace(bi.single_cut_cuboid(edge_z0=0.0505, speed=1.0, n_down=500),
+                             model="fixed_corotated")
+    o = O.OracleScene(sc)
+    o.step(100)
+    g = pkg.Scene(sc, wrench_history=100)
+    g.step(100)
+    L = domain(sc)
+    x = g.read("x")["x"]
+    assert np.max(np.abs(x - o.get("x"))) <= 1e-5 * L
+    wo, wg = o.wrench_history(0, 100), g.wrench_history(0, 100)
+    assert np.max(np.abs(wg[:, :3] - wo[:, :3])) <= 1e-4 * np.max(np.abs(wo[:, :3]))
+    assert g.info().error_bits == 0
+    nh = pkg.Scene(dataclasses.replace(sc, model="neo_hookean"))
+    nh.step(100)
+    assert np.max(np.abs(nh.read("x")["x"] - x)) > 1e-3 * np.max(np.abs(x - sc.X))
