@@ -151,6 +151,8 @@ class Scene:
     blade: Optional[Blade] = None
     name: str = ""
     model: str = "neo_hookean"   # or "fixed_corotated" (the paper's elastic model)
+    yield_stress: float = 0.0    # > 0: von Mises plasticity projection (Pa)
+    viscosity: float = 0.0       # > 0: Newtonian viscosity (Pa s)
 
     @property
     def n(self) -> int:

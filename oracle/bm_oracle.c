@@ -61,6 +61,8 @@ typedef struct {
   int tool_contact_on;
   int single_field; /* 1: P2G/G2P ignore codes (the single-field baseline) */
   int model;        /* 0: compressible neo-Hookean; 1: fixed-corotated (Sec. III-B) */
+  double yield_stress; /* > 0: von Mises plasticity projection (Sec. III-B) */
+  double viscosity;    /* > 0: Newtonian viscosity eta (Sec. III-B) */
 } or_params;
 
 typedef struct {
@@ -104,6 +106,8 @@ typedef struct {
   int has_blade;
   int64_t n;
   double *X, *x, *v, *F, *D, *ut;
+  double *Fpi;  /* inverse plastic deformation F_p^{-1} (n x 9), identity without plasticity */
+  double *Fdot; /* dF/dt of the last substep (n x 9), for the viscous stress */
   unsigned char *digit, *digit_next; /* n * OR_MAX_CUTS ternary digits */
   double *J;                          /* per-particle total contact+body impulse this step */
   or_hist *hist, *hist_next;
@@ -335,6 +339,101 @@ int or_piola_fcr(const double F[9], double mu, double lam, double P[9]) {
 /* the scene's elastic model */
 static int or_stress(const or_params *P, const double F[9], double mu, double lam, double Pk[9]) {
   return P->model == 1 ? or_piola_fcr(F, mu, lam, Pk) : or_piola(F, mu, lam, Pk);
+}
+
+/* ------------------------------------------------------------------------ */
+/* von Mises plasticity projection (Sec. III-B), radial return in principal  */
+/* Hencky strains.  Fe = U diag(s) V^T, eps = log s, e = eps - mean(eps);    */
+/* the von Mises equivalent of the deviatoric Kirchhoff stress 2 mu e is     */
+/* q = sqrt(3/2) |2 mu e|; for q > sigma_y the deviatoric strain is scaled   */
+/* back onto the yield surface, e <- e sigma_y / q, which keeps det Fe.      */
+/* Returns 1 when the projection acted.                                      */
+/* ------------------------------------------------------------------------ */
+int or_vonmises(double Fe[9], double mu, double sigma_y) {
+  double C[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = Fe[i] * Fe[j] + Fe[3 + i] * Fe[3 + j] + Fe[6 + i] * Fe[6 + j];
+  double V[9], w[3];
+  or_sym_eig3(C, V, w);
+  double sg[3], eps[3];
+  for (int k = 0; k < 3; ++k) {
+    if (!(w[k] > 0)) return 0; /* degenerate: left to the inversion flag */
+    sg[k] = sqrt(w[k]);
+    eps[k] = log(sg[k]);
+  }
+  double mean = (eps[0] + eps[1] + eps[2]) / 3.0;
+  double e[3] = {eps[0] - mean, eps[1] - mean, eps[2] - mean};
+  double en = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  double q = sqrt(1.5) * 2.0 * mu * en;
+  if (!(q > sigma_y)) return 0;
+  double scale = sigma_y / q;
+  /* U = Fe V diag(1/s); Fe_new = U diag(s_new) V^T = Fe V diag(s_new / s) V^T */
+  double M[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a = 0;
+      for (int k = 0; k < 3; ++k) {
+        double snew = exp(mean + scale * e[k]);
+        a += V[3 * i + k] * (snew / sg[k]) * V[3 * j + k];
+      }
+      M[3 * i + j] = a;
+    }
+  double out[9];
+  matmul(Fe, M, out);
+  memcpy(Fe, out, sizeof out);
+  return 1;
+}
+
+/* Newtonian viscosity (Sec. III-B): Cauchy stress sigma_v = eta (L + L^T)
+   with L = dF/dt F^{-1}; its first Piola-Kirchhoff form J sigma_v F^{-T}
+   is added to P.  dF/dt is the last substep's rate. */
+void or_viscous_piola(const double F[9], const double Fdot[9], double eta, double P[9]) {
+  double Fi[9];
+  if (!inv3(F, Fi)) return;
+  double L[9];
+  matmul(Fdot, Fi, L);
+  double sv[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) sv[3 * i + j] = eta * (L[3 * i + j] + L[3 * j + i]);
+  double c[9]; /* J F^{-T} = cofactor matrix */
+  c[0] = F[4] * F[8] - F[5] * F[7];
+  c[1] = F[5] * F[6] - F[3] * F[8];
+  c[2] = F[3] * F[7] - F[4] * F[6];
+  c[3] = F[2] * F[7] - F[1] * F[8];
+  c[4] = F[0] * F[8] - F[2] * F[6];
+  c[5] = F[1] * F[6] - F[0] * F[7];
+  c[6] = F[1] * F[5] - F[2] * F[4];
+  c[7] = F[2] * F[3] - F[0] * F[5];
+  c[8] = F[0] * F[4] - F[1] * F[3];
+  double add[9];
+  matmul(sv, c, add);
+  for (int k = 0; k < 9; ++k) P[k] += add[k];
+}
+
+/* stress of particle p at the start of the substep: plastic projection of
+   Fe = F Fp^{-1} (updating Fp^{-1}), elastic P(Fe) Fp^{-T}, viscous part */
+static int or_particle_stress(or_scene *s, int64_t p, double Pk[9]) {
+  const or_params *P = &s->P;
+  const double *F = s->F + 9 * p;
+  int clamped;
+  if (P->yield_stress > 0) {
+    double *Fpi = s->Fpi + 9 * p;
+    double Fe[9];
+    matmul(F, Fpi, Fe);
+    if (or_vonmises(Fe, s->mu, P->yield_stress)) {
+      double Fi[9];
+      if (inv3(F, Fi)) matmul(Fi, Fe, Fpi); /* Fp^{-1} = F^{-1} Fe */
+    }
+    double Pe[9], FpiT[9];
+    clamped = or_stress(P, Fe, s->mu, s->lam, Pe);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) FpiT[3 * i + j] = Fpi[3 * j + i];
+    matmul(Pe, FpiT, Pk);
+  } else {
+    clamped = or_stress(P, F, s->mu, s->lam, Pk);
+  }
+  if (P->viscosity > 0) or_viscous_piola(F, s->Fdot + 9 * p, P->viscosity, Pk);
+  return clamped;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -588,6 +687,8 @@ or_scene *or_create(const or_params *P, const or_blade *B, int64_t n, const doub
   s->x = (double *)malloc(sizeof(double) * n3);
   s->v = (double *)calloc(n3, sizeof(double));
   s->F = (double *)calloc((size_t)n * 9, sizeof(double));
+  s->Fpi = (double *)calloc((size_t)n * 9, sizeof(double));
+  s->Fdot = (double *)calloc((size_t)n * 9, sizeof(double));
   s->D = (double *)calloc((size_t)n, sizeof(double));
   s->ut = (double *)calloc(n3, sizeof(double));
   s->J = (double *)calloc(n3, sizeof(double));
@@ -599,7 +700,10 @@ or_scene *or_create(const or_params *P, const or_blade *B, int64_t n, const doub
   s->hist_cnt_next = (int *)calloc((size_t)n, sizeof(int));
   memcpy(s->X, X, sizeof(double) * n3);
   memcpy(s->x, X, sizeof(double) * n3);
-  for (int64_t p = 0; p < n; ++p) s->F[9 * p] = s->F[9 * p + 4] = s->F[9 * p + 8] = 1.0;
+  for (int64_t p = 0; p < n; ++p) {
+    s->F[9 * p] = s->F[9 * p + 4] = s->F[9 * p + 8] = 1.0;
+    s->Fpi[9 * p] = s->Fpi[9 * p + 4] = s->Fpi[9 * p + 8] = 1.0;
+  }
   /* node range covering every particle's stencil */
   int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
   for (int64_t p = 0; p < n; ++p) {
@@ -637,6 +741,7 @@ void or_destroy(or_scene *s) {
   for (size_t i = 0; i < nn; ++i) free(s->nodes[i].g);
   free(s->nodes);
   free(s->X); free(s->x); free(s->v); free(s->F); free(s->D); free(s->ut); free(s->J);
+  free(s->Fpi); free(s->Fdot);
   free(s->digit); free(s->digit_next);
   free(s->hist); free(s->hist_next); free(s->hist_cnt); free(s->hist_cnt_next);
   free(s->wrench_hist);
@@ -918,7 +1023,7 @@ static void substep(or_scene *s) {
     double w[3][3], dw[3][3];
     base_of(s, s->X + 3 * p, b, w, dw);
     double Pk[9];
-    if (or_stress(P, s->F + 9 * p, s->mu, s->lam, Pk)) s->err |= OR_E_INVERTED;
+    if (or_particle_stress(s, p, Pk)) s->err |= OR_E_INVERTED;
     int64_t c = pcode(s, p, s->digit);
     double Jb[3];
     for (int i = 0; i < 3; ++i) {
@@ -1049,7 +1154,10 @@ static void substep(or_scene *s) {
           for (int a = 0; a < 3; ++a)
             for (int d = 0; d < 3; ++d) G[3 * a + d] += g->vstar[a] * gN[d];
         }
-    for (int k = 0; k < 9; ++k) s->F[9 * p + k] += dt * G[k];
+    for (int k = 0; k < 9; ++k) {
+      s->F[9 * p + k] += dt * G[k];
+      s->Fdot[9 * p + k] = G[k];
+    }
     for (int a = 0; a < 3; ++a)
       if (!isfinite(s->x[3 * p + a]) || !isfinite(s->v[3 * p + a])) s->err |= OR_E_NONFINITE;
   }
@@ -1286,6 +1394,7 @@ or_scene *or_clone(const or_scene *s) {
   t->f = malloc(sizeof(*s->f) * (cnt) > 0 ? sizeof(*s->f) * (cnt) : 1); \
   memcpy(t->f, s->f, sizeof(*s->f) * (cnt))
   OR_DUP(X, n3); OR_DUP(x, n3); OR_DUP(v, n3); OR_DUP(F, n * 9); OR_DUP(D, n);
+  OR_DUP(Fpi, n * 9); OR_DUP(Fdot, n * 9);
   OR_DUP(ut, n3); OR_DUP(J, n3);
   OR_DUP(digit, n * OR_MAX_CUTS); OR_DUP(digit_next, n * OR_MAX_CUTS);
   OR_DUP(hist, n * OR_HIST); OR_DUP(hist_next, n * OR_HIST);
@@ -1519,7 +1628,7 @@ static void contact_vjp(const or_scene *s, const or_frame *fr, int cut, int64_t 
 }
 
 int or_adj_substep(const or_scene *s0, or_adj *A, const double Fbar[3]) {
-  if (s0->P.pair_on || s0->P.model != 0) return -1;
+  if (s0->P.pair_on || s0->P.model != 0 || s0->P.yield_stress > 0 || s0->P.viscosity > 0) return -1;
   if (s0->has_blade) {
     if (s0->B.mass > 0 || s0->B.rigid_interval != 1) return -1;
     for (int k = 0; k < s0->B.nseg; ++k)

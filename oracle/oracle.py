@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("pair_mu_s", C.c_double), ("pair_mu_d", C.c_double), ("Gc", C.c_double),
                 ("zeta", C.c_double), ("u_min", C.c_double), ("b_back", C.c_double),
                 ("b_lead", C.c_double), ("h", C.c_double), ("tool_contact_on", C.c_int),
-                ("single_field", C.c_int), ("model", C.c_int)]
+                ("single_field", C.c_int), ("model", C.c_int), ("yield_stress", C.c_double),
+                ("viscosity", C.c_double)]
 
 
 class Seg(C.Structure):
@@ -130,6 +131,9 @@ def lib():
             L.or_piola_fcr.restype = C.c_int
             L.or_psi_fcr.argtypes = [dp, C.c_double, C.c_double]
             L.or_psi_fcr.restype = C.c_double
+            L.or_vonmises.argtypes = [dp, C.c_double, C.c_double]
+            L.or_vonmises.restype = C.c_int
+            L.or_viscous_piola.argtypes = [dp, dp, C.c_double, dp]
             _lib = L
     return _lib
 
@@ -178,6 +182,21 @@ def piola_fcr(F, mu, lam):
     P = np.zeros(9)
     clamped = lib().or_piola_fcr(_dp(F), mu, lam, _dp(P))
     return P.reshape(3, 3), bool(clamped)
+
+
+def vonmises(Fe, mu, sigma_y):
+    """von Mises projection of an elastic deformation gradient; returns the
+    projected matrix and whether the projection acted."""
+    a = _arr(Fe, 9).copy()
+    acted = lib().or_vonmises(_dp(a), mu, sigma_y)
+    return a.reshape(3, 3), bool(acted)
+
+
+def viscous_piola(F, Fdot, eta):
+    """First Piola-Kirchhoff form of the Newtonian viscous stress."""
+    P = np.zeros(9)
+    lib().or_viscous_piola(_dp(_arr(F, 9)), _dp(_arr(Fdot, 9)), eta, _dp(P))
+    return P.reshape(3, 3)
 
 
 def psi_fcr(F, mu, lam) -> float:
@@ -279,6 +298,8 @@ def _params(sc, single_field=False) -> Params:
     p.tool_contact_on = int(sc.tool_contact)
     p.single_field = int(single_field)
     p.model = {"neo_hookean": 0, "fixed_corotated": 1}[getattr(sc, "model", "neo_hookean")]
+    p.yield_stress = float(getattr(sc, "yield_stress", 0.0))
+    p.viscosity = float(getattr(sc, "viscosity", 0.0))
     return p
 
 
