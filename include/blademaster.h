@@ -101,6 +101,10 @@ typedef struct {
   int tool_contact;          /* 0: the blade only assigns labels */
   int wrench_history;        /* substeps of per-substep wrench kept on device */
   int model;                 /* elastic model: BM_MODEL_NEO_HOOKEAN or BM_MODEL_FIXED_COROTATED */
+  double yield_stress;       /* > 0: von Mises plasticity (Pa), radial return of the deviatoric
+                                principal Hencky strains of Fe = F Fp^-1; P = P(Fe) Fp^-T */
+  double viscosity;          /* > 0: Newtonian viscosity eta (Pa s): J eta (L + L^T) F^-T added
+                                to P, L = dF/dt F^-1 from the previous substep */
 } bm_scene_desc;
 
 /* Elastic models (first Piola-Kirchhoff stress P(F), Sec. III-B):

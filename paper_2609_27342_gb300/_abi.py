@@ -51,7 +51,8 @@ class SceneDesc(C.Structure):
                 ("pair_mu_d", C.c_double), ("G_c", C.c_double), ("zeta", C.c_double),
                 ("u_min", C.c_double), ("b_back", C.c_double), ("b_lead", C.c_double),
                 ("band_half_width", C.c_double), ("tool_contact", C.c_int),
-                ("wrench_history", C.c_int), ("model", C.c_int)]
+                ("wrench_history", C.c_int), ("model", C.c_int), ("yield_stress", C.c_double),
+                ("viscosity", C.c_double)]
 
 
 class Segment(C.Structure):

@@ -49,6 +49,8 @@ struct DevScene {
   float dx, inv_dx;
   float mp, V0, Rp, dt, beta, g[3], mu, lam;
   int model;                // BM_MODEL_*
+  float yield_stress;       // > 0: von Mises projection
+  float viscosity;          // > 0: Newtonian viscosity
   float Wth, u_min, b_back, b_lead, h;
   float s_n, gamma_k, gamma_c;
   float pair_mu_s, pair_mu_d;
@@ -88,6 +90,8 @@ struct PPool {
   float *fx[3];
   uint32_t *base;           // packed local base cell: bx | by << 10 | bz << 20
   float *x[3], *v[3], *F[9], *D, *ut[3];
+  float *Fpi[9];            // inverse plastic deformation Fp^-1 (identity without plasticity)
+  float *Fdot[9];           // dF/dt of the last substep (viscosity)
   uint32_t *s1, *s2;        // bit k: digit k == 1 (s1) or == 2 (s2)
   float *A[9];              // -dt V0 P(F) / dx of this substep (k_pre -> k_p2g_brick)
   float *J[3];              // impulse of this substep: pair contact, then the total

@@ -147,6 +147,163 @@ __device__ bool piola_fcr(const float F[9], float mu, float lam, float P[9]) {
   return clamped;
 }
 
+__device__ __forceinline__ void mat3mul(const float A[9], const float B[9], float C[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+// symmetric 3x3 eigen-decomposition A = V diag(w) V^T by cyclic Jacobi
+// rotations (float32, at most 10 sweeps)
+__device__ void sym_eig3(const float Ain[9], float V[9], float w[3]) {
+  float A[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    A[k] = Ain[k];
+    V[k] = (k % 4 == 0) ? 1.0f : 0.0f;
+  }
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    const float off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    const float dg = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (!(off > 1e-14f * dg)) break;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;
+      const float apq = A[3 * p + q];
+      if (apq == 0.0f) continue;
+      const float th = (A[3 * q + q] - A[3 * p + p]) / (2.0f * apq);
+      const float t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
+      const float c = 1.0f / sqrtf(t * t + 1.0f), sn = t * c;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - sn * akq;
+        A[3 * k + q] = sn * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - sn * aqk;
+        A[3 * q + k] = sn * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - sn * vkq;
+        V[3 * k + q] = sn * vkp + c * vkq;
+      }
+    }
+  }
+  w[0] = A[0];
+  w[1] = A[4];
+  w[2] = A[8];
+}
+
+// von Mises plasticity: radial return of the deviatoric principal Hencky
+// strains e of Fe onto sqrt(3/2) |2 mu e| = sigma_y (isochoric).  Returns
+// whether Fe was projected.
+__device__ bool vonmises(float Fe[9], float mu, float sy) {
+  float C[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = Fe[i] * Fe[j] + Fe[3 + i] * Fe[3 + j] + Fe[6 + i] * Fe[6 + j];
+  float V[9], w[3];
+  sym_eig3(C, V, w);
+  if (!(w[0] > 0.f) || !(w[1] > 0.f) || !(w[2] > 0.f)) return false;
+  float sg[3], e[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sg[k] = sqrtf(w[k]);
+    e[k] = logf(sg[k]);
+  }
+  const float mean = (e[0] + e[1] + e[2]) * (1.0f / 3.0f);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) e[k] -= mean;
+  const float q = 2.4494897f * mu * sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);  // sqrt(6) mu |e|
+  if (!(q > sy)) return false;
+  const float sc = sy / q;
+  float rt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) rt[k] = expf(mean + sc * e[k]) / sg[k];
+  float M[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      M[3 * i + j] = V[3 * i] * rt[0] * V[3 * j] + V[3 * i + 1] * rt[1] * V[3 * j + 1] +
+                     V[3 * i + 2] * rt[2] * V[3 * j + 2];
+  float out[9];
+  mat3mul(Fe, M, out);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Fe[k] = out[k];
+  return true;
+}
+
+// Stress of a particle of a scene with plasticity or viscosity (kept out of
+// line so that the elastic path keeps its registers): plastic projection of
+// Fe = F Fp^-1 with Fp^-1 = F^-1 Fe stored back, P = P(Fe) Fp^-T, and the
+// viscous part J eta (L + L^T) F^-T with L = dF/dt F^-1 of the last substep.
+__device__ __noinline__ bool inelastic_stress(const DevScene &sc, const PPool &P, int p, const float F[9],
+                                              float Pk[9]) {
+  bool clamped = false;
+  if (sc.yield_stress > 0.0f) {
+    // Fe = F Fp^-1, projected; Fp^-1 = F^-1 Fe; P = P(Fe) Fp^-T
+    float Fpi[9], Fe[9], Pe[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fpi[k] = P.Fpi[k][p];
+    mat3mul(F, Fpi, Fe);
+    if (vonmises(Fe, sc.mu, sc.yield_stress)) {
+      float c[9];
+      cof3(F, c);
+      const float d = F[0] * c[0] + F[1] * c[1] + F[2] * c[2];
+      if (d != 0.0f) {
+        const float id = 1.0f / d;
+        float Fi[9] = {c[0] * id, c[3] * id, c[6] * id, c[1] * id, c[4] * id,
+                       c[7] * id, c[2] * id, c[5] * id, c[8] * id};  // F^-1 = cof(F)^T / det F
+        mat3mul(Fi, Fe, Fpi);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) P.Fpi[k][p] = Fpi[k];
+      }
+    }
+    clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(Fe, sc.mu, sc.lam, Pe)
+                                                    : piola(Fe, sc.mu, sc.lam, Pe);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Pk[3 * i + j] = Pe[3 * i] * Fpi[3 * j] + Pe[3 * i + 1] * Fpi[3 * j + 1] + Pe[3 * i + 2] * Fpi[3 * j + 2];
+  } else {
+    clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk)
+                                                    : piola(F, sc.mu, sc.lam, Pk);
+  }
+  if (sc.viscosity > 0.0f) {
+    // Cauchy eta (L + L^T), L = dF/dt F^-1 (last substep), as J sigma F^-T = sigma cof(F)
+    float c[9], Fd[9], L[9];
+    cof3(F, c);
+    const float d = F[0] * c[0] + F[1] * c[1] + F[2] * c[2];
+    if (d != 0.0f) {
+      const float id = 1.0f / d;
+      const float Fi[9] = {c[0] * id, c[3] * id, c[6] * id, c[1] * id, c[4] * id,
+                           c[7] * id, c[2] * id, c[5] * id, c[8] * id};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Fd[k] = P.Fdot[k][p];
+      mat3mul(Fd, Fi, L);
+      float sv[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) sv[3 * i + j] = sc.viscosity * (L[3 * i + j] + L[3 * j + i]);
+      float add[9];
+      mat3mul(sv, c, add);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Pk[k] += add[k];
+    }
+  }
+  return clamped;
+}
+
 // --------------------------------------------------------------------------
 // Eq. 12: spring-history Coulomb friction (float32)
 // --------------------------------------------------------------------------
@@ -555,8 +712,10 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
     float Pk[9];
-    clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk)
-                                                    : piola(F, sc.mu, sc.lam, Pk);
+    if (sc.yield_stress > 0.0f || sc.viscosity > 0.0f) clamped |= inelastic_stress(sc, P, p, F, Pk);
+    else
+      clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk)
+                                                      : piola(F, sc.mu, sc.lam, Pk);
     const float cA = -dt * sc.V0 * sc.inv_dx;  // grad N is applied per axis in units of 1/dx
 #pragma unroll
     for (int k = 0; k < 9; ++k) P.A[k][p] = cA * Pk[k];
@@ -1348,6 +1507,9 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
       }
 #pragma unroll
     for (int k = 0; k < 9; ++k) P.F[k][p] += c * G[k];
+    if (sc.viscosity > 0.0f)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) P.Fdot[k][p] = sc.inv_dx * G[k];
     const uint8_t pend = P.pend[p];
     if (pend && cut >= 0) {
       if (pend == 1) P.s1[p] = s1 | (1u << cut);

@@ -201,6 +201,8 @@ int world_alloc(WorldH *W) {
   for (int k = 0; k < 9; ++k) {
     F(pp.F[k], P);
     F(pp.A[k], P);
+    F(pp.Fpi[k], P);
+    F(pp.Fdot[k], P);
   }
   F(pp.D, P);
   U(pp.base, P);
@@ -378,6 +380,8 @@ void fill_template(bm_scene_s *s) {
   t.beta = (float)d.beta;
   for (int a = 0; a < 3; ++a) t.g[a] = (float)d.gravity[a];
   t.model = d.model;
+  t.yield_stress = (float)d.yield_stress;
+  t.viscosity = (float)d.viscosity;
   t.mu = (float)(d.E / (2.0 * (1.0 + d.nu)));
   t.lam = (float)(d.E * d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
   t.Wth = (float)(d.G_c * std::pow(d.V0, 2.0 / 3.0) * (1.0 - d.zeta) / d.zeta);
@@ -539,8 +543,14 @@ int place_fresh(WorldH *W, bm_scene_s *s) {
   }
   std::vector<float> one((size_t)n, 1.0f);
   for (int k = 0; k < 9; ++k) {
-    if (k % 4 == 0) CK(cudaMemcpyAsync(P.F[k] + pb, one.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
-    else CK(cudaMemsetAsync(P.F[k] + pb, 0, sizeof(float) * n, st));
+    if (k % 4 == 0) {
+      CK(cudaMemcpyAsync(P.F[k] + pb, one.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(P.Fpi[k] + pb, one.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    } else {
+      CK(cudaMemsetAsync(P.F[k] + pb, 0, sizeof(float) * n, st));
+      CK(cudaMemsetAsync(P.Fpi[k] + pb, 0, sizeof(float) * n, st));
+    }
+    CK(cudaMemsetAsync(P.Fdot[k] + pb, 0, sizeof(float) * n, st));
   }
   CK(cudaMemsetAsync(P.D + pb, 0, sizeof(float) * n, st));
   CK(cudaMemsetAsync(P.pend + pb, 0, n, st));
@@ -612,7 +622,11 @@ int move_scene(bm_scene_s *s, WorldH *W) {
     CK(cp(B.v[a] + pd, A.v[a] + ps, sizeof(float) * n));
     CK(cp(B.ut[a] + pd, A.ut[a] + ps, sizeof(float) * n));
   }
-  for (int k = 0; k < 9; ++k) CK(cp(B.F[k] + pd, A.F[k] + ps, sizeof(float) * n));
+  for (int k = 0; k < 9; ++k) {
+    CK(cp(B.F[k] + pd, A.F[k] + ps, sizeof(float) * n));
+    CK(cp(B.Fpi[k] + pd, A.Fpi[k] + ps, sizeof(float) * n));
+    CK(cp(B.Fdot[k] + pd, A.Fdot[k] + ps, sizeof(float) * n));
+  }
   CK(cp(B.D + pd, A.D + ps, sizeof(float) * n));
   CK(cp(B.base + pd, A.base + ps, sizeof(uint32_t) * n));
   CK(cp(B.s1 + pd, A.s1 + ps, sizeof(uint32_t) * n));
@@ -700,6 +714,8 @@ int validate_desc(const bm_scene_desc *d) {
   if (!(d->zeta > 0 && d->zeta < 1)) return fail(BM_E_INVALID, "zeta must lie in (0, 1)");
   if (d->model != BM_MODEL_NEO_HOOKEAN && d->model != BM_MODEL_FIXED_COROTATED)
     return fail(BM_E_INVALID, "unknown elastic model");
+  if (!(d->yield_stress >= 0) || !(d->viscosity >= 0))
+    return fail(BM_E_INVALID, "yield stress and viscosity must be >= 0");
   return BM_OK;
 }
 
@@ -1070,6 +1086,8 @@ std::vector<CkSection> ck_layout(const bm_scene_s *s, size_t *total) {
   for (int a = 0; a < 3; ++a) add(P.x[a] + pb, sizeof(float) * n);
   for (int a = 0; a < 3; ++a) add(P.v[a] + pb, sizeof(float) * n);
   for (int k = 0; k < 9; ++k) add(P.F[k] + pb, sizeof(float) * n);
+  for (int k = 0; k < 9; ++k) add(P.Fpi[k] + pb, sizeof(float) * n);
+  for (int k = 0; k < 9; ++k) add(P.Fdot[k] + pb, sizeof(float) * n);
   add(P.D + pb, sizeof(float) * n);
   for (int a = 0; a < 3; ++a) add(P.ut[a] + pb, sizeof(float) * n);
   add(P.s1 + pb, sizeof(uint32_t) * n);
@@ -1165,7 +1183,8 @@ struct bm_adjoint_s {
 namespace {
 int adjoint_scope(const bm_scene_s *s) {
   if (s->desc.pair_contact) return fail(BM_E_INVALID, "adjoint: material-material contact is not supported");
-  if (s->desc.model != BM_MODEL_NEO_HOOKEAN) return fail(BM_E_INVALID, "adjoint: neo-Hookean scenes only");
+  if (s->desc.model != BM_MODEL_NEO_HOOKEAN || s->desc.yield_stress > 0 || s->desc.viscosity > 0)
+    return fail(BM_E_INVALID, "adjoint: elastic neo-Hookean scenes only");
   if (s->has_blade) {
     if (s->blade.mass > 0) return fail(BM_E_INVALID, "adjoint: the blade must be kinematic (mass 0)");
     if (s->blade.rigid_interval > 1) return fail(BM_E_INVALID, "adjoint: rigid interval must be 1");
@@ -1385,7 +1404,8 @@ int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
   if (particles) *particles = n;
   if (nodes) *nodes = s.n_node;
   if (bricks) *bricks = s.n_brick;
-  const int64_t per_p = 4 * (3 * 5 + 9 + 1) + 4 * 2 + 4 + 1 + (desc->pair_contact ? (3 * 4 + 2 * BM_HIST * 16) : 0);
+  // fx, x, v, u_t, J (3 each); F, A, Fp^-1, dF/dt (9 each); D; base, masks, perm; pending label
+  const int64_t per_p = 4 * (3 * 5 + 9 * 4 + 1) + 4 * 4 + 1 + (desc->pair_contact ? (3 * 4 + 2 * BM_HIST * 16) : 0);
   const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (3 * 16 + 8) + 6 * 32;
   const int64_t per_brick = 2 * BM_TILE_NODES + 48 + 16 + 8;
   if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.n_brick * per_brick + s.hist_cap * 48;

@@ -62,8 +62,8 @@ class Server:
     """
 
     # pool capacity per budget byte (particles, nodes): a scene's footprint is
-    # roughly 190 B per particle and its node count under half its particles
-    BYTES_PER_PARTICLE = 190
+    # roughly 260 B per particle and its node count under half its particles
+    BYTES_PER_PARTICLE = 260
 
     def __init__(self, budget_bytes: int, max_scenes: int = 256, max_chunk: int = 16,
                  stream=None, max_particles: Optional[int] = None, node_tile: int = 128,

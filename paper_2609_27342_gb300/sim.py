@@ -34,6 +34,8 @@ def scene_desc(sc, wrench_history: int = 0) -> A.SceneDesc:
     d.wrench_history = int(wrench_history)
     d.model = {"neo_hookean": A.MODEL_NEO_HOOKEAN, "fixed_corotated": A.MODEL_FIXED_COROTATED}[
         getattr(sc, "model", "neo_hookean")]
+    d.yield_stress = float(getattr(sc, "yield_stress", 0.0))
+    d.viscosity = float(getattr(sc, "viscosity", 0.0))
     return d
 
 

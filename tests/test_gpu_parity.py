@@ -371,3 +371,27 @@ def test_fixed_corotated_matches_oracle(pkg):
     nh = pkg.Scene(dataclasses.replace(sc, model="neo_hookean"))
     nh.step(100)
     assert np.max(np.abs(nh.read("x")["x"] - x)) > 1e-3 * np.max(np.abs(x - sc.X))
+
+
+def test_plasticity_and_viscosity_match_oracle(pkg):
+    """Fixed-corotated elasticity with von Mises plasticity (yield stress
+    2 kPa, as in the paper's knife scene) and Newtonian viscosity on the
+    single-cut cuboid: positions and the wrench history after 100 substeps
+    against the FP64 oracle; the plastic run differs from the elastic one."""
+    import dataclasses
+    sc = dataclasses.replace(bi.single_cut_cuboid(edge_z0=0.0505, speed=1.0, n_down=500),
+                             model="fixed_corotated", yield_stress=2e3, viscosity=5.0)
+    o = O.OracleScene(sc)
+    o.step(100)
+    g = pkg.Scene(sc, wrench_history=100)
+    g.step(100)
+    L = domain(sc)
+    x = g.read("x")["x"]
+    assert np.max(np.abs(x - o.get("x"))) <= 1e-5 * L
+    wo, wg = o.wrench_history(0, 100), g.wrench_history(0, 100)
+    assert np.max(np.abs(wg[:, :3] - wo[:, :3])) <= 1e-4 * np.max(np.abs(wo[:, :3]))
+    assert np.max(np.abs(g.read("F")["F"] - o.get("F"))) <= 1e-4
+    assert g.info().error_bits == 0
+    el = pkg.Scene(dataclasses.replace(sc, yield_stress=0.0, viscosity=0.0))
+    el.step(100)
+    assert np.max(np.abs(el.read("x")["x"] - x)) > 1e-3 * np.max(np.abs(x - sc.X))
