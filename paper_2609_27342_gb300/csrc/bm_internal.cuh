@@ -161,6 +161,7 @@ struct LaunchSet {
   const int *scene_ids;     // scenes in this set
   int n_scenes;
   int any_pair;             // some scene has pair contact
+  int any_inelastic;        // some scene has plasticity or viscosity
   int pair_n_particles;     // particles of pair-contact scenes (hash sizing)
 };
 

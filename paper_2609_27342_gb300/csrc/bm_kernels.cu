@@ -610,6 +610,9 @@ __device__ __forceinline__ int tile_slot(const World &w, const Tile &T, const ui
 // reaction wrench (Eq. 16), side label for the next substep (Eq. 3, 4, 6),
 // and A = -dt V0 P(F) / dx with the total impulse J for P2G.
 // --------------------------------------------------------------------------
+// INELASTIC: the launch set holds a scene with plasticity or viscosity (the
+// elastic instantiation carries no trace of those paths)
+template <bool INELASTIC>
 __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
   __shared__ float red[6][4];
   const int4 bt = ls.btiles[blockIdx.x];
@@ -712,7 +715,8 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
     float Pk[9];
-    if (sc.yield_stress > 0.0f || sc.viscosity > 0.0f) clamped |= inelastic_stress(sc, P, p, F, Pk);
+    if (INELASTIC && (sc.yield_stress > 0.0f || sc.viscosity > 0.0f))
+      clamped |= inelastic_stress(sc, P, p, F, Pk);
     else
       clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk)
                                                       : piola(F, sc.mu, sc.lam, Pk);
@@ -1428,7 +1432,7 @@ struct K1S {
   int any;
 };
 
-template <int MB>
+template <int MB, bool INELASTIC>
 __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
   __shared__ K1S S;
   const int4 bt = ls.btiles[blockIdx.x];
@@ -1507,7 +1511,7 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
       }
 #pragma unroll
     for (int k = 0; k < 9; ++k) P.F[k][p] += c * G[k];
-    if (sc.viscosity > 0.0f)
+    if (INELASTIC && sc.viscosity > 0.0f)
 #pragma unroll
       for (int k = 0; k < 9; ++k) P.Fdot[k][p] = sc.inv_dx * G[k];
     const uint8_t pend = P.pend[p];
@@ -2240,7 +2244,8 @@ cudaError_t bm_kernels_init() {
 template <int PPC, int V>
 static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   rec(ev, 18, 0, st);
-  k_pre<<<ls.n_btiles, 128, 0, st>>>(w, ls);
+  if (ls.any_inelastic) k_pre<true><<<ls.n_btiles, 128, 0, st>>>(w, ls);
+  else k_pre<false><<<ls.n_btiles, 128, 0, st>>>(w, ls);
   rec(ev, 18, 1, st);
   rec(ev, 0, 0, st);
   k_p2g_brick<PPC, Occ<V>::p2g><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
@@ -2255,7 +2260,8 @@ static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, 
   k_musl_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 3, 1, st);
   rec(ev, 4, 0, st);
-  k_fupd<Occ<V>::fupd><<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  if (ls.any_inelastic) k_fupd<Occ<V>::fupd, true><<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  else k_fupd<Occ<V>::fupd, false><<<ls.n_btiles, BT, 0, st>>>(w, ls);
   rec(ev, 4, 1, st);
 }
 

@@ -337,6 +337,7 @@ LaunchSet scene_set(const WorldH *W, const bm_scene_s *s) {
   ls.scene_ids = W->d_slot_ids + s->slot;
   ls.n_scenes = 1;
   ls.any_pair = s->desc.pair_contact;
+  ls.any_inelastic = s->desc.yield_stress > 0 || s->desc.viscosity > 0;
   return ls;
 }
 
@@ -352,6 +353,7 @@ LaunchSet world_set(const WorldH *W) {
   ls.n_scenes = (int)W->members.size();
   for (auto *s : W->members) {
     ls.any_pair |= s->desc.pair_contact;
+    ls.any_inelastic |= s->desc.yield_stress > 0 || s->desc.viscosity > 0;
     ls.ppc16 |= s->ppc_max > 8;
   }
   return ls;
