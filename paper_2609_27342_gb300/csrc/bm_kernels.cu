@@ -1250,6 +1250,29 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
             so[2] += N * vo.z;
           }
         }
+    } else if (in_smem) {
+      // tile slots in shared memory: branch-free over the stencil (a missing
+      // or massless logical grid contributes zero)
+      const int t0 = (lz * TE + ly) * TE + lx;
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+          const float wyz = wy[oy] * wz[oz];
+#pragma unroll
+          for (int ox = 0; ox < 3; ++ox) {
+            const int s = tile_slot(w, S.T, tcodes, t0 + (oz * TE + oy) * TE + ox, s1, s2);
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 vo = s >= 0 ? S.tvo[s] : zero, vn = s >= 0 ? S.tvn[s] : zero;
+            const float N = vo.w > 0.f ? wx[ox] * wyz : 0.f;
+            sn[0] += N * vn.x;
+            sn[1] += N * vn.y;
+            sn[2] += N * vn.z;
+            so[0] += N * vo.x;
+            so[1] += N * vo.y;
+            so[2] += N * vo.z;
+          }
+        }
     } else
 #pragma unroll
     for (int oz = 0; oz < 3; ++oz)
@@ -1261,10 +1284,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
           const int s = tile_slot(w, S.T, tcodes, t, s1, s2);
           if (s < 0) continue;
           float4 vo, vn;
-          if (in_smem) {
-            vo = S.tvo[s];
-            vn = S.tvn[s];
-          } else {
+          {
             const int g = S.T.goff[t] + s - S.T.lo[t];
             vo = w.S.vold[g];
             vn = w.S.vnew[g];
