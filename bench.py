@@ -57,7 +57,7 @@ KERNEL_MODEL = {
     "k_fupd": {"bytes": (97, 0, 54, 1080), "flops": (650, 0, 0, 0)},
 }
 STEP_ALGORITHMIC_BYTES = 156  # per particle-substep: the state the method must move
-LAUNCHES_PER_SUBSTEP = 10     # kernels one batched substep launches (no pair contact)
+LAUNCHES_PER_SUBSTEP = 11     # kernels one batched substep launches (no pair contact)
 
 
 def log(*a):
