@@ -415,6 +415,34 @@ def run_native(args):
         g1.close()
         log(f"configs: {configs}")
 
+    # parity of the batched path in the timed launch shape: the benchmark's
+    # smallest scene in a one-scene batch, 400 substeps (the blade is well
+    # into the material by then), against the FP64
+    # oracle on the host (position error relative to the domain size)
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        i0 = int(np.argmin([s.n for s in scenes]))
+        sp = scenes[i0]
+        pb = pkg.Batch(max_particles=sp.n, max_nodes=fps[i0][1], max_scenes=1, max_bricks=fps[i0][2],
+                       stream=stream)
+        gp = pkg.Scene(sp, stream=stream)
+        pb.add(gp)
+        pb.set_tiles(shape["graph_chunk"], shape["node_tile"], shape["brick_variant"])
+        pb.step(400)
+        r = gp.read("x", "mask1", "mask2")
+        op = O.OracleScene(sp)
+        op.step(400)
+        dom = float(np.max(sp.X.max(0) - sp.X.min(0)))
+        od = op.get("digits")[:, 0].astype(int)
+        gdig = np.where(r["mask1"] & 1, 1, np.where(r["mask2"] & 1, 2, 0))
+        parity = {"scene": i0, "particles": sp.n, "substeps": 400, "path": "batched, timed launch shape",
+                  "pos_err_max_rel_domain": float(np.abs(r["x"] - op.get("x")).max() / dom),
+                  "label_disagreement": int((od != gdig).sum()), "labelled": int((od > 0).sum())}
+        pb.close()
+        gp.close()
+        log(f"parity: {parity}")
+
     # continuous-batching server on a Poisson request stream (rollouts of
     # 8k-500k particles, 200-2000 substeps, 1-3 cuts), admission by an HBM budget
     serving = None
@@ -479,6 +507,7 @@ def run_native(args):
             "clocks": clk,
             "serving": serving,
             "adjoint": adjoint,
+            "parity": parity,
             "configs": configs,
             "cpu_baseline": cpu,
             "error_bits": err_bits,
