@@ -127,6 +127,11 @@ typedef struct {
   double impulse_sum[3]; /* sum of impulses scattered last step (Eq. 18) */
   unsigned err;
   double mp, Rp, mu, lam;
+  /* plane of each cut in the world frame at the substep the cut begins:
+     unit normal n and offset n . x_e (Sec. III-F uses it as the cut
+     faces' Hermite data); bit k of cutpl_set marks cut k as recorded */
+  double cutpl[OR_MAX_CUTS][4];
+  unsigned cutpl_set;
 } or_scene;
 
 /* ------------------------------------------------------------------------ */
@@ -921,11 +926,17 @@ static void substep(or_scene *s) {
       }
     }
     /* D_p is reset to zero at the beginning of each new cut (Sec. III-A) */
-    if (cut >= 0 && cut != s->cur_cut) {
+    int started = cut >= 0 && cut != s->cur_cut;
+    if (started) {
       for (int64_t p = 0; p < n; ++p) s->D[p] = 0.0;
       s->cur_cut = cut;
     }
     or_make_frame(s, &fr);
+    if (started) {
+      for (int i = 0; i < 3; ++i) s->cutpl[cut][i] = fr.n[i];
+      s->cutpl[cut][3] = dot3(fr.n, fr.xe);
+      s->cutpl_set |= 1u << cut;
+    }
   }
   double Wth = P->Gc * pow(V0, 2.0 / 3.0) * (1.0 - P->zeta) / P->zeta; /* Eq. 5 */
 
@@ -1289,6 +1300,13 @@ void or_get_frame(const or_scene *s, double out[15]) {
 
 int64_t or_step_count(const or_scene *s) { return s->step; }
 unsigned or_errors(const or_scene *s) { return s->err; }
+
+/* recorded cut planes: out[k * 4 + 0..3] = (n, n . x_e) of cut k; returns the
+   mask of recorded cuts */
+unsigned or_cut_planes(const or_scene *s, double *out) {
+  memcpy(out, s->cutpl, sizeof s->cutpl);
+  return s->cutpl_set;
+}
 void or_impulse_sum(const or_scene *s, double out[3]) { memcpy(out, s->impulse_sum, 24); }
 void or_last_wrench(const or_scene *s, double out[6]) { memcpy(out, s->lastF, 48); }
 int or_wrench_history(const or_scene *s, int64_t first, int64_t count, double *out) {

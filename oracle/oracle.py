@@ -86,6 +86,8 @@ def lib():
             L.or_step_count.restype = C.c_int64
             L.or_errors.argtypes = [C.c_void_p]
             L.or_errors.restype = C.c_uint
+            L.or_cut_planes.argtypes = [C.c_void_p, dp]
+            L.or_cut_planes.restype = C.c_uint
             L.or_impulse_sum.argtypes = [C.c_void_p, dp]
             L.or_last_wrench.argtypes = [C.c_void_p, dp]
             L.or_wrench_history.argtypes = [C.c_void_p, C.c_int64, C.c_int64, dp]
@@ -400,6 +402,13 @@ class OracleScene:
     @property
     def errors(self) -> int:
         return self._L.or_errors(self._h)
+
+    def cut_planes(self):
+        """(planes, mask): planes[k] = (n, n . x_e) of cut k in the world frame
+        at the substep the cut began; bit k of mask marks cut k as recorded."""
+        out = np.zeros(MAX_CUTS * 4)
+        mask = self._L.or_cut_planes(self._h, _dp(out))
+        return out.reshape(MAX_CUTS, 4), int(mask)
 
     def impulse_sum(self) -> np.ndarray:
         out = np.zeros(3)
