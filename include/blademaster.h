@@ -352,6 +352,60 @@ const char *bm_kernel_name(int i);
 int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile, int brick_variant);
 int bm_batch_destroy(bm_batch_t b);
 
+/* ---------------------------------------------------------------------------
+ * Reference-grid surface reconstruction (Sec. III-F), for visualisation.
+ *
+ * The uniform reference grid is the scene's sub-cell particle lattice: with
+ * lattice[a] particles per reference cell along axis a the spacing is
+ * h_a = dx / lattice[a], and a lattice vertex is material when a particle
+ * sits on it (the original boundary is the boundary of the union of the
+ * material vertices' voxels).  Links between lattice neighbours are
+ * disconnected where the two particles' side codes conflict (the blade's
+ * sweep labelled them apart); a disconnected link's Hermite data is the
+ * crossing of the lowest conflicting cut's plane with it, the plane being
+ * the blade's (n, n . x_e) recorded when that cut began.  In every lattice
+ * cell the connected components of material vertices over the connected
+ * links are the local regions; each region with a disconnected or boundary
+ * link gets one vertex by local dual contouring (the pseudo-inverse
+ * minimiser of the quadratic error of its links' Hermite data, relative to
+ * their mean, eigenvalues below 0.1 dropped, clamped to the cell), so the two
+ * sides of a cut keep separate, coincident faces.  Each (Hermite link,
+ * material end) gives a quad over that end's regions in the four cells
+ * around the link, split into two triangles wound outward (triangles with a
+ * repeated vertex dropped).  Motion is one-way: a vertex carries the code of
+ * its region's lowest corner particle and follows that code's logical grid
+ * through fixed trilinear weights over the 8 reference nodes around it,
+ * each node's displacement being the B-spline-weighted mean of x - X over
+ * the particles with exactly that code.
+ *
+ * Ordering: vertices by cell (lower-corner lattice index, x fastest, from
+ * -1), then region (by lowest corner); triangles by link (lower end's
+ * lattice index, then axis x, y, z), lower end's quad first.  Integer output
+ * is deterministic; positions are float32.
+ * ------------------------------------------------------------------------- */
+typedef struct bm_surface_s *bm_surface_t;
+/* Build the lattice map of a scene (plain or batched).  lattice[3] >= 1.
+ * BM_E_INVALID if a particle is off the lattice (more than 1e-3 h from a
+ * lattice point), two share a point, or the lattice does not sit at the
+ * reference cells' sub-cell centres (every lattice point's stencil base cell
+ * must equal its particle's).  The handle keeps device buffers from the
+ * scene's allocator and stays valid while the scene lives (also across
+ * batch add/remove). */
+int bm_surface_create(bm_scene_t s, const int lattice[3], bm_surface_t *out);
+/* Rebuild the topology from the scene's current side codes (rebuild != 0)
+ * and re-embed every vertex in the current motion field; returns the vertex
+ * and triangle counts.  Enqueued on the scene's stream; synchronises to
+ * return the counts. */
+int bm_surface_update(bm_surface_t f, int rebuild, int64_t *n_vertices, int64_t *n_triangles);
+/* Copy the last update's output: vertices [n_vertices][3] current
+ * positions, reference [n_vertices][3] reference positions, triangles
+ * [n_triangles][3] vertex indices, masks [n_vertices][2] the vertex codes
+ * (s1, s2 bit masks).  Any pointer may be NULL.  dst_on_device selects device
+ * or host destinations.  Synchronises. */
+int bm_surface_read(bm_surface_t f, float *vertices, float *reference, int32_t *triangles,
+                    uint32_t *masks, int dst_on_device);
+int bm_surface_destroy(bm_surface_t f);
+
 const char *bm_last_error(void);
 const char *bm_version(void);
 

@@ -114,6 +114,10 @@ SIGNATURES = {
     "bm_adjoint_state": (C.c_int, [VP, C.c_uint32, PVP, C.c_int, C.c_int]),
     "bm_adjoint_params": (C.c_int, [VP, PD, C.c_int]),
     "bm_adjoint_destroy": (C.c_int, [VP]),
+    "bm_surface_create": (C.c_int, [VP, C.POINTER(C.c_int), PVP]),
+    "bm_surface_update": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "bm_surface_read": (C.c_int, [VP, VP, VP, VP, VP, C.c_int]),
+    "bm_surface_destroy": (C.c_int, [VP]),
     "bm_scene_destroy": (C.c_int, [VP]),
     "bm_batch_create": (C.c_int, [C.POINTER(BatchDesc), C.POINTER(Alloc), VP, PVP]),
     "bm_batch_scene_create": (C.c_int, [VP, C.POINTER(SceneDesc), C.POINTER(BladeDesc),

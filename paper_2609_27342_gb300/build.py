@@ -1,6 +1,6 @@
 """Build the sm_103a shared library in-tree (``_build/libblademaster.so``).
 
-Three translation units are compiled in parallel with nvcc for
+Four translation units are compiled in parallel with nvcc for
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into one shared object
 with a plain C ABI (include/blademaster.h).
 """
@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libblademaster.so")
-SOURCES = ["bm_kernels.cu", "bm_runtime.cu", "bm_adjoint.cu"]
+SOURCES = ["bm_kernels.cu", "bm_runtime.cu", "bm_adjoint.cu", "bm_surface.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-ffp-contract=off", "-diag-suppress", "177"]

@@ -77,6 +77,11 @@ struct DevScene {
   double dxe[3], dn[3], de[3], dd[3], dve[3];
   float fxe[3], fn[3], fe[3], fd[3], fve[3], fc[3], fxB[3], fvB[3], fwB[3];
   float fIinv[9], finv_mass, fmu_s, fmu_d, fhext[3], fL;
+  // plane of each cut in the world frame at the substep it began (n, n . x_e),
+  // the Hermite data of its faces in the surface reconstruction (Sec. III-F);
+  // bit k of cutpl_set marks cut k as recorded
+  double cutpl[BM_MAX_CUTS][4];
+  unsigned int cutpl_set;
   // counters and flags
   long long step;
   unsigned int err;
@@ -164,6 +169,37 @@ struct LaunchSet {
   int any_inelastic;        // some scene has plasticity or viscosity
   int pair_n_particles;     // particles of pair-contact scenes (hash sizing)
 };
+
+// surface reconstruction (bm_surface.cu, Sec. III-F) over a scene's sub-cell
+// particle lattice; the runtime fills it, the kernels only read the inputs
+struct SurfParams {
+  int n[3];                  // lattice points per axis
+  int nc[3];                 // cells (and link lower ends) per axis: n + 1, lower corners from -1
+  long long n_cells;         // nc[0] * nc[1] * nc[2]
+  double Xmin[3], h[3];      // lattice point j sits at Xmin + j h
+  double origin[3], dx;      // the scene's reference grid
+  int lo[3];                 // absolute index of the scene's local base cell 0
+  int bmin[3], bmax[3];      // stencil base cells of the first and last lattice point per axis
+  const int *jstart[3];      // [B - bmin]: first lattice index whose base cell is >= B
+  int *lat;                  // lattice point (x fastest) -> scene-relative pool index, -1 empty
+  float *Xr[3];              // scene-relative reference positions
+  int p_begin, slot;         // the scene's first pool particle and its record in the world
+  int *cell_cnt, *cell_off;  // per cell: vertices, first vertex (n_cells + 1 entries)
+  uint32_t *cell_reg;        // per cell: 4 bits per corner, vertex ordinal of its region (15: none)
+  int *pt_cnt, *pt_off;      // per link lower end: triangles, first triangle (n_cells + 1)
+  int *scan_tmp;             // block sums of the scans
+  float *ref[3], *cur[3];    // vertex reference and current positions
+  int *anchor;               // vertex anchor particle (scene-relative)
+  uint32_t *vmask[2];        // vertex code
+  int *tri;                  // [3 * triangles]
+};
+cudaError_t bm_launch_surface_map(const World &w, const SurfParams &sp, int n, const int *jlin,
+                                  const float *Xc, cudaStream_t st);
+cudaError_t bm_launch_surface_cells(const World &w, const SurfParams &sp, cudaStream_t st);
+cudaError_t bm_launch_surface_vertices(const World &w, const SurfParams &sp, cudaStream_t st);
+cudaError_t bm_launch_surface_tri_count(const World &w, const SurfParams &sp, cudaStream_t st);
+cudaError_t bm_launch_surface_tris(const World &w, const SurfParams &sp, cudaStream_t st);
+cudaError_t bm_launch_surface_embed(const World &w, const SurfParams &sp, int n_vertices, cudaStream_t st);
 
 // kernel launchers (bm_kernels.cu)
 #define BM_NUM_KERNELS 19

@@ -1836,6 +1836,12 @@ __device__ void prepare_substep(DevScene &sc) {
                   __dsub_rn(__dmul_rn(sc.wB[2], r[0]), __dmul_rn(sc.wB[0], r[2])),
                   __dsub_rn(__dmul_rn(sc.wB[0], r[1]), __dmul_rn(sc.wB[1], r[0]))};
   for (int i = 0; i < 3; ++i) sc.dve[i] = __dadd_rn(sc.vB[i], wr[i]);
+  if (sc.reset_D) {  // a new cut begins: keep its plane for the cut faces
+    for (int i = 0; i < 3; ++i) sc.cutpl[cut][i] = sc.dn[i];
+    sc.cutpl[cut][3] = __dadd_rn(__dadd_rn(__dmul_rn(sc.dn[0], sc.dxe[0]), __dmul_rn(sc.dn[1], sc.dxe[1])),
+                                 __dmul_rn(sc.dn[2], sc.dxe[2]));
+    sc.cutpl_set |= 1u << cut;
+  }
   for (int i = 0; i < 3; ++i) {
     sc.fxe[i] = (float)sc.dxe[i];
     sc.fn[i] = (float)sc.dn[i];

@@ -1682,3 +1682,285 @@ int bm_batch_destroy(bm_batch_t b) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Reference-grid surface reconstruction (Sec. III-F): host side.  The lattice
+// map and its tables are built once; each update runs the count / scan /
+// write kernels of bm_surface.cu on the scene's current stream.
+// ============================================================================
+struct bm_surface_s {
+  bm_scene_s *scene = nullptr;
+  SurfParams sp{};
+  Allocator al;
+  std::vector<void *> fixed;           // lattice map, tables, per-cell arrays
+  void *vbuf = nullptr, *tbuf = nullptr;  // vertex and triangle arrays (grown on demand)
+  int64_t vcap = 0, tcap = 0;
+  int64_t nv = 0, nt = 0;
+  void release_all(cudaStream_t st) {
+    if (st) cudaStreamSynchronize(st);
+    for (void *p : fixed) al.release(p);
+    fixed.clear();
+    al.release(vbuf);
+    al.release(tbuf);
+    vbuf = tbuf = nullptr;
+    vcap = tcap = 0;
+  }
+};
+
+namespace {
+
+template <class T>
+T *surf_get(bm_surface_s *f, int64_t count) {
+  void *p = f->al.alloc(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+  if (p) f->fixed.push_back(p);
+  return (T *)p;
+}
+
+// vertex arrays: ref[3], cur[3] floats, anchor int, masks 2 x uint32 (9 words per vertex)
+int surf_grow_vertices(bm_surface_s *f, int64_t nv) {
+  if (nv <= f->vcap) return BM_OK;
+  int64_t cap = std::max<int64_t>(nv + nv / 4, 1024);
+  void *b = f->al.alloc(sizeof(uint32_t) * 9 * (size_t)cap);
+  if (!b) return fail(BM_E_OOM, "surface vertex arrays");
+  f->al.release(f->vbuf);
+  f->vbuf = b;
+  f->vcap = cap;
+  float *fb = (float *)b;
+  for (int a = 0; a < 3; ++a) {
+    f->sp.ref[a] = fb + (size_t)a * cap;
+    f->sp.cur[a] = fb + (size_t)(3 + a) * cap;
+  }
+  f->sp.anchor = (int *)(fb + (size_t)6 * cap);
+  f->sp.vmask[0] = (uint32_t *)(fb + (size_t)7 * cap);
+  f->sp.vmask[1] = (uint32_t *)(fb + (size_t)8 * cap);
+  return BM_OK;
+}
+
+int surf_grow_tris(bm_surface_s *f, int64_t nt) {
+  if (nt <= f->tcap) return BM_OK;
+  int64_t cap = std::max<int64_t>(nt + nt / 4, 1024);
+  void *b = f->al.alloc(sizeof(int) * 3 * (size_t)cap);
+  if (!b) return fail(BM_E_OOM, "surface triangle array");
+  f->al.release(f->tbuf);
+  f->tbuf = b;
+  f->tcap = cap;
+  f->sp.tri = (int *)b;
+  return BM_OK;
+}
+
+bool valid_surface(bm_surface_t f) { return f && f->scene && valid_scene(f->scene); }
+
+}  // namespace
+
+extern "C" {
+
+int bm_surface_create(bm_scene_t s, const int lattice[3], bm_surface_t *out) {
+  if (!out) return fail(BM_E_INVALID, "null output handle");
+  *out = nullptr;
+  if (!valid_scene(s) || !lattice) return fail(BM_E_INVALID, "bad scene or lattice");
+  for (int a = 0; a < 3; ++a)
+    if (lattice[a] < 1 || lattice[a] > 64) return fail(BM_E_INVALID, "lattice counts must lie in [1, 64]");
+  const int64_t n = s->n;
+  const bm_scene_desc &d = s->desc;
+  double h[3], Xmin[3];
+  for (int a = 0; a < 3; ++a) {
+    h[a] = d.dx / lattice[a];
+    Xmin[a] = HUGE_VAL;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) Xmin[a] = std::min(Xmin[a], (double)s->X[3 * i + a]);
+  // lattice index of every particle (caller order)
+  std::vector<int64_t> jj((size_t)n * 3);
+  int64_t nl[3] = {0, 0, 0};
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double X = (double)s->X[3 * i + a];
+      const double r = (X - Xmin[a]) / h[a];
+      const int64_t j = (int64_t)std::llround(r);
+      if (!(std::fabs(Xmin[a] + (double)j * h[a] - X) <= 1e-3 * h[a]) || j < 0 || j > (1 << 20))
+        return fail(BM_E_INVALID, "particle off the sub-cell lattice");
+      jj[3 * i + a] = j;
+      nl[a] = std::max(nl[a], j + 1);
+    }
+  const int64_t total = nl[0] * nl[1] * nl[2];
+  const int64_t ncells = (nl[0] + 1) * (nl[1] + 1) * (nl[2] + 1);
+  if (total > ((int64_t)1 << 30) || ncells > ((int64_t)1 << 30))
+    return fail(BM_E_INVALID, "surface lattice too large");
+  std::vector<int> jlin((size_t)n);
+  {
+    std::vector<uint8_t> seen((size_t)total, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t lin = (jj[3 * i + 2] * nl[1] + jj[3 * i + 1]) * nl[0] + jj[3 * i];
+      if (seen[(size_t)lin]) return fail(BM_E_INVALID, "two particles share a lattice point");
+      seen[(size_t)lin] = 1;
+      jlin[(size_t)i] = (int)lin;
+    }
+  }
+  // stencil base cell of every lattice coordinate; it must be the particles'
+  std::vector<int> base[3], jstart[3];
+  int bmin[3], bmax[3];
+  for (int a = 0; a < 3; ++a) {
+    base[a].resize((size_t)nl[a]);
+    for (int64_t j = 0; j < nl[a]; ++j)
+      base[a][(size_t)j] = (int)std::floor((Xmin[a] + (double)j * h[a] - d.origin[a]) / d.dx - 0.5);
+    bmin[a] = base[a].front();
+    bmax[a] = base[a].back();
+    for (int64_t j = 1; j < nl[a]; ++j)
+      if (base[a][(size_t)j] < base[a][(size_t)j - 1]) return fail(BM_E_INVALID, "lattice not monotone");
+    jstart[a].assign((size_t)(bmax[a] - bmin[a] + 2), (int)nl[a]);
+    for (int B = bmin[a]; B <= bmax[a] + 1; ++B) {
+      int64_t j = 0;
+      while (j < nl[a] && base[a][(size_t)j] < B) ++j;
+      jstart[a][(size_t)(B - bmin[a])] = (int)j;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double xl = ((double)s->X[3 * i + a] - d.origin[a]) / d.dx;
+      if ((int)std::floor(xl - 0.5) != base[a][(size_t)jj[3 * i + a]])
+        return fail(BM_E_INVALID, "lattice is not at the reference cells' sub-cell centres");
+    }
+
+  bm_surface_s *f = new bm_surface_s();
+  f->scene = s;
+  f->al.has = s->has_home_alloc;
+  f->al.a = s->home_alloc;
+  f->al.st = s->home_stream;
+  SurfParams &sp = f->sp;
+  for (int a = 0; a < 3; ++a) {
+    sp.n[a] = (int)nl[a];
+    sp.nc[a] = (int)nl[a] + 1;
+    sp.Xmin[a] = Xmin[a];
+    sp.h[a] = h[a];
+    sp.origin[a] = d.origin[a];
+    sp.lo[a] = s->lo[a];
+    sp.bmin[a] = bmin[a];
+    sp.bmax[a] = bmax[a];
+  }
+  sp.dx = d.dx;
+  sp.n_cells = ncells;
+  bool ok = true;
+  int *js[3];
+  for (int a = 0; a < 3; ++a) ok &= (js[a] = surf_get<int>(f, (int64_t)jstart[a].size())) != nullptr;
+  ok &= (sp.lat = surf_get<int>(f, total)) != nullptr;
+  for (int a = 0; a < 3; ++a) ok &= (sp.Xr[a] = surf_get<float>(f, n)) != nullptr;
+  ok &= (sp.cell_cnt = surf_get<int>(f, ncells)) != nullptr;
+  ok &= (sp.cell_off = surf_get<int>(f, ncells + 1)) != nullptr;
+  ok &= (sp.cell_reg = surf_get<uint32_t>(f, ncells)) != nullptr;
+  ok &= (sp.pt_cnt = surf_get<int>(f, ncells)) != nullptr;
+  ok &= (sp.pt_off = surf_get<int>(f, ncells + 1)) != nullptr;
+  ok &= (sp.scan_tmp = surf_get<int>(f, ncells / 1024 + 2)) != nullptr;
+  int *d_jlin = nullptr;
+  float *d_X = nullptr;
+  if (ok) {
+    d_jlin = (int *)f->al.alloc(sizeof(int) * (size_t)n);
+    d_X = (float *)f->al.alloc(sizeof(float) * 3 * (size_t)n);
+    ok = d_jlin && d_X;
+  }
+  if (!ok) {
+    f->al.release(d_jlin);
+    f->al.release(d_X);
+    f->release_all(nullptr);
+    delete f;
+    return fail(BM_E_OOM, "surface buffers");
+  }
+  for (int a = 0; a < 3; ++a) sp.jstart[a] = js[a];
+  WorldH *W = s->world;
+  sp.p_begin = (int)s->p_begin;
+  sp.slot = s->slot;
+  cudaStream_t st = W->st;
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+    e = cudaMemcpyAsync(js[a], jstart[a].data(), sizeof(int) * jstart[a].size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sp.lat, 0xff, sizeof(int) * (size_t)total, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_jlin, jlin.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_X, s->X.data(), sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = bm_launch_surface_map(W->w, sp, (int)n, d_jlin, d_X, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  f->al.release(d_jlin);
+  f->al.release(d_X);
+  if (e != cudaSuccess) {
+    f->release_all(st);
+    delete f;
+    return fail(BM_E_CUDA, std::string("surface set-up: ") + cudaGetErrorString(e));
+  }
+  *out = f;
+  return BM_OK;
+}
+
+int bm_surface_update(bm_surface_t f, int rebuild, int64_t *n_vertices, int64_t *n_triangles) {
+  if (!valid_surface(f)) return fail(BM_E_INVALID, "bad surface or its scene has no storage");
+  bm_scene_s *s = f->scene;
+  WorldH *W = s->world;
+  SurfParams &sp = f->sp;
+  sp.p_begin = (int)s->p_begin;  // the scene may have moved between worlds
+  sp.slot = s->slot;
+  cudaStream_t st = W->st;
+  if (rebuild || f->vbuf == nullptr) {
+    CK(bm_launch_surface_cells(W->w, sp, st));
+    int nv = 0;
+    CK(cudaMemcpyAsync(&nv, sp.cell_off + sp.n_cells, sizeof nv, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int rc = surf_grow_vertices(f, nv);
+    if (rc) return rc;
+    CK(bm_launch_surface_vertices(W->w, sp, st));
+    CK(bm_launch_surface_tri_count(W->w, sp, st));
+    int nt = 0;
+    CK(cudaMemcpyAsync(&nt, sp.pt_off + sp.n_cells, sizeof nt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    rc = surf_grow_tris(f, nt);
+    if (rc) return rc;
+    CK(bm_launch_surface_tris(W->w, sp, st));
+    f->nv = nv;
+    f->nt = nt;
+  }
+  CK(bm_launch_surface_embed(W->w, sp, (int)f->nv, st));
+  CK(cudaStreamSynchronize(st));
+  if (n_vertices) *n_vertices = f->nv;
+  if (n_triangles) *n_triangles = f->nt;
+  return BM_OK;
+}
+
+int bm_surface_read(bm_surface_t f, float *vertices, float *reference, int32_t *triangles, uint32_t *masks,
+                    int dst_on_device) {
+  if (!valid_surface(f)) return fail(BM_E_INVALID, "bad surface or its scene has no storage");
+  cudaStream_t st = f->scene->world->st;
+  CK(cudaStreamSynchronize(st));
+  const size_t nv = (size_t)f->nv, nt = (size_t)f->nt;
+  const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // struct-of-arrays on the device, [n][3] / [n][2] at the ABI
+  auto interleave = [&](void *dst, void *const *cols, int ncol, size_t cnt) -> cudaError_t {
+    for (int a = 0; a < ncol; ++a) {
+      cudaError_t e = cudaMemcpy2DAsync((char *)dst + 4 * a, 4 * (size_t)ncol, cols[a], 4, 4, cnt, kind, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (nv && vertices) {
+    void *c[3] = {f->sp.cur[0], f->sp.cur[1], f->sp.cur[2]};
+    CK(interleave(vertices, c, 3, nv));
+  }
+  if (nv && reference) {
+    void *c[3] = {f->sp.ref[0], f->sp.ref[1], f->sp.ref[2]};
+    CK(interleave(reference, c, 3, nv));
+  }
+  if (nv && masks) {
+    void *c[2] = {f->sp.vmask[0], f->sp.vmask[1]};
+    CK(interleave(masks, c, 2, nv));
+  }
+  if (nt && triangles) CK(cudaMemcpyAsync(triangles, f->sp.tri, sizeof(int) * 3 * nt, kind, st));
+  CK(cudaStreamSynchronize(st));
+  return BM_OK;
+}
+
+int bm_surface_destroy(bm_surface_t f) {
+  if (!f) return fail(BM_E_INVALID, "null surface");
+  cudaStream_t st = (f->scene && f->scene->world) ? f->scene->world->st : nullptr;
+  f->release_all(st);
+  delete f;
+  return BM_OK;
+}
+
+}  // extern "C"
