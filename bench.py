@@ -412,6 +412,29 @@ def run_native(args):
                                "particles": sc1.n, "path": "plain (one scene per launch)",
                                "value": r1, "unit": UNIT, "substeps_timed": 200,
                                "first_substep": 100, "error_bits": int(g1.info().error_bits)}
+        # reference-grid surface of the cylinder mid-stroke (visual only; not
+        # part of the substep): full rebuild from the codes + embedding, and
+        # the embedding alone, each call timed by the wall clock (it
+        # synchronises to return the vertex and triangle counts)
+        from paper_2609_27342_gb300.surface import Surface
+        surf = Surface(g1, (2, 2, 2))
+        nv, nt = surf.update()
+        reps = 20
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            surf.update(rebuild=True)
+        t_rebuild = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            surf.update(rebuild=False)
+        t_embed = (time.perf_counter() - t0) / reps
+        lat = (2 * 100 + 1) * (2 * 20 + 1) * (2 * 20 + 1)
+        configs["surface"] = {"workload": "cylinder surface at substep 300 (cut 0 mid-stroke), "
+                                          "sub-cell lattice 2x2x2 per cell",
+                              "vertices": nv, "triangles": nt, "lattice_cells": lat,
+                              "rebuild_and_embed_ms": 1e3 * t_rebuild, "embed_ms": 1e3 * t_embed,
+                              "lattice_cells_per_s": lat / t_rebuild, "calls_timed": reps}
+        surf.close()
         g1.close()
         log(f"configs: {configs}")
 
