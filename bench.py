@@ -16,6 +16,7 @@ sampled SM clocks (``clocks``) and the FP64 oracle on the host cores
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -316,6 +317,12 @@ def run_native(args):
         roof = {"bound": "alu", "achieved": round(tfs, 3), "peak": round(alu_peak, 2),
                 "unit": "TFLOP/s", "frac": round(alu_frac, 4),
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"}
+    # the FP32 FMA ceiling measured on this GPU (independent FMA chains on
+    # every SM), beside the one derived from unit counts and the clock
+    fma = ctypes.c_double(0.0)
+    pkg._abi.check(pkg.load().bm_fp32_fma_peak(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(fma)))
+    roof["alu_peak_measured_tflops"] = round(fma.value, 2)
+    roof["alu_frac_of_measured"] = round(tfs / fma.value, 4) if fma.value > 0 else None
     traffic = ncu_traffic(dom, units)
     roof.update({"kernel": dom, "traffic": traffic, "algorithmic_bytes": alg_bytes,
                  "algorithmic_flops": alg_flops, "avg_launch_ms": round(ktimes[dom], 4),

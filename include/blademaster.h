@@ -406,6 +406,13 @@ int bm_surface_read(bm_surface_t f, float *vertices, float *reference, int32_t *
                     uint32_t *masks, int dst_on_device);
 int bm_surface_destroy(bm_surface_t f);
 
+/* Diagnostic: FP32 FMA throughput of the current device, measured by a
+ * kernel of independent fused multiply-add chains filling every SM (eight
+ * 256-thread blocks per SM), timed with CUDA events on `stream` (NULL: the
+ * default stream).  *tflops receives 2 x FMAs / second / 1e12.  The ceiling
+ * for the ALU-bound parts of the substep (no tensor cores are involved). */
+int bm_fp32_fma_peak(void *stream, double *tflops);
+
 const char *bm_last_error(void);
 const char *bm_version(void);
 

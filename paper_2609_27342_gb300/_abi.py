@@ -118,6 +118,7 @@ SIGNATURES = {
     "bm_surface_update": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "bm_surface_read": (C.c_int, [VP, VP, VP, VP, VP, C.c_int]),
     "bm_surface_destroy": (C.c_int, [VP]),
+    "bm_fp32_fma_peak": (C.c_int, [VP, PD]),
     "bm_scene_destroy": (C.c_int, [VP]),
     "bm_batch_create": (C.c_int, [C.POINTER(BatchDesc), C.POINTER(Alloc), VP, PVP]),
     "bm_batch_scene_create": (C.c_int, [VP, C.POINTER(SceneDesc), C.POINTER(BladeDesc),

@@ -1964,3 +1964,60 @@ int bm_surface_destroy(bm_surface_t f) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Diagnostic: measured FP32 FMA throughput (the ALU roofline's ceiling)
+// ============================================================================
+namespace {
+constexpr int kFmaUnroll = 16;
+__global__ void __launch_bounds__(256) k_fma_peak(float *out, int iters, float seed) {
+  // eight independent chains per thread keep every FMA pipe busy
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + (float)(threadIdx.x + k);
+  const float b = 0.999999f, c = 1e-6f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kFmaUnroll; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == 1234.5f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+}  // namespace
+
+extern "C" int bm_fp32_fma_peak(void *stream, double *tflops) {
+  if (!tflops) return fail(BM_E_INVALID, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  float *out = nullptr;
+  CK(cudaMalloc(&out, sizeof(float) * (size_t)blocks * threads));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaSuccess;
+  float best = 0.f;
+  for (int r = 0; r < 4 && e == cudaSuccess; ++r) {  // first run warms up
+    cudaEventRecord(e0, st);
+    k_fma_peak<<<blocks, threads, 0, st>>>(out, iters, 1.0f);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && r > 0 && ms > 0.f) best = std::max(best, 1.f / ms);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  CK(e);
+  const double flop = 2.0 * kFmaUnroll * 8 * (double)iters * blocks * threads;
+  *tflops = flop * (double)best * 1e3 / 1e12;
+  return BM_OK;
+}
