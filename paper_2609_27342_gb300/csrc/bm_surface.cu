@@ -356,10 +356,12 @@ __global__ void k_sf_tris(World w, SurfParams sp) {
 }
 
 // --------------------------------------------------------------------------
-// side-aware embedding: 8 lanes per vertex, one per trilinear node; each
-// lane takes the B-spline-weighted mean displacement of the particles with
-// the anchor's exact code around its node, then the group sums the 8 in node
-// order
+// side-aware embedding: 8 lanes per vertex share the lattice points around
+// its 8 trilinear nodes (the union of the nodes' B-spline supports, split by
+// z slice); each lane sums, for every node, the weights and weighted
+// displacements of the particles with the anchor's exact code, then the
+// group adds the lanes' sums (xor butterfly) and lane 0 combines the nodes
+// in node order
 // --------------------------------------------------------------------------
 __device__ __forceinline__ int jfirst(const SurfParams &sp, int a, int B) {
   if (B <= sp.bmin[a]) return 0;
@@ -367,7 +369,8 @@ __device__ __forceinline__ int jfirst(const SurfParams &sp, int a, int B) {
   return sp.jstart[a][B - sp.bmin[a]];
 }
 
-// quadratic B-spline weight of node base + o for fractional offset f in [0.5, 1.5)
+// quadratic B-spline weight of node base + o for fractional offset f in
+// [0.5, 1.5); zero outside the stencil (o not in 0..2)
 __device__ __forceinline__ float bsw(int o, float f) {
   if (o == 0) {
     const float t = 1.5f - f;
@@ -377,73 +380,90 @@ __device__ __forceinline__ float bsw(int o, float f) {
     const float t = f - 1.f;
     return 0.75f - t * t;
   }
-  const float t = f - 0.5f;
-  return 0.5f * t * t;
+  if (o == 2) {
+    const float t = f - 0.5f;
+    return 0.5f * t * t;
+  }
+  return 0.f;
 }
 
 __global__ void k_sf_embed(World w, SurfParams sp, int nv) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int v = (int)(t >> 3), d = (int)(t & 7);
+  const int v = (int)(t >> 3), lane8 = (int)(t & 7);
   const bool valid = v < nv;
-  float q[4] = {0.f, 0.f, 0.f, 0.f};  // t_d U / W (xyz), t_d
-  float c[3] = {0.f, 0.f, 0.f};
+  float acc[8][4];  // per trilinear node: sum N, sum N (x - X)
+#pragma unroll
+  for (int d = 0; d < 8; ++d) acc[d][0] = acc[d][1] = acc[d][2] = acc[d][3] = 0.f;
+  float c[3] = {0.f, 0.f, 0.f}, tw[3] = {0.f, 0.f, 0.f};
   int g0 = 0;
   uint32_t a1 = 0u, a2 = 0u;
   if (valid) {
     g0 = sp.p_begin + sp.anchor[v];
     a1 = w.P.s1[g0];
     a2 = w.P.s2[g0];
-    int node[3], j0[3], j1[3];
-    float wt = 1.f;
+    int n0[3], jlo[3], jhi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       c[a] = sp.ref[a][v];
       const double f = ((double)c[a] - sp.origin[a]) / sp.dx;
       const double fb = floor(f);
-      const float tt = (float)(f - fb);
-      node[a] = (int)fb + ((d >> a) & 1);
-      wt *= ((d >> a) & 1) ? tt : 1.f - tt;
-      j0[a] = jfirst(sp, a, node[a] - 2);
-      j1[a] = jfirst(sp, a, node[a] + 1);
+      tw[a] = (float)(f - fb);
+      n0[a] = (int)fb;
+      // particles whose stencil holds node n0 or n0 + 1: base cells n0 - 2 .. n0 + 1
+      jlo[a] = jfirst(sp, a, n0[a] - 2);
+      jhi[a] = jfirst(sp, a, n0[a] + 2);
     }
-    float W = 0.f, U[3] = {0.f, 0.f, 0.f};
-    for (int z = j0[2]; z < j1[2]; ++z)
-      for (int y = j0[1]; y < j1[1]; ++y)
-        for (int x = j0[0]; x < j1[0]; ++x) {
+    for (int z = jlo[2] + lane8; z < jhi[2]; z += 8)
+      for (int y = jlo[1]; y < jhi[1]; ++y)
+        for (int x = jlo[0]; x < jhi[0]; ++x) {
           const int p = sp.lat[((long long)z * sp.n[1] + y) * sp.n[0] + x];
           if (p < 0) continue;
           const int g = sp.p_begin + p;
           if (w.P.s1[g] != a1 || w.P.s2[g] != a2) continue;
           const uint32_t bb = w.P.base[g];
-          const int ox = node[0] - ((int)(bb & 1023u) + sp.lo[0]);
-          const int oy = node[1] - ((int)((bb >> 10) & 1023u) + sp.lo[1]);
-          const int oz = node[2] - ((int)((bb >> 20) & 1023u) + sp.lo[2]);
-          const float N = bsw(ox, w.P.fx[0][g]) * bsw(oy, w.P.fx[1][g]) * bsw(oz, w.P.fx[2][g]);
-          W += N;
-          U[0] += N * (w.P.x[0][g] - sp.Xr[0][p]);
-          U[1] += N * (w.P.x[1][g] - sp.Xr[1][p]);
-          U[2] += N * (w.P.x[2][g] - sp.Xr[2][p]);
+          const int ox = n0[0] - ((int)(bb & 1023u) + sp.lo[0]);
+          const int oy = n0[1] - ((int)((bb >> 10) & 1023u) + sp.lo[1]);
+          const int oz = n0[2] - ((int)((bb >> 20) & 1023u) + sp.lo[2]);
+          const float fx = w.P.fx[0][g], fy = w.P.fx[1][g], fz = w.P.fx[2][g];
+          const float wx[2] = {bsw(ox, fx), bsw(ox + 1, fx)};
+          const float wy[2] = {bsw(oy, fy), bsw(oy + 1, fy)};
+          const float wz[2] = {bsw(oz, fz), bsw(oz + 1, fz)};
+          const float u0 = w.P.x[0][g] - sp.Xr[0][p], u1 = w.P.x[1][g] - sp.Xr[1][p],
+                      u2 = w.P.x[2][g] - sp.Xr[2][p];
+#pragma unroll
+          for (int d = 0; d < 8; ++d) {
+            const float N = wx[d & 1] * wy[(d >> 1) & 1] * wz[d >> 2];
+            acc[d][0] += N;
+            acc[d][1] += N * u0;
+            acc[d][2] += N * u1;
+            acc[d][3] += N * u2;
+          }
         }
-    if (W > 0.f) {
-      const float s = wt / W;
-      q[0] = s * U[0];
-      q[1] = s * U[1];
-      q[2] = s * U[2];
-      q[3] = wt;
-    }
   }
-  // fixed-order sum over the group's 8 lanes
-  const int lane0 = (threadIdx.x & 31) & ~7;
-  float sum[4] = {0.f, 0.f, 0.f, 0.f};
+  // sums over the group's 8 lanes (the xor partners stay inside the group)
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
+  for (int m = 1; m < 8; m <<= 1)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) sum[e] += __shfl_sync(kFull, q[e], lane0 + k);
-  if (valid && d == 0) {
+    for (int d = 0; d < 8; ++d)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[d][e] += __shfl_xor_sync(kFull, acc[d][e], m);
+  if (valid && lane8 == 0) {
+    float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      if (!(acc[d][0] > 0.f)) continue;  // no particle of this code around the node
+      const float wt = ((d & 1) ? tw[0] : 1.f - tw[0]) * (((d >> 1) & 1) ? tw[1] : 1.f - tw[1]) *
+                       ((d >> 2) ? tw[2] : 1.f - tw[2]);
+      const float s = wt / acc[d][0];
+      num[0] += s * acc[d][1];
+      num[1] += s * acc[d][2];
+      num[2] += s * acc[d][3];
+      den += wt;
+    }
     const int p0 = sp.anchor[v];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float u = sum[3] > 0.f ? sum[a] / sum[3] : w.P.x[a][g0] - sp.Xr[a][p0];
+      const float u = den > 0.f ? num[a] / den : w.P.x[a][g0] - sp.Xr[a][p0];
       sp.cur[a][v] = c[a] + u;
     }
     sp.vmask[0][v] = a1;
