@@ -331,25 +331,41 @@ def run_native(args):
     step_ms = ms / args.steps
     step_roof = STEP_ALGORITHMIC_BYTES * n_particles / (step_ms * 1e-3) / 1e9
 
-    # end to end through the C ABI: host tool states in, wrenches out, each step
-    n = len(plain_objs)
+    # end to end through the C ABI on a fresh copy of the workload, over the
+    # same substeps as the device-timed region: every substep the tool states
+    # go in from pinned host memory and the reaction wrenches come back to it
+    e2e_objs = [pkg.Scene(s, stream=stream) for s in scenes]
+    eb = make_batch(e2e_objs)
+    eb.set_tiles(shape["graph_chunk"], shape["node_tile"], shape["brick_variant"])
+    n = len(e2e_objs)
     h_states = torch.empty((n, 18), dtype=torch.float64, pin_memory=True)
     h_wr = torch.empty((n, 6), dtype=torch.float64, pin_memory=True)
-    st0 = np.stack([o.tool_state() for o in plain_objs])
-    vel = st0[:, 12:15].copy()
+    pose = np.stack([o.tool_state() for o in e2e_objs])
+    vel = pose[:, 12:15].copy()
     dts = np.array([s.dt for s in scenes])
-    pose = st0.copy()
-    e2e_steps = max(3, min(args.steps, 50))
+
+    def e2e_substep():
+        pose[:, 0:3] += vel * dts[:, None]
+        h_states.numpy()[:] = pose
+        eb.set_tool_states_ptr(h_states.data_ptr(), n, False)
+        eb.step(1)
+        eb.tool_wrenches_ptr(h_wr.data_ptr(), n, False)
+
+    for _ in range(args.warmup):
+        e2e_substep()
+    e2e_steps = args.steps
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        pose[:, 0:3] += vel * dts[:, None]
-        h_states.numpy()[:] = pose
-        batch.set_tool_states_ptr(h_states.data_ptr(), n, False)
-        batch.step(1)
-        batch.tool_wrenches_ptr(h_wr.data_ptr(), n, False)
+        e2e_substep()
     wall, _ = reduce_over_ranks(dist, (time.perf_counter() - t0) * 1e3, n_particles)
     e2e_value = job_particles * e2e_steps / (wall * 1e-3)
+    eb.close()
+    for o in e2e_objs:
+        o.close()
+    del e2e_objs, eb
 
     # adjoint calibration workload: 32,000 particles, 200 substeps, checkpoint
     # every 20, loss on the reaction-force trajectory against a target made at
