@@ -491,19 +491,17 @@ def run_native(args):
 
     # continuous-batching server on a Poisson request stream (rollouts of
     # 8k-500k particles, 200-2000 substeps, 1-3 cuts), admission by an HBM budget
+    # (one server per GPU; requests routed to ranks by assigned work, the same
+    # assignment computed on every rank; statistics combined on the host)
     serving = None
     if args.serve_requests > 0:
-        from paper_2609_27342_gb300.serving import Server
+        from paper_2609_27342_gb300.serving import serve_sharded
         reqs = bi.serving_requests(n_requests=args.serve_requests, seed=3)
         budget = int(args.serve_budget_gb * (1 << 30))
-        srv = Server(budget_bytes=budget, max_scenes=args.serve_requests, max_chunk=16,
-                     max_particles=sum(r.scene.n for r in reqs), node_tile=shape["node_tile"],
-                     brick_variant=shape["brick_variant"])
-        for r in reqs:
-            srv.submit(r.scene, r.n_substeps, arrival_s=r.arrival_s)
-        st = srv.run(realtime=True, timeout_s=600)
-        srv.close()
-        serving = {"requests": st["requests"], "rate_hz": 50, "budget_gb": args.serve_budget_gb,
+        st = serve_sharded(reqs, rank, world, budget, dist=dist, max_chunk=16,
+                           node_tile=shape["node_tile"], brick_variant=shape["brick_variant"])
+        serving = {"requests": st["requests"], "ranks": st["ranks"], "rate_hz": 50,
+                   "budget_gb": args.serve_budget_gb,
                    "throughput": st["throughput"], "unit": UNIT, "wall_s": st["wall_s"],
                    "step_ms_p50": st["step_ms_p50"], "step_ms_p99": st["step_ms_p99"],
                    "request_latency_s_p50": st["request_latency_s_p50"],

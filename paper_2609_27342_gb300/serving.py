@@ -177,3 +177,62 @@ class Server:
 
     def close(self):
         self.batch.close()
+
+
+# -- several GPUs -------------------------------------------------------------
+def route(requests, n_ranks: int, budget_bytes: int, footprint_bytes=None) -> List[int]:
+    """Rank of every request when one server per GPU shares a request stream.
+
+    Requests (objects with ``scene``, ``n_substeps`` and ``arrival_s``) are
+    taken in arrival order and each goes to the rank with the least work
+    assigned so far (particles x substeps) among those whose budget holds its
+    footprint; ties go to the lower rank.  The assignment depends only on the
+    request stream, so every rank computes the same one on its own: no
+    message carries requests and the data path has no collective.  A request
+    that fits no rank's budget is refused with ValueError."""
+    if footprint_bytes is None:
+        footprint_bytes = lambda sc: footprint(sc)[3]  # noqa: E731
+    order = sorted(range(len(requests)), key=lambda i: (requests[i].arrival_s, i))
+    work = [0] * n_ranks
+    out = [-1] * len(requests)
+    for i in order:
+        r = requests[i]
+        nb = footprint_bytes(r.scene)
+        if nb > budget_bytes:
+            raise ValueError(f"request {i} needs {nb} bytes, more than a rank's budget")
+        k = min(range(n_ranks), key=lambda q: (work[q], q))
+        out[i] = k
+        work[k] += r.scene.n * int(r.n_substeps)
+    return out
+
+
+def serve_sharded(requests, rank: int, n_ranks: int, budget_bytes: int, dist=None, **server_kw) -> dict:
+    """Serve this rank's share of a request stream (see ``route``) on its GPU
+    and combine the ranks' statistics on the host: the job's throughput is
+    the particle-substeps of all ranks over the slowest rank's wall time.
+    ``dist`` is ``torch.distributed`` (initialised) or None for one rank."""
+    ranks = route(requests, n_ranks, budget_bytes)
+    mine = [r for r, k in zip(requests, ranks) if k == rank]
+    srv = Server(budget_bytes=budget_bytes, max_scenes=max(1, len(mine)),
+                 max_particles=max(1, sum(r.scene.n for r in mine)), **server_kw)
+    for r in mine:
+        srv.submit(r.scene, r.n_substeps, arrival_s=r.arrival_s)
+    st = srv.run(realtime=True, timeout_s=600) if mine else srv.stats(0.0)
+    srv.close()
+    return combine_stats(st, dist, n_requests=len(mine))
+
+
+def combine_stats(st: dict, dist=None, n_requests: Optional[int] = None) -> dict:
+    """Job-wide serving statistics from every rank's (host-side gather)."""
+    if dist is None:
+        return dict(st, ranks=1)
+    allst = [None] * dist.get_world_size()
+    dist.all_gather_object(allst, dict(st, requests=st["requests"] if n_requests is None else n_requests))
+    wall = max(s["wall_s"] for s in allst)
+    ps = sum(s["particle_substeps"] for s in allst)
+    return {"ranks": len(allst), "requests": sum(s["requests"] for s in allst), "wall_s": wall,
+            "throughput": ps / wall if wall > 0 else 0.0, "particle_substeps": ps,
+            "step_ms_p50": max(s["step_ms_p50"] for s in allst),
+            "step_ms_p99": max(s["step_ms_p99"] for s in allst),
+            "request_latency_s_p50": max(s["request_latency_s_p50"] for s in allst),
+            "request_latency_s_p99": max(s["request_latency_s_p99"] for s in allst)}
