@@ -492,6 +492,13 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sm, int &total) {
 #define TE 6
 #define TN 216
 #define TSCAP BM_TILE_SLOTS
+
+// Index of particle j of cell c in a brick's [particle-in-cell][cell]
+// staging in shared memory.  The cell column is XOR-swizzled by the particle
+// index, so that both the staging stores (consecutive particles of a few
+// cells) and the per-cell reads (consecutive cells, one particle index) fall
+// on distinct banks.
+__device__ __forceinline__ int pic(int j, int c) { return j * BR3 + (c ^ ((j & 7) << 2)); }
 #define BT 192  // threads per brick CTA: 64 cells x 3 z-offsets
 
 __device__ __forceinline__ void node_coords(const DevScene &sc, int li, int &ix, int &iy, int &iz) {
@@ -810,7 +817,7 @@ __device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, 
           const int cc = (zz * BR + yy) * BR + xx;
           if (it >= ncode[cc]) continue;
           if (n > 1) {
-            const int k = ccode[cc][it] * BR3 + cc;
+            const int k = pic(ccode[cc][it], cc);
             if (ps1[k] != code.x || ps2[k] != code.y) continue;
           }
           const int src = ozz * BR3 + cc, q = (oyy * 3 + oxx) * NV;
@@ -852,7 +859,7 @@ __device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y
     particle_base(P.base[p], bx, by, bz);
     const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
     if (pass > 0 && S.ncode[c] <= pass) continue;
-    const int si = (i - S.cs[c]) * BR3 + c;
+    const int si = pic(i - S.cs[c], c);
     S.part[0][si] = P.fx[0][p];
     S.part[1][si] = P.fx[1][p];
     S.part[2][si] = P.fx[2][p];
@@ -882,11 +889,11 @@ __device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s
   const int n = cs[c + 1] - cs[c];
   int cnt = 0;
   for (int j = 0; j < n; ++j) {
-    const int k = j * BR3 + c;
+    const int k = pic(j, c);
     const uint32_t a = s1[k], b = s2[k];
     bool seen = false;
     for (int q = 0; q < cnt; ++q) {
-      const int kq = ccode[c][q] * BR3 + c;
+      const int kq = pic(ccode[c][q], c);
       if (s1[kq] == a && s2[kq] == b) {
         seen = true;
         break;
@@ -895,29 +902,6 @@ __device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s
     if (!seen) ccode[c][cnt++] = (uint8_t)j;
   }
   ncode[c] = (uint8_t)cnt;
-  atomicMax(maxcodes, cnt);
-}
-
-template <int PPC>
-__device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s2, const int *cs,
-                                           bool pool_order, uint2 (*ccode)[PPC], int *ncode,
-                                           int *maxcodes) {
-  const int c = threadIdx.x;
-  if (c >= BR3) return;
-  const int n = cs[c + 1] - cs[c];
-  int cnt = 0;
-  for (int j = 0; j < n; ++j) {
-    const int k = pool_order ? cs[c] + j : j * BR3 + c;
-    const uint32_t a = s1[k], b = s2[k];
-    bool seen = false;
-    for (int q = 0; q < cnt; ++q)
-      if (ccode[c][q].x == a && ccode[c][q].y == b) {
-        seen = true;
-        break;
-      }
-    if (!seen) ccode[c][cnt++] = make_uint2(a, b);
-  }
-  ncode[c] = cnt;
   atomicMax(maxcodes, cnt);
 }
 
@@ -963,7 +947,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
       __syncthreads();
     }
     const bool has = it < S.ncode[c];
-    const int kc = has ? S.ccode[c][it] * BR3 + c : 0;
+    const int kc = has ? pic(S.ccode[c][it], c) : 0;
     const uint32_t k1 = has ? S.ps1[kc] : 0u, k2 = has ? S.ps2[kc] : 0u;
     const bool uniform = S.ncode[c] == 1;
     float a[9][7];
@@ -973,7 +957,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
       for (int f = 0; f < 7; ++f) a[q][f] = 0.f;
     if (has) {
       for (int j = 0; j < n_c; ++j) {
-        const int si = j * BR3 + c;
+        const int si = pic(j, c);
         if (!uniform && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
         float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
         const float f0 = S.part[0][si], f1 = S.part[1][si], f2 = S.part[2][si];
@@ -1220,7 +1204,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
     particle_base(P.base[p], bx, by, bz);
     const int lx = bx - c0x, ly = by - c0y, lz = bz - c0z;
     const int c = (lz * BR + ly) * BR + lx;
-    const int si = (i - S.cs[c]) * BR3 + c;
+    const int si = pic(i - S.cs[c], c);
     const uint32_t s1 = P.s1[p], s2 = P.s2[p];
     const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
     float wx[3], wy[3], wz[3], d;
@@ -1326,7 +1310,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   const int pbase = w.B.poff[bt.y];
   for (int it = 0; it < iters; ++it) {
     const bool has = it < S.ncode[c];
-    const int kc = has ? S.ccode[c][it] * BR3 + c : 0;
+    const int kc = has ? pic(S.ccode[c][it], c) : 0;
     const uint32_t k1 = has ? S.ps1[kc] : 0u, k2 = has ? S.ps2[kc] : 0u;
     const bool uniform = S.ncode[c] == 1;
     float a[9][3];
@@ -1334,7 +1318,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
     for (int q = 0; q < 9; ++q) a[q][0] = a[q][1] = a[q][2] = 0.f;
     if (has) {
       for (int j = 0; j < n_c; ++j) {
-        const int si = j * BR3 + c;
+        const int si = pic(j, c);
         if (!uniform && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
         float wx[3], wy[3], wz, d;
         const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
