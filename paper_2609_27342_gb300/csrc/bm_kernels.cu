@@ -499,6 +499,12 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sm, int &total) {
 // cells) and the per-cell reads (consecutive cells, one particle index) fall
 // on distinct banks.
 __device__ __forceinline__ int pic(int j, int c) { return j * BR3 + (c ^ ((j & 7) << 2)); }
+
+// Staged per-(cell, z-offset) sums: one row per value, one column per thread,
+// each 32 columns followed by one pad word, so that sources 32 apart (cells
+// two z-layers apart) and rows fall on different banks in the tile gather.
+#define STG (BT + BT / 32)
+__device__ __forceinline__ int stg(int src) { return src + (src >> 5); }
 #define BT 192  // threads per brick CTA: 64 cells x 3 z-offsets
 
 __device__ __forceinline__ void node_coords(const DevScene &sc, int li, int &ix, int &iy, int &iz) {
@@ -775,7 +781,7 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
 // code in the whole brick, one logical grid at every tile node) no source
 // needs a code test: cells without particles staged zeros.
 template <int PPC, int NV, class Put>
-__device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, const float (*stage)[BT],
+__device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, const float (*stage)[STG],
                                                  const uint8_t *ncode, const uint8_t (*ccode)[PPC],
                                                  const uint32_t *ps1, const uint32_t *ps2, int it,
                                                  int t, bool uniform, int pbase, Put put) {
@@ -797,7 +803,7 @@ __device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, 
           const int src = ozz * BR3 + ((tz - ozz) * BR + (ty - oyy)) * BR + (tx - oxx);
           const int q = (oyy * 3 + oxx) * NV;
 #pragma unroll
-          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][src];
+          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][stg(src)];
         }
     put(e0, acc);
     return;
@@ -822,7 +828,7 @@ __device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, 
           }
           const int src = ozz * BR3 + cc, q = (oyy * 3 + oxx) * NV;
 #pragma unroll
-          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][src];
+          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][stg(src)];
         }
       }
     }
@@ -834,7 +840,7 @@ template <int PPC>
 struct K2S {
   Tile T;
   union {
-    float stage[9 * 7][BT];      // per (cell, z-offset) thread: sums for its 9 nodes
+    float stage[9 * 7][STG];     // per (cell, z-offset) thread: sums for its 9 nodes
     float part[18][PPC * BR3];   // the brick's particles (fx, v, A, J), [particle-in-cell][cell]
   };
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
@@ -1001,7 +1007,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
 #pragma unroll
       for (int q = 0; q < 9; ++q)
 #pragma unroll
-        for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][tid] = a[q][f];
+        for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][stg(tid)] = a[q][f];
     __syncthreads();
     // tile nodes gather the staged sums of the cells around them: nodes
     // 0..191 one per thread, the last 24 one (node, value) per thread
@@ -1147,7 +1153,7 @@ struct K4S {
       float4 tvo[TSCAP];      // v_old xyz, m of the tile slots (G2P)
       float4 tvn[TSCAP];      // v_new xyz
     };
-    float stage[9 * 3][BT];   // then: per (cell, z-offset) MUSL sums for 9 nodes
+    float stage[9 * 3][STG];  // then: per (cell, z-offset) MUSL sums for 9 nodes
   };
   float pf[3][PPC * BR3];
   float pv[3][PPC * BR3];
@@ -1343,7 +1349,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
 #pragma unroll
       for (int q = 0; q < 9; ++q)
 #pragma unroll
-        for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][tid] = a[q][f];
+        for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][stg(tid)] = a[q][f];
     __syncthreads();
     if (pbase >= 0) {
       auto put = [&](size_t e, const float *acc) {  // pm = MUSL momentum sums
