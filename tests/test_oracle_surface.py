@@ -310,3 +310,30 @@ def test_surface_of_a_simulated_cut():
     x = o.get("x")
     cur = S.embed(r, X, x, s1, s2, sc.dx, sc.origin)
     assert np.isfinite(cur).all() and np.abs(cur - V).max() < 5 * sc.dx
+
+
+def test_two_intersecting_cuts_give_four_closed_boxes():
+    """Two full axis cuts (x and y mid-planes, cuts 0 and 1) split the box into
+    four closed quarter boxes; along the line where the cuts cross, each
+    quarter keeps its own vertices."""
+    X = box(4, 4, 2)
+    s1x, s2x = split_codes(X, 0, 4 * DX / 2)
+    s1y, s2y = split_codes(X, 1, 4 * DX / 2)
+    s1 = (s1x | (s1y << 1)).astype(np.uint32)
+    s2 = (s2x | (s2y << 1)).astype(np.uint32)
+    pl = np.zeros((32, 4))
+    pl[0] = [1, 0, 0, 2 * DX]
+    pl[1] = [0, 1, 0, 2 * DX]
+    r = S.reconstruct(X, s1, s2, DX, planes=pl, plane_mask=3)
+    V, T = r["ref"], r["tris"]
+    comp = S.components(len(V), T)
+    assert len(np.unique(comp)) == 4
+    quarter = 2 * DX * 2 * DX * 2 * DX
+    for c in np.unique(comp):
+        Tc = T[np.isin(T[:, 0], np.nonzero(comp == c)[0])]
+        assert S.directed_edges_paired(Tc)
+        assert euler(int((comp == c).sum()), Tc) == 2
+        assert S.signed_volume(V, Tc) == pytest.approx(quarter, rel=1e-6)
+        # every vertex of a quarter carries that quarter's code
+        codes = {(int(s1[a]), int(s2[a])) for a in r["anchor"][comp == c]}
+        assert len(codes) == 1
