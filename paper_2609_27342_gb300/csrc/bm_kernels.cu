@@ -643,8 +643,10 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
     float v[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
     const uint32_t s1 = P.s1[p], s2 = P.s2[p];
     float J[3] = {0.f, 0.f, 0.f};
-    float D = sc.reset_D ? 0.0f : P.D[p];
-    float uh[3] = {P.ut[0][p], P.ut[1][p], P.ut[2][p]};
+    const float D0 = P.D[p];
+    float D = sc.reset_D ? 0.0f : D0;
+    const float u00 = P.ut[0][p], u01 = P.ut[1][p], u02 = P.ut[2][p];
+    float uh[3] = {u00, u01, u02};
     if (sc.has_blade && sc.tool_contact_on) {
       float xc[3], nB[3], phi;
       box_closest(sc, x, sc.Rp, xc, nB, phi);
@@ -739,10 +741,14 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
     P.J[0][p] = J[0];
     P.J[1][p] = J[1];
     P.J[2][p] = J[2];
-    P.D[p] = D;
-    P.ut[0][p] = uh[0];
-    P.ut[1][p] = uh[1];
-    P.ut[2][p] = uh[2];
+    // cutting progress and friction history are written back only when they
+    // change (most particles touch no tool in a substep)
+    if (!(D == D0)) P.D[p] = D;
+    if (!(uh[0] == u00 && uh[1] == u01 && uh[2] == u02)) {
+      P.ut[0][p] = uh[0];
+      P.ut[1][p] = uh[1];
+      P.ut[2][p] = uh[2];
+    }
     P.pend[p] = pend;
   }
   if (clamped) atomicOr(&scm.err, BM_ERRBIT_INVERTED);
