@@ -58,6 +58,7 @@ KERNEL_MODEL = {
     "k_fupd": {"bytes": (97, 0, 54, 1080), "flops": (650, 0, 0, 0)},
 }
 STEP_ALGORITHMIC_BYTES = 156  # per particle-substep: the state the method must move
+LATE_FIRST = 900              # first substep of the late timing window (of the 1,000-substep rollout)
 LAUNCHES_PER_SUBSTEP = 11     # kernels one batched substep launches (no pair contact)
 
 
@@ -331,6 +332,33 @@ def run_native(args):
     step_ms = ms / args.steps
     step_roof = STEP_ALGORITHMIC_BYTES * n_particles / (step_ms * 1e-3) / 1e9
 
+    # late window: the same batch advanced (untimed) to substep LATE_FIRST of
+    # its 1,000-substep rollout, where most bricks hold cut faces, then the
+    # same number of substeps timed again (the early window above starts at
+    # the rollout's beginning, where the cuts are still shallow)
+    late = None
+    done = args.warmup + args.steps + max(3, min(args.steps, 20))
+    if args.late_window and done < LATE_FIRST:
+        batch.step(LATE_FIRST - done)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0.record(stream)
+        batch.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms_late, _ = reduce_over_ranks(dist, e0.elapsed_time(e1), n_particles)
+        prof_late = batch.profile(max(3, min(args.steps, 20)))
+        late = {"value": job_particles * args.steps / (ms_late * 1e-3), "unit": UNIT,
+                "first_substep": LATE_FIRST, "substeps": args.steps,
+                "ms_per_step": ms_late / args.steps,
+                "step_hbm_frac": round(STEP_ALGORITHMIC_BYTES * n_particles /
+                                       (ms_late / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
+                "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof_late.items()}}
+        log(f"late window: {late}")
+
     # end to end through the C ABI on a fresh copy of the workload, over the
     # same substeps as the device-timed region: every substep the tool states
     # go in from pinned host memory and the reaction wrenches come back to it
@@ -534,6 +562,10 @@ def run_native(args):
                        "job_particles": job_particles, "seeds": f"{SEED}..{SEED + world - 1} (one per rank)",
                        "nodes": n_nodes, "slots": n_slots, "seed": SEED,
                        "bricks": n_bricks, "substeps_timed": args.steps,
+                       "windows": {"value": f"substeps {args.warmup}..{args.warmup + args.steps - 1} "
+                                            "of the 1,000-substep rollout",
+                                   "late_window": f"substeps {LATE_FIRST}..{LATE_FIRST + args.steps - 1}"
+                                   if late else None},
                        "launch_shape": shape,
                        "parallelism": f"scene-sharded x{world} (each rank its own batch)",
                        "l2": "inputs larger than L2 (state ~1.2 GB vs 129 MB L2)"},
@@ -545,6 +577,7 @@ def run_native(args):
             "step_hbm_roofline": {"bytes_per_particle_substep": STEP_ALGORITHMIC_BYTES,
                                   "achieved": round(step_roof, 1), "peak": hbm_peak,
                                   "unit": "GB/s", "frac": round(step_roof / hbm_peak, 4)},
+            "late_window": late,
             "plain": {"value": plain_rate, "unit": UNIT, "substeps": plain_steps,
                       "launches_per_substep_per_scene": LAUNCHES_PER_SUBSTEP},
             "batched_over_plain": (value / world / plain_rate) if plain_rate else None,
@@ -617,6 +650,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-configs", dest="configs", action="store_false")
+    ap.add_argument("--no-late-window", dest="late_window", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -142,7 +142,14 @@ typedef struct {
 /* Field ids for bm_read_state / bm_write_state.  Element types:
  *   X, x, v, ut: float32 [n][3];  F: float32 [n][9];  D: float32 [n];
  *   CODE: int64 [n] ternary code c_p of Eq. 7 (read only);
- *   MASK1, MASK2: uint32 [n] -- bit k set <=> digit k is 1 (resp. 2). */
+ *   MASK1, MASK2: uint32 [n] -- bit k set <=> digit k is 1 (resp. 2);
+ *   PAIR_PARTNER: int32 [n][16], PAIR_U: float32 [n][16][3] (read only,
+ *   scenes with material-material contact): the tangential spring history of
+ *   Eq. 12 between particle pairs in contact, as the next substep will read
+ *   it.  Each pair in contact is listed once, by one of its two particles:
+ *   entry k of particle p names the partner q (caller index; -1 ends the
+ *   list) and PAIR_U[p][k] is the spring displacement u of p's motion
+ *   relative to q (the same pair seen from q has -u). */
 enum {
   BM_FIELD_X = 1u << 0,
   BM_FIELD_x = 1u << 1,
@@ -152,9 +159,11 @@ enum {
   BM_FIELD_UT = 1u << 5,
   BM_FIELD_CODE = 1u << 6,
   BM_FIELD_MASK1 = 1u << 7,
-  BM_FIELD_MASK2 = 1u << 8
+  BM_FIELD_MASK2 = 1u << 8,
+  BM_FIELD_PAIR_PARTNER = 1u << 9,
+  BM_FIELD_PAIR_U = 1u << 10
 };
-#define BM_NUM_FIELDS 9
+#define BM_NUM_FIELDS 11
 
 typedef struct {
   int64_t n_particles;
@@ -164,6 +173,7 @@ typedef struct {
   int64_t step;              /* substeps taken */
   uint32_t error_bits;       /* sticky BM_ERRBIT_* word */
   int grid_lo[3], grid_dim[3];
+  int32_t current_cut;       /* id of the cut in progress (the last cut-creating segment), -1 before any */
 } bm_scene_info;
 
 /* ---- scene ------------------------------------------------------------- */
@@ -212,11 +222,13 @@ int bm_wrench_history(bm_scene_t s, int blade_id, int64_t first, int64_t count, 
  * stall for milliseconds), or a process whose device memory is already
  * reserved by a framework's caching allocator, where a per-call cudaMalloc
  * can fail.  Same layout and result as bm_read_state with host destinations
- * (dst are host pointers).  Each field is gathered into a fixed 16 MiB
- * staging array that the library keeps in device memory for the life of the
- * process (every GPU that loads the library holds it), then copied to dst;
- * a field larger than 16 MiB (e.g. F beyond 466,033 particles) is rejected
- * with BM_E_INVALID before any work is enqueued.  The first call on a device
+ * (dst are host pointers).  The library keeps ONE staging array of 16 MiB
+ * in device memory for the life of the process (every GPU that loads the
+ * library holds its own copy); each requested field in turn is gathered into
+ * it and copied to dst, so each field may be at most 16 MiB: a larger field
+ * (e.g. F beyond 466,033 particles) is rejected with BM_E_INVALID before any
+ * work is enqueued.  The scene's device (current when it was created) must
+ * be the current device, else BM_E_INVALID.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
  * device current -- make that first call before any stream capture.  All
  * calls share the one array and synchronise the scene's stream before they

@@ -1240,7 +1240,9 @@ int or_step(or_scene *s, int nsteps) {
 /* ------------------------------------------------------------------------ */
 /* state access                                                              */
 /* ------------------------------------------------------------------------ */
-/* field ids: 0 X, 1 x, 2 v, 3 F, 4 D, 5 ut, 6 code (as double), 7 J, 8 digits (n*32) */
+/* field ids: 0 X, 1 x, 2 v, 3 F, 4 D, 5 ut, 6 code (as double), 7 J, 8 digits (n*32),
+   9 pair-contact history (n * OR_HIST entries of {partner or -1, u[3]}; the
+   pair list of particle p holds the pairs it owns, i.e. partners q > p) */
 
 int or_get(const or_scene *s, int field, double *out) {
   int64_t n = s->n;
@@ -1258,6 +1260,19 @@ int or_get(const or_scene *s, int field, double *out) {
     case 8:
       for (int64_t p = 0; p < n * OR_MAX_CUTS; ++p) out[p] = s->digit[p];
       return 0;
+    case 9:
+      for (int64_t p = 0; p < n; ++p)
+        for (int k = 0; k < OR_HIST; ++k) {
+          double *o = out + (p * OR_HIST + k) * 4;
+          if (k < s->hist_cnt[p]) {
+            o[0] = (double)s->hist[p * OR_HIST + k].partner;
+            memcpy(o + 1, s->hist[p * OR_HIST + k].u, sizeof(double) * 3);
+          } else {
+            o[0] = -1.0;
+            o[1] = o[2] = o[3] = 0.0;
+          }
+        }
+      return 0;
   }
   return -1;
 }
@@ -1273,8 +1288,28 @@ int or_set(or_scene *s, int field, const double *in) {
     case 8:
       for (int64_t p = 0; p < n * OR_MAX_CUTS; ++p) s->digit[p] = (unsigned char)in[p];
       return 0;
+    case 9:
+      for (int64_t p = 0; p < n; ++p) {
+        int c = 0;
+        for (int k = 0; k < OR_HIST; ++k) {
+          const double *e = in + (p * OR_HIST + k) * 4;
+          if (e[0] < 0) break;
+          s->hist[p * OR_HIST + c].partner = (int64_t)e[0];
+          memcpy(s->hist[p * OR_HIST + c].u, e + 1, sizeof(double) * 3);
+          ++c;
+        }
+        s->hist_cnt[p] = c;
+      }
+      return 0;
   }
   return -1;
+}
+
+/* substep counter and the cut in progress (to continue from a state that
+   was copied in from elsewhere) */
+void or_set_step(or_scene *s, int64_t step, int cur_cut) {
+  s->step = step;
+  s->cur_cut = cur_cut;
 }
 
 /* tool state: xB[3], R[9], vB[3], wB[3] */

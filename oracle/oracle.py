@@ -22,6 +22,7 @@ _lib = None
 
 MAX_CUTS = 32
 MAX_SEG = 16
+HIST = 16   # pair-contact history entries per particle
 
 E_INVERTED = 1
 E_NONFINITE = 2
@@ -82,6 +83,7 @@ def lib():
             L.or_get_tool.argtypes = [C.c_void_p, dp]
             L.or_set_tool.argtypes = [C.c_void_p, dp]
             L.or_get_frame.argtypes = [C.c_void_p, dp]
+            L.or_set_step.argtypes = [C.c_void_p, C.c_int64, C.c_int]
             L.or_step_count.argtypes = [C.c_void_p]
             L.or_step_count.restype = C.c_int64
             L.or_errors.argtypes = [C.c_void_p]
@@ -332,7 +334,8 @@ class OracleScene:
     """One FP64 scene built from a ``bm_inputs.Scene``."""
 
     FIELDS = {"X": (0, 3), "x": (1, 3), "v": (2, 3), "F": (3, 9), "D": (4, 1),
-              "ut": (5, 3), "code": (6, 1), "J": (7, 3), "digits": (8, MAX_CUTS)}
+              "ut": (5, 3), "code": (6, 1), "J": (7, 3), "digits": (8, MAX_CUTS),
+              "hist": (9, 4 * HIST)}
 
     def __init__(self, sc, single_field: bool = False, wrench_capacity: int = 0,
                  _handle=None):
@@ -394,6 +397,10 @@ class OracleScene:
         out = np.zeros(15)
         self._L.or_get_frame(self._h, _dp(out))
         return {"xe": out[0:3], "n": out[3:6], "e": out[6:9], "d": out[9:12], "ve": out[12:15]}
+
+    def set_step(self, step: int, current_cut: int) -> None:
+        """Substep counter and cut in progress, for continuing from a copied state."""
+        self._L.or_set_step(self._h, int(step), int(current_cut))
 
     @property
     def step_count(self) -> int:

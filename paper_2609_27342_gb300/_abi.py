@@ -29,6 +29,8 @@ MODEL_NEO_HOOKEAN, MODEL_FIXED_COROTATED = 0, 1
 
 FIELD_X, FIELD_x, FIELD_v, FIELD_F, FIELD_D = 1, 2, 4, 8, 16
 FIELD_UT, FIELD_CODE, FIELD_MASK1, FIELD_MASK2 = 32, 64, 128, 256
+FIELD_PAIR_PARTNER, FIELD_PAIR_U = 512, 1024
+PAIR_HIST = 16
 
 # name -> (bit, components, numpy dtype)
 FIELDS = {
@@ -36,6 +38,8 @@ FIELDS = {
     "F": (FIELD_F, 9, "float32"), "D": (FIELD_D, 1, "float32"), "ut": (FIELD_UT, 3, "float32"),
     "code": (FIELD_CODE, 1, "int64"), "mask1": (FIELD_MASK1, 1, "uint32"),
     "mask2": (FIELD_MASK2, 1, "uint32"),
+    "pair_partner": (FIELD_PAIR_PARTNER, PAIR_HIST, "int32"),
+    "pair_u": (FIELD_PAIR_U, 3 * PAIR_HIST, "float32"),
 }
 
 D3 = C.c_double * 3
@@ -71,7 +75,7 @@ class BladeDesc(C.Structure):
 class SceneInfo(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("n_nodes", C.c_int64), ("n_slots", C.c_int64),
                 ("slot_capacity", C.c_int64), ("step", C.c_int64), ("error_bits", C.c_uint32),
-                ("grid_lo", C.c_int * 3), ("grid_dim", C.c_int * 3)]
+                ("grid_lo", C.c_int * 3), ("grid_dim", C.c_int * 3), ("current_cut", C.c_int32)]
 
 
 class BatchDesc(C.Structure):

@@ -2118,7 +2118,7 @@ __global__ void k_slot_fill(World w, LaunchSet ls, int force) {
 // --------------------------------------------------------------------------
 // state I/O between pool order and the caller's order
 // --------------------------------------------------------------------------
-__global__ void k_io(World w, int p_begin, int n, int field, void *buf, int to_pool) {
+__global__ void k_io(World w, int scene_slot, int p_begin, int n, int field, void *buf, int to_pool) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int p = p_begin + i;
@@ -2165,6 +2165,23 @@ __global__ void k_io(World w, int p_begin, int n, int field, void *buf, int to_p
       if (to_pool) P.s2[p] = ub[o];
       else ub[o] = P.s2[p];
       break;
+    case 9:    // pair history partners (read only): caller indices, -1 ends the list
+    case 10: {  // pair history spring displacements (read only)
+      if (to_pool || !P.hist_partner[0]) break;
+      const int rb = (int)(w.scenes[scene_slot].step & 1);  // the buffer the next substep reads
+      bool live = true;
+      for (int h = 0; h < BM_HIST; ++h) {
+        const int pt = live ? P.hist_partner[rb][(size_t)p * BM_HIST + h] : -1;
+        live = pt >= 0;
+        if (field == 9) {
+          ((int *)buf)[(size_t)o * BM_HIST + h] = live ? P.perm[pt] : -1;
+        } else {
+          const float *u = P.hist_u[rb] + ((size_t)p * BM_HIST + h) * 3;
+          for (int a = 0; a < 3; ++a) fb[((size_t)o * BM_HIST + h) * 3 + a] = live ? u[a] : 0.0f;
+        }
+      }
+      break;
+    }
   }
 }
 
@@ -2342,9 +2359,8 @@ cudaError_t bm_launch_substep(const World &w, const LaunchSet &ls, cudaStream_t 
 
 cudaError_t bm_launch_io(const World &w, int scene_slot, int p_begin, int n, int field, void *buf,
                          int to_pool, cudaStream_t st) {
-  (void)scene_slot;
   if (n == 0) return cudaSuccess;
-  k_io<<<(n + 255) / 256, 256, 0, st>>>(w, p_begin, n, field, buf, to_pool);
+  k_io<<<(n + 255) / 256, 256, 0, st>>>(w, scene_slot, p_begin, n, field, buf, to_pool);
   return cudaGetLastError();
 }
 

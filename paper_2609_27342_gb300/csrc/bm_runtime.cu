@@ -131,6 +131,7 @@ struct WorldH {
   Allocator al;
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  int device = -1;          // device current when the world was created (its memory and stream live there)
   int64_t cap_p = 0, cap_cell = 0, cap_node = 0, cap_slot = 0, cap_hist = 0, cap_brick = 0, cap_ppool = 0;
   int cap_scenes = 0, cap_ntile = 0;
   bool pair = false;
@@ -598,6 +599,10 @@ WorldH *new_world(const bm_alloc *alloc, cudaStream_t st) {
   }
   W->al.st = st;
   W->st = st;
+  if (cudaGetDevice(&W->device) != cudaSuccess) {
+    cudaGetLastError();
+    W->device = -1;
+  }
   return W;
 }
 
@@ -801,7 +806,7 @@ bool valid_scene(bm_scene_t s) { return s && s->world; }
 // so its device address is looked up once per device with
 // cudaGetSymbolAddress() (with that device current) and passed to the kernel.
 // ============================================================================
-#define BM_NOALLOC_STAGE_BYTES (16u << 20)  // 16 MiB per requested field
+#define BM_NOALLOC_STAGE_BYTES (16u << 20)  // one 16 MiB array, reused field by field
 
 static __device__ __align__(256) unsigned char bm_noalloc_stage[BM_NOALLOC_STAGE_BYTES];
 
@@ -810,10 +815,9 @@ namespace {
 std::mutex g_stage_mu;
 std::vector<void *> g_stage_ptr;  // device ordinal -> device address of the array
 
-// set-up, once per device: resolve the array's device address
-int stage_address(void **out) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+// set-up, once per device: resolve the array's device address.  `dev` must
+// be the current device (the address is that device's copy of the array).
+int stage_address(int dev, void **out) {
   std::lock_guard<std::mutex> lk(g_stage_mu);
   if ((int)g_stage_ptr.size() <= dev) g_stage_ptr.resize((size_t)dev + 1, nullptr);
   if (!g_stage_ptr[dev]) {
@@ -999,7 +1003,10 @@ int bm_read_state(bm_scene_t s, uint32_t field_mask, void *const *dst, int dst_o
     if (!(field_mask & (1u << f))) continue;
     void *d = dst[j++];
     if (!d) return fail(BM_E_INVALID, "null destination pointer");
-    size_t w = (f == 3) ? 9 : (f == 1 || f == 2 || f == 5 || f == 0) ? 3 : 1;
+    if ((f == 9 || f == 10) && !s->desc.pair_contact)
+      return fail(BM_E_INVALID, "pair-contact history: the scene has no material-material contact");
+    size_t w = (f == 3) ? 9 : (f == 1 || f == 2 || f == 5 || f == 0) ? 3 : (f == 9) ? BM_HIST
+             : (f == 10) ? 3 * BM_HIST : 1;
     size_t es = (f == 6) ? 8 : 4;
     size_t bytes = (size_t)n * w * es;
     if (f == 0) {
@@ -1024,7 +1031,8 @@ int bm_read_state(bm_scene_t s, uint32_t field_mask, void *const *dst, int dst_o
 
 int bm_write_state(bm_scene_t s, uint32_t field_mask, const void *const *src, int src_on_device) {
   if (!valid_scene(s) || !src) return fail(BM_E_INVALID, "bad scene or source");
-  if (field_mask & (BM_FIELD_X | BM_FIELD_CODE)) return fail(BM_E_INVALID, "X and CODE are read-only");
+  if (field_mask & (BM_FIELD_X | BM_FIELD_CODE | BM_FIELD_PAIR_PARTNER | BM_FIELD_PAIR_U))
+    return fail(BM_E_INVALID, "X, CODE and the pair-contact history are read-only");
   WorldH *W = s->world;
   CK(cudaStreamSynchronize(W->st));
   const int64_t n = s->n;
@@ -1301,6 +1309,8 @@ int bm_read_state_noalloc(bm_scene_t s, uint32_t field_mask, void *const *dst) {
   if (!valid_scene(s) || !dst) return fail(BM_E_INVALID, "bad scene or destination");
   WorldH *W = s->world;
   const int64_t n = s->n;
+  if (field_mask & (BM_FIELD_PAIR_PARTNER | BM_FIELD_PAIR_U))
+    return fail(BM_E_INVALID, "bm_read_state_noalloc: the pair-contact history is read by bm_read_state");
   // size check first: nothing is launched for a request the array cannot hold
   for (int f = 0; f < BM_NUM_FIELDS; ++f) {
     if (!(field_mask & (1u << f)) || f == 0) continue;
@@ -1310,10 +1320,18 @@ int bm_read_state_noalloc(bm_scene_t s, uint32_t field_mask, void *const *dst) {
       return fail(BM_E_INVALID, "bm_read_state_noalloc: field " + std::to_string(f) + " of " +
                                     std::to_string(n) + " particles needs " + std::to_string(bytes) +
                                     " bytes; the staging array holds " +
-                                    std::to_string((size_t)BM_NOALLOC_STAGE_BYTES) + " bytes per field");
+                                    std::to_string((size_t)BM_NOALLOC_STAGE_BYTES) +
+                                    " bytes (one array, reused by each field in turn)");
   }
+  // the array's address is per device: the scene's device must be current,
+  // or the lookup would name another GPU's copy of the array
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (W->device >= 0 && dev != W->device)
+    return fail(BM_E_INVALID, "bm_read_state_noalloc: the scene lives on device " + std::to_string(W->device) +
+                                  " but device " + std::to_string(dev) + " is current");
   void *stage = nullptr;
-  int rc = stage_address(&stage);
+  int rc = stage_address(dev, &stage);
   if (rc) return rc;
   int j = 0;
   for (int f = 0; f < BM_NUM_FIELDS; ++f) {
@@ -1346,6 +1364,7 @@ int bm_scene_info_get(bm_scene_t s, bm_scene_info *out) {
   out->slot_capacity = s->slot_cap;
   out->step = cur.step;
   out->error_bits = cur.err;
+  out->current_cut = cur.cur_cut;
   for (int a = 0; a < 3; ++a) {
     out->grid_lo[a] = s->lo[a];
     out->grid_dim[a] = s->nn[a];

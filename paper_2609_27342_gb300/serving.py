@@ -58,7 +58,8 @@ class Server:
     from bm_scene_footprint); the batch pools are sized from it once.
     ``max_chunk`` bounds the substeps run between admission points;
     ``node_tile`` and ``brick_variant`` are the launch shape (for instance an
-    autotuned one; results do not depend on it).
+    autotuned one; results do not depend on it).  ``allocator`` (a
+    ``TorchAllocator``) makes PyTorch's caching allocator own the batch pools.
     """
 
     # pool capacity per budget byte (particles, nodes): a scene's footprint is
@@ -67,7 +68,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, max_scenes: int = 256, max_chunk: int = 16,
                  stream=None, max_particles: Optional[int] = None, node_tile: int = 128,
-                 brick_variant: int = 0):
+                 brick_variant: int = 0, allocator=None):
         import torch
         self._torch = torch
         self.budget = int(budget_bytes)
@@ -75,7 +76,7 @@ class Server:
         cap_n = cap_p // 2 + 27 * max_scenes
         self.stream = stream or torch.cuda.Stream()
         self.batch = Batch(max_particles=cap_p, max_nodes=cap_n, max_scenes=max_scenes,
-                           graph_chunk=max_chunk, stream=self.stream)
+                           graph_chunk=max_chunk, stream=self.stream, allocator=allocator)
         self.batch.set_tiles(max_chunk, node_tile, brick_variant)
         self.max_chunk = max_chunk
         self.queue: List[tuple] = []

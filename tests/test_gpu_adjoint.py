@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import bm_inputs as bi
+from conftest import record
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -87,6 +88,51 @@ def test_adjoint_matches_oracle_adjoint(pkg):
     assert abs(g["v_seg"][0, 2] - ref["dv_seg"][0, 2]) <= 5e-4 * abs(ref["dv_seg"][0, 2])
 
 
+def test_adjoint_full_size_matches_oracle_adjoint_and_differences(pkg):
+    """The calibration workload itself (32,000 particles, 200 substeps,
+    checkpoint every 20; target at E = 1.5e5 Pa): float32 GPU adjoint vs the
+    FP64 oracle adjoint, the error stated per result; and the oracle adjoint
+    vs central differences of the FP64 forward at relative step 1e-7.
+
+    The force trajectory has jumps (a cutting-progress release or a label
+    moving by one substep when a parameter moves), so differences at a large
+    step mix the smooth derivative with the density of those events; at a
+    step of 1e-7 no event moves (an event inside the bracket would show as
+    a difference many orders of magnitude off) and the differences measure
+    the derivative with the decisions held, which is what the adjoint
+    computes."""
+    from paper_2609_27342_gb300.calibration import force_loss_and_grad
+    n, every = 200, 20
+    target = O.forces(bi.calibration_scene(E=1.5e5), n)
+    sc = bi.calibration_scene()
+    ref = O.gradient(sc, target, n, every=every)
+    loss, g = force_loss_and_grad(sc, target, n, every=every)
+    err = {"loss": abs(loss - ref["loss"]) / ref["loss"],
+           "E": abs(g["E"] - ref["dE"]) / abs(ref["dE"]),
+           "nu": abs(g["nu"] - ref["dnu"]) / abs(ref["dnu"]),
+           "speed": abs(g["v_seg"][0, 2] - ref["dv_seg"][0, 2]) / abs(ref["dv_seg"][0, 2])}
+
+    def L(**kw):
+        return O.force_loss(O.forces(bi.calibration_scene(**kw), n), target)
+
+    h = 1e-7
+    jobs = {"E": ({"E": 1e5 * (1 + h)}, {"E": 1e5 * (1 - h)}, 2 * h * 1e5),
+            "nu": ({"nu": 0.3 * (1 + h)}, {"nu": 0.3 * (1 - h)}, 2 * h * 0.3),
+            "speed": ({"speed": 0.2 * (1 + h)}, {"speed": 0.2 * (1 - h)}, 2 * h * 0.2)}
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(6) as ex:
+        fut = {k: (ex.submit(L, **a), ex.submit(L, **b), d) for k, (a, b, d) in jobs.items()}
+        fd = {k: (p.result() - m.result()) / d for k, (p, m, d) in fut.items()}
+    # d/d(speed) of a downward segment velocity v_z = -speed is -dL/dv_z
+    ad_o = {"E": ref["dE"], "nu": ref["dnu"], "speed": -ref["dv_seg"][0, 2]}
+    fd_err = {k: abs(ad_o[k] - fd[k]) / abs(fd[k]) for k in fd}
+    record("adjoint_full_size", **{"gpu_vs_oracle_" + k: v for k, v in err.items()},
+           **{"oracle_vs_fd_" + k: v for k, v in fd_err.items()})
+    assert err["loss"] <= 1e-3, err
+    assert err["E"] <= 1e-3 and err["nu"] <= 1e-3 and err["speed"] <= 1e-3, err
+    assert all(v <= 1e-4 for v in fd_err.values()), fd_err
+
+
 def test_adjoint_autograd_matches_central_differences(pkg):
     """The autograd.Function on the calibration workload (32,000 particles,
     200 substeps, checkpoint every 20; target at E = 1.5e5 Pa) against
@@ -111,10 +157,15 @@ def test_adjoint_autograd_matches_central_differences(pkg):
           "nu": (L(nu=0.3 * 1.001) - L(nu=0.3 * 0.999)) / (2e-3 * 0.3),
           "speed": (L(speed=0.2 * 1.001) - L(speed=0.2 * 0.999)) / (2e-3 * 0.2)}
     ad = {"E": E.grad.item(), "nu": nu.grad.item(), "speed": -v.grad[0, 2].item()}
-    # the loss jumps where a D release or a label moves by a substep, so the
-    # differences carry noise of their own: for nu, steps of 1e-3 and 1e-2
-    # differ by 3.7% and bracket the adjoint (measured: E 5e-5, nu 2%,
-    # speed 0.2% from the 1e-3 differences)
-    tol = {"E": 1e-3, "nu": 0.05, "speed": 1e-2}
+    rel = {k: abs(ad[k] - fd[k]) / abs(fd[k]) for k in fd}
+    record("adjoint_autograd_fd_1e-3", **rel)
+    # E and the blade speed: the float32 differences at relative step 1e-3
+    # agree with the adjoint.  For nu a step of 1e-3 moves cutting-progress
+    # releases and labels by a substep (the loss jumps there), so those
+    # differences include the event density that the adjoint -- the
+    # derivative with the decisions held -- leaves out by construction; nu is
+    # checked against the FP64 adjoint and FP64 differences at a step that
+    # moves no event (test above) and only loosely here.
+    tol = {"E": 1e-3, "nu": 0.1, "speed": 1e-2}
     for k in fd:
-        assert abs(ad[k] - fd[k]) <= tol[k] * abs(fd[k]), (k, ad[k], fd[k])
+        assert rel[k] <= tol[k], (k, ad[k], fd[k])
