@@ -50,8 +50,11 @@ FALLBACK_HBM_GBS = 6800.0
 # and writes of each kernel's own inputs and outputs, with brick-tile
 # partials counted at 3.375 tiles per slot (6^3 tile nodes per 4^3 cells).
 KERNEL_MODEL = {
-    "k_pre": {"bytes": (149, 0, 0, 0), "flops": (420, 0, 0, 0)},
-    "k_p2g_brick": {"bytes": (84, 0, 108, 2000), "flops": (1050, 0, 0, 0)},
+    # contact, labels and stress are computed in the P2G brick kernel's
+    # staging phase: it reads x, v, F, D, u_t, masks, the fractional offset
+    # and the base cell (100 B) and writes the pending label (D and u_t only
+    # where they change)
+    "k_p2g_brick": {"bytes": (101, 0, 108, 2000), "flops": (1470, 0, 0, 0)},
     "k_p2g_node": {"bytes": (0, 12, 140, 0), "flops": (0, 0, 40, 0)},
     "k_g2p_musl": {"bytes": (72, 0, 162, 1080), "flops": (570, 0, 0, 0)},
     "k_musl_node": {"bytes": (0, 12, 86, 0), "flops": (0, 0, 20, 0)},
@@ -59,7 +62,7 @@ KERNEL_MODEL = {
 }
 STEP_ALGORITHMIC_BYTES = 156  # per particle-substep: the state the method must move
 LATE_FIRST = 900              # first substep of the late timing window (of the 1,000-substep rollout)
-LAUNCHES_PER_SUBSTEP = 11     # kernels one batched substep launches (no pair contact)
+LAUNCHES_PER_SUBSTEP = 10     # kernels one batched substep launches (no pair contact)
 
 
 def log(*a):

@@ -500,11 +500,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sm, int &total) {
 // on distinct banks.
 __device__ __forceinline__ int pic(int j, int c) { return j * BR3 + (c ^ ((j & 7) << 2)); }
 
-// Staged per-(cell, z-offset) sums: one row per value, one column per thread,
-// each 32 columns followed by one pad word, so that sources 32 apart (cells
-// two z-layers apart) and rows fall on different banks in the tile gather.
-#define STG (BT + BT / 32)
-__device__ __forceinline__ int stg(int src) { return src + (src >> 5); }
 #define BT 192  // threads per brick CTA: 64 cells x 3 z-offsets
 
 __device__ __forceinline__ void node_coords(const DevScene &sc, int li, int &ix, int &iy, int &iz) {
@@ -618,161 +613,145 @@ __device__ __forceinline__ int tile_slot(const World &w, const Tile &T, const ui
 }
 
 // --------------------------------------------------------------------------
-// k_pre, one thread per particle (CTA per brick): tool and floor contact
-// (Eq. 14-15 with friction Eq. 12), cutting progress D and release (Eq. 5),
-// reaction wrench (Eq. 16), side label for the next substep (Eq. 3, 4, 6),
-// and A = -dt V0 P(F) / dx with the total impulse J for P2G.
+// Per-particle work ahead of P2G (one thread per particle, inside the P2G
+// brick kernel): tool and floor contact (Eq. 14-15 with friction Eq. 12),
+// cutting progress D and release (Eq. 5), reaction wrench (Eq. 16), side
+// label for the next substep (Eq. 3, 4, 6), and the P2G inputs
+// A = -dt V0 P(F) / dx and the particle's total impulse J.
 // --------------------------------------------------------------------------
 // INELASTIC: the launch set holds a scene with plasticity or viscosity (the
 // elastic instantiation carries no trace of those paths)
 template <bool INELASTIC>
-__global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
-  __shared__ float red[6][4];
-  const int4 bt = ls.btiles[blockIdx.x];
-  DevScene &scm = w.scenes[bt.x];
-  const DevScene &sc = scm;
-  const PPool &P = w.P;
-  const int tid = threadIdx.x;
-  float wr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  bool clamped = false, anyc = false;
+__device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P, int p, const float x[3],
+                                             const float v[3], uint32_t s1, uint32_t s2, float A[9], float J[3],
+                                             float wr[6], bool &clamped, bool &anyc) {
   const float dt = sc.dt, mp = sc.mp;
   const int cut = sc.cut;
-  for (int i = tid; i < bt.w; i += blockDim.x) {
-    const int p = bt.z + i;
-    float x[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
-    float v[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
-    const uint32_t s1 = P.s1[p], s2 = P.s2[p];
-    float J[3] = {0.f, 0.f, 0.f};
-    const float D0 = P.D[p];
-    float D = sc.reset_D ? 0.0f : D0;
-    const float u00 = P.ut[0][p], u01 = P.ut[1][p], u02 = P.ut[2][p];
-    float uh[3] = {u00, u01, u02};
-    if (sc.has_blade && sc.tool_contact_on) {
-      float xc[3], nB[3], phi;
-      box_closest(sc, x, sc.Rp, xc, nB, phi);
-      float rc[3] = {xc[0] - sc.fxB[0], xc[1] - sc.fxB[1], xc[2] - sc.fxB[2]};
-      float wr3[3] = {sc.fwB[1] * rc[2] - sc.fwB[2] * rc[1], sc.fwB[2] * rc[0] - sc.fwB[0] * rc[2],
-                      sc.fwB[0] * rc[1] - sc.fwB[1] * rc[0]};
-      float vrel[3] = {v[0] - (sc.fvB[0] + wr3[0]), v[1] - (sc.fvB[1] + wr3[1]),
-                       v[2] - (sc.fvB[2] + wr3[2])};
-      float vn = vrel[0] * nB[0] + vrel[1] * nB[1] + vrel[2] * nB[2];
-      float phihat = phi + dt * fminf(vn, 0.0f);
-      float wB = 0.0f;
-      if (sc.finv_mass > 0.0f) {
-        float rn[3] = {rc[1] * nB[2] - rc[2] * nB[1], rc[2] * nB[0] - rc[0] * nB[2],
-                       rc[0] * nB[1] - rc[1] * nB[0]};
-        float q0 = sc.fIinv[0] * rn[0] + sc.fIinv[1] * rn[1] + sc.fIinv[2] * rn[2];
-        float q1 = sc.fIinv[3] * rn[0] + sc.fIinv[4] * rn[1] + sc.fIinv[5] * rn[2];
-        float q2 = sc.fIinv[6] * rn[0] + sc.fIinv[7] * rn[1] + sc.fIinv[8] * rn[2];
-        wB = sc.finv_mass + rn[0] * q0 + rn[1] * q1 + rn[2] * q2;
+  J[0] = J[1] = J[2] = 0.f;
+  const float D0 = P.D[p];
+  float D = sc.reset_D ? 0.0f : D0;
+  const float u00 = P.ut[0][p], u01 = P.ut[1][p], u02 = P.ut[2][p];
+  float uh[3] = {u00, u01, u02};
+  if (sc.has_blade && sc.tool_contact_on) {
+    float xc[3], nB[3], phi;
+    box_closest(sc, x, sc.Rp, xc, nB, phi);
+    float rc[3] = {xc[0] - sc.fxB[0], xc[1] - sc.fxB[1], xc[2] - sc.fxB[2]};
+    float wr3[3] = {sc.fwB[1] * rc[2] - sc.fwB[2] * rc[1], sc.fwB[2] * rc[0] - sc.fwB[0] * rc[2],
+                    sc.fwB[0] * rc[1] - sc.fwB[1] * rc[0]};
+    float vrel[3] = {v[0] - (sc.fvB[0] + wr3[0]), v[1] - (sc.fvB[1] + wr3[1]), v[2] - (sc.fvB[2] + wr3[2])};
+    float vn = vrel[0] * nB[0] + vrel[1] * nB[1] + vrel[2] * nB[2];
+    float phihat = phi + dt * fminf(vn, 0.0f);
+    float wB = 0.0f;
+    if (sc.finv_mass > 0.0f) {
+      float rn[3] = {rc[1] * nB[2] - rc[2] * nB[1], rc[2] * nB[0] - rc[0] * nB[2], rc[0] * nB[1] - rc[1] * nB[0]};
+      float q0 = sc.fIinv[0] * rn[0] + sc.fIinv[1] * rn[1] + sc.fIinv[2] * rn[2];
+      float q1 = sc.fIinv[3] * rn[0] + sc.fIinv[4] * rn[1] + sc.fIinv[5] * rn[2];
+      float q2 = sc.fIinv[6] * rn[0] + sc.fIinv[7] * rn[1] + sc.fIinv[8] * rn[2];
+      wB = sc.finv_mass + rn[0] * q0 + rn[1] * q1 + rn[2] * q2;
+    }
+    float meff = 1.0f / (1.0f / mp + wB);
+    float Jn = sc.s_n * meff / dt * fmaxf(-phihat, 0.0f);
+    float JB[3] = {0.f, 0.f, 0.f};
+    if (Jn > 0.0f) {
+      float ft[3], un[3];
+      friction(uh, nB, vrel, Jn / dt, meff, dt, sc.gamma_k, sc.gamma_c, sc.fmu_s, sc.fmu_d, ft, un);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        JB[a] = Jn * nB[a] + dt * ft[a];
+        uh[a] = un[a];
       }
-      float meff = 1.0f / (1.0f / mp + wB);
-      float Jn = sc.s_n * meff / dt * fmaxf(-phihat, 0.0f);
-      float JB[3] = {0.f, 0.f, 0.f};
-      if (Jn > 0.0f) {
-        float ft[3], un[3];
-        friction(uh, nB, vrel, Jn / dt, meff, dt, sc.gamma_k, sc.gamma_c, sc.fmu_s, sc.fmu_d, ft, un);
+      if (cut >= 0) {  // Eq. 5: front band, advancing cut
+        float r[3] = {x[0] - sc.fxe[0], x[1] - sc.fxe[1], x[2] - sc.fxe[2]};
+        float sp = r[0] * sc.fn[0] + r[1] * sc.fn[1] + r[2] * sc.fn[2];
+        float lp = r[0] * sc.fe[0] + r[1] * sc.fe[1] + r[2] * sc.fe[2];
+        float fp = r[0] * sc.fd[0] + r[1] * sc.fd[1] + r[2] * sc.fd[2];
+        float uc = (sc.fve[0] - v[0]) * sc.fd[0] + (sc.fve[1] - v[1]) * sc.fd[1] + (sc.fve[2] - v[2]) * sc.fd[2];
+        bool front = fabsf(sp) <= sc.h && fabsf(lp) <= sc.fL && fp >= 0.0f && fp <= sc.b_lead && uc > sc.u_min;
+        if (front) {
+          float Jc = fmaxf(JB[0] * sc.fd[0] + JB[1] * sc.fd[1] + JB[2] * sc.fd[2], 0.0f);
+          if (D < 1.0f) {
+            D = fminf(D + Jc * uc / sc.Wth, 1.0f);
+          } else {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          JB[a] = Jn * nB[a] + dt * ft[a];
-          uh[a] = un[a];
-        }
-        if (cut >= 0) {  // Eq. 5: front band, advancing cut
-          float r[3] = {x[0] - sc.fxe[0], x[1] - sc.fxe[1], x[2] - sc.fxe[2]};
-          float sp = r[0] * sc.fn[0] + r[1] * sc.fn[1] + r[2] * sc.fn[2];
-          float lp = r[0] * sc.fe[0] + r[1] * sc.fe[1] + r[2] * sc.fe[2];
-          float fp = r[0] * sc.fd[0] + r[1] * sc.fd[1] + r[2] * sc.fd[2];
-          float uc = (sc.fve[0] - v[0]) * sc.fd[0] + (sc.fve[1] - v[1]) * sc.fd[1] +
-                     (sc.fve[2] - v[2]) * sc.fd[2];
-          bool front = fabsf(sp) <= sc.h && fabsf(lp) <= sc.fL && fp >= 0.0f && fp <= sc.b_lead &&
-                       uc > sc.u_min;
-          if (front) {
-            float Jc = fmaxf(JB[0] * sc.fd[0] + JB[1] * sc.fd[1] + JB[2] * sc.fd[2], 0.0f);
-            if (D < 1.0f) {
-              D = fminf(D + Jc * uc / sc.Wth, 1.0f);
-            } else {
-#pragma unroll
-              for (int a = 0; a < 3; ++a) JB[a] -= Jc * sc.fd[a];
-            }
+            for (int a = 0; a < 3; ++a) JB[a] -= Jc * sc.fd[a];
           }
         }
-      } else {
-        uh[0] = uh[1] = uh[2] = 0.0f;
       }
-      const float idt = 1.0f / dt;
-      const float FB[3] = {-JB[0] * idt, -JB[1] * idt, -JB[2] * idt};
-      anyc |= Jn > 0.0f;
-      wr[0] += FB[0];
-      wr[1] += FB[1];
-      wr[2] += FB[2];
-      wr[3] += rc[1] * FB[2] - rc[2] * FB[1];
-      wr[4] += rc[2] * FB[0] - rc[0] * FB[2];
-      wr[5] += rc[0] * FB[1] - rc[1] * FB[0];
-      J[0] += JB[0];
-      J[1] += JB[1];
-      J[2] += JB[2];
+    } else {
+      uh[0] = uh[1] = uh[2] = 0.0f;
     }
-    if (sc.floor_on) {
-      const float phi = x[2] - sc.floor_z - sc.Rp;
-      const float phihat = phi + dt * fminf(v[2], 0.0f);
-      J[2] += sc.s_n * mp / dt * fmaxf(-phihat, 0.0f);
-    }
-    if (sc.pair_on) {
-      J[0] += P.J[0][p];
-      J[1] += P.J[1][p];
-      J[2] += P.J[2][p];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) J[a] += mp * sc.g[a] * dt;
-    uint8_t pend = 0;
-    if (cut >= 0 && ((s1 | s2) & (1u << cut)) == 0u) pend = (uint8_t)side_label(sc, x, v);
-    float F[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
-    float Pk[9];
-    if (INELASTIC && (sc.yield_stress > 0.0f || sc.viscosity > 0.0f))
-      clamped |= inelastic_stress(sc, P, p, F, Pk);
-    else
-      clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk)
-                                                      : piola(F, sc.mu, sc.lam, Pk);
-    const float cA = -dt * sc.V0 * sc.inv_dx;  // grad N is applied per axis in units of 1/dx
-#pragma unroll
-    for (int k = 0; k < 9; ++k) P.A[k][p] = cA * Pk[k];
-    P.J[0][p] = J[0];
-    P.J[1][p] = J[1];
-    P.J[2][p] = J[2];
-    // cutting progress and friction history are written back only when they
-    // change (most particles touch no tool in a substep)
-    if (!(D == D0)) P.D[p] = D;
-    if (!(uh[0] == u00 && uh[1] == u01 && uh[2] == u02)) {
-      P.ut[0][p] = uh[0];
-      P.ut[1][p] = uh[1];
-      P.ut[2][p] = uh[2];
-    }
-    P.pend[p] = pend;
+    const float idt = 1.0f / dt;
+    const float FB[3] = {-JB[0] * idt, -JB[1] * idt, -JB[2] * idt};
+    anyc |= Jn > 0.0f;
+    wr[0] += FB[0];
+    wr[1] += FB[1];
+    wr[2] += FB[2];
+    wr[3] += rc[1] * FB[2] - rc[2] * FB[1];
+    wr[4] += rc[2] * FB[0] - rc[0] * FB[2];
+    wr[5] += rc[0] * FB[1] - rc[1] * FB[0];
+    J[0] += JB[0];
+    J[1] += JB[1];
+    J[2] += JB[2];
   }
-  if (clamped) atomicOr(&scm.err, BM_ERRBIT_INVERTED);
-  if (sc.has_blade) {
-    // per-brick wrench partial: float32 sums inside the brick (fixed shuffle
-    // tree, warps in order); bricks without tool contact write zeros
-    if (__syncthreads_or(anyc)) {
-      const int lane = tid & 31, wid = tid >> 5;
+  if (sc.floor_on) {
+    const float phi = x[2] - sc.floor_z - sc.Rp;
+    const float phihat = phi + dt * fminf(v[2], 0.0f);
+    J[2] += sc.s_n * mp / dt * fmaxf(-phihat, 0.0f);
+  }
+  if (sc.pair_on) {
+    J[0] += P.J[0][p];
+    J[1] += P.J[1][p];
+    J[2] += P.J[2][p];
+  }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        float v = wr[k];
+  for (int a = 0; a < 3; ++a) J[a] += mp * sc.g[a] * dt;
+  uint8_t pend = 0;
+  if (cut >= 0 && ((s1 | s2) & (1u << cut)) == 0u) pend = (uint8_t)side_label(sc, x, v);
+  float F[9];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-        if (lane == 0) red[k][wid] = v;
-      }
-      __syncthreads();
-      if (tid < 6) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += (double)red[tid][q];
-        w.wpart[(size_t)bt.y * 6 + tid] = s;
-      }
-    } else if (tid < 6) {
-      w.wpart[(size_t)bt.y * 6 + tid] = 0.0;
+  for (int k = 0; k < 9; ++k) F[k] = P.F[k][p];
+  float Pk[9];
+  if (INELASTIC && (sc.yield_stress > 0.0f || sc.viscosity > 0.0f))
+    clamped |= inelastic_stress(sc, P, p, F, Pk);
+  else
+    clamped |= sc.model == BM_MODEL_FIXED_COROTATED ? piola_fcr(F, sc.mu, sc.lam, Pk) : piola(F, sc.mu, sc.lam, Pk);
+  const float cA = -dt * sc.V0 * sc.inv_dx;  // grad N is applied per axis in units of 1/dx
+#pragma unroll
+  for (int k = 0; k < 9; ++k) A[k] = cA * Pk[k];
+  // cutting progress and friction history are written back only when they
+  // change (most particles touch no tool in a substep)
+  if (!(D == D0)) P.D[p] = D;
+  if (!(uh[0] == u00 && uh[1] == u01 && uh[2] == u02)) {
+    P.ut[0][p] = uh[0];
+    P.ut[1][p] = uh[1];
+    P.ut[2][p] = uh[2];
+  }
+  P.pend[p] = pend;
+}
+
+// Per-brick wrench partial of this substep: float32 sums inside the brick
+// (fixed shuffle tree, warps in order), one double per component; bricks
+// without tool contact write zeros.  All threads of the CTA call it.
+__device__ __forceinline__ void brick_wrench(const World &w, int brick, const float wr[6], bool anyc,
+                                             float (*red)[BT / 32]) {
+  const int tid = threadIdx.x;
+  if (__syncthreads_or(anyc)) {
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float v = wr[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+      if (lane == 0) red[k][wid] = v;
     }
+    __syncthreads();
+    if (tid < 6) {
+      double s = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += (double)red[tid][q];
+      w.wpart[(size_t)brick * 6 + tid] = s;
+    }
+  } else if (tid < 6) {
+    w.wpart[(size_t)brick * 6 + tid] = 0.0;
   }
 }
 
@@ -780,113 +759,180 @@ __global__ void __launch_bounds__(128, 10) k_pre(World w, LaunchSet ls) {
 // k_p2g_brick: the brick's share of P2G (Eq. 2) into its node tile, per
 // logical grid, from the particles' A, J, v staged in shared memory.
 // --------------------------------------------------------------------------
-// Sums of the staged (cell, z-offset) values of tile node t for each of its
-// logical grids (pass `it` over the cells' codes), handed to put(slot
-// entry, sums).  Sources are visited in ascending offset order, so every sum
-// is taken in the same order wherever it is computed.  With `uniform` (one
-// code in the whole brick, one logical grid at every tile node) no source
-// needs a code test: cells without particles staged zeros.
-template <int PPC, int NV, class Put>
-__device__ __forceinline__ void gather_tile_node(const World &w, const Tile &T, const float (*stage)[STG],
-                                                 const uint8_t *ncode, const uint8_t (*ccode)[PPC],
-                                                 const uint32_t *ps1, const uint32_t *ps2, int it,
-                                                 int t, bool uniform, int pbase, Put put) {
-  const int n = T.cnt[t];
-  // a node with one logical grid sees one code in every source cell (each
-  // particle of a source cell touches it), so passes after the first add nothing
-  if (n == 0 || (it > 0 && n == 1)) return;
-  const int tx = t % TE, ty = (t / TE) % TE, tz = t / (TE * TE);
-  const size_t e0 = (size_t)pbase + T.lo[t];
-  const int x0 = max(0, tx - (BR - 1)), x1 = min(2, tx), y0 = max(0, ty - (BR - 1)), y1 = min(2, ty);
-  const int z0 = max(0, tz - (BR - 1)), z1 = min(2, tz);
-  if (uniform) {
-    float acc[NV];
+// Reduction of per-(cell, z-offset) sums to per-node sums inside a warp.
+// Cells are x-fastest in a brick and a warp holds 32 consecutive cells of one
+// z-offset, so the 4 cells of an x-row are adjacent lanes and the 4 rows of a
+// z-layer are 4 lanes apart.  On entry a[i][j][k] is value k of the thread's
+// own cell for node (cx + j, cy + i, cz + oz).  The x pass adds, for node
+// cx, the contributions of cells cx - 1 and cx - 2 (shuffles); the lane at
+// the row's end also keeps the row's sums for the two node columns beyond it
+// (nodes 4 and 5 of the tile's 6).  The y pass does the same along y.  On
+// exit lane (cx, cy) holds, for its z-layer, the sums over the layer's cells
+// of nodes (tx, ty) = (cx + j, cy + i), with j > 0 only at cx = 3 and i > 0
+// only at cy = 3 (zeros elsewhere).  Each sum is taken in a fixed order (own
+// cell, then the one before, then the one before that).
+template <int NV>
+__device__ __forceinline__ void xy_reduce(float (&a)[3][3][NV], int cx, int cy) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.f;
-    for (int ozz = z0; ozz <= z1; ++ozz)
-      for (int oyy = y0; oyy <= y1; ++oyy)
-        for (int oxx = x0; oxx <= x1; ++oxx) {
-          const int src = ozz * BR3 + ((tz - ozz) * BR + (ty - oyy)) * BR + (tx - oxx);
-          const int q = (oyy * 3 + oxx) * NV;
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][stg(src)];
-        }
-    put(e0, acc);
-    return;
-  }
-  for (int sl = 0; sl < n; ++sl) {
-    const uint2 code = n > 1 ? w.S.code[T.goff[t] + sl] : make_uint2(0u, 0u);
-    float acc[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.f;
-    // offsets o with 0 <= t - o < 4 on every axis, in ascending order
-    for (int ozz = z0; ozz <= z1; ++ozz) {
-      const int zz = tz - ozz;
-      for (int oyy = y0; oyy <= y1; ++oyy) {
-        const int yy = ty - oyy;
-        for (int oxx = x0; oxx <= x1; ++oxx) {
-          const int xx = tx - oxx;
-          const int cc = (zz * BR + yy) * BR + xx;
-          if (it >= ncode[cc]) continue;
-          if (n > 1) {
-            const int k = pic(ccode[cc][it], cc);
-            if (ps1[k] != code.x || ps2[k] != code.y) continue;
-          }
-          const int src = ozz * BR3 + cc, q = (oyy * 3 + oxx) * NV;
-#pragma unroll
-          for (int k = 0; k < NV; ++k) acc[k] += stage[q + k][stg(src)];
-        }
-      }
+    for (int k = 0; k < NV; ++k) {
+      const float t1 = __shfl_up_sync(FULL, a[i][1][k], 1);
+      const float t2 = __shfl_up_sync(FULL, a[i][2][k], 2);
+      const float t3 = __shfl_up_sync(FULL, a[i][2][k], 1);
+      float sum = a[i][0][k];
+      if (cx >= 1) sum += t1;
+      if (cx >= 2) sum += t2;
+      a[i][0][k] = sum;
+      a[i][1][k] = cx == 3 ? a[i][1][k] + t3 : 0.f;
+      a[i][2][k] = cx == 3 ? a[i][2][k] : 0.f;
     }
-    put(e0 + sl, acc);
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const float t1 = __shfl_up_sync(FULL, a[1][j][k], 4);
+      const float t2 = __shfl_up_sync(FULL, a[2][j][k], 8);
+      const float t3 = __shfl_up_sync(FULL, a[2][j][k], 4);
+      float sum = a[0][j][k];
+      if (cy >= 1) sum += t1;
+      if (cy >= 2) sum += t2;
+      a[0][j][k] = sum;
+      a[1][j][k] = cy == 3 ? a[1][j][k] + t3 : 0.f;
+      a[2][j][k] = cy == 3 ? a[2][j][k] : 0.f;
+    }
+}
+
+// The layer sums of xy_reduce into the z stage: sz[k][oz][t] is value k of
+// tile node t from the cells of z-layer t_z - oz.  Each (node, oz) entry that
+// the tile gather reads has exactly one writer.
+template <int NV>
+__device__ __forceinline__ void stage_layer(float (*sz)[3][TN], const float (&a)[3][3][NV], int cx, int cy,
+                                            int cz, int oz) {
+  const int tz = cz + oz;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if ((i > 0 && cy != 3) || (j > 0 && cx != 3)) continue;
+      const int t = (tz * TE + cy + i) * TE + cx + j;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sz[k][oz][t] = a[i][j][k];
+    }
+}
+
+// Sums of tile node t over the z-offsets of the z stage (<= 3 terms, in
+// ascending offset order).
+template <int NV>
+__device__ __forceinline__ void gather_z(const float (*sz)[3][TN], int t, float (&acc)[NV]) {
+  const int tz = t / (TE * TE);
+  const int o0 = max(0, tz - (BR - 1)), o1 = min(2, tz);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.f;
+  for (int o = o0; o <= o1; ++o)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += sz[k][o][t];
+}
+
+#define BM_BRICK_CODES 64  // distinct codes kept per brick (more raise the slot-overflow flag)
+
+// Distinct codes of the brick's particles (one warp, lane L holding cells 2L
+// and 2L + 1): the next code not yet listed is taken from the lowest lane
+// that has one, so the list is in first-occurrence order over the cells.
+template <int PPC>
+__device__ void brick_codes(const uint32_t *ps1, const uint32_t *ps2, const uint8_t (*ccode)[PPC],
+                            const uint8_t *ncode, uint2 *bcode, int *nbcode, unsigned int *err) {
+  const int lane = threadIdx.x & 31;
+  const int c0 = 2 * lane;
+  const int tot = ncode[c0] + ncode[c0 + 1];
+  int cur = 0, n = 0;
+  auto code_of = [&](int q, uint32_t &a, uint32_t &b) {
+    const int c = q < ncode[c0] ? c0 : c0 + 1;
+    const int j = ccode[c][q < ncode[c0] ? q : q - ncode[c0]];
+    const int k = pic(j, c);
+    a = ps1[k];
+    b = ps2[k];
+  };
+  for (;;) {
+    // advance past candidates already listed
+    uint32_t a = 0, b = 0;
+    while (cur < tot) {
+      code_of(cur, a, b);
+      bool seen = false;
+      for (int q = 0; q < n; ++q)
+        if (bcode[q].x == a && bcode[q].y == b) {
+          seen = true;
+          break;
+        }
+      if (!seen) break;
+      ++cur;
+    }
+    const unsigned pend = __ballot_sync(FULL, cur < tot);
+    if (!pend) break;
+    const int src = __ffs(pend) - 1;
+    const uint32_t ka = __shfl_sync(FULL, a, src), kb = __shfl_sync(FULL, b, src);
+    if (n < BM_BRICK_CODES) {
+      if (lane == 0) bcode[n] = make_uint2(ka, kb);
+      __syncwarp();
+    } else if (lane == 0) {
+      atomicOr(err, BM_ERRBIT_SLOT_OVERFLOW);
+    }
+    ++n;
+    if (n > BM_BRICK_CODES) break;
   }
+  if (lane == 0) *nbcode = min(n, BM_BRICK_CODES);
 }
 
 template <int PPC>
 struct K2S {
   Tile T;
-  union {
-    float stage[9 * 7][STG];     // per (cell, z-offset) thread: sums for its 9 nodes
-    float part[18][PPC * BR3];   // the brick's particles (fx, v, A, J), [particle-in-cell][cell]
-  };
+  float part[18][PPC * BR3];   // the brick's particles (fx, v, A, J), [particle-in-cell][cell]
+  float sz[7][3][TN];          // one pass's (node, z-offset) sums
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
+  uint2 bcode[BM_BRICK_CODES]; // distinct codes of the brick's particles
+  float red[6][BT / 32];       // wrench partials of the warps
   uint8_t ccode[BR3][PPC];  // distinct codes of each cell: particle-in-cell index of the
                             // first particle with each code (first-occurrence order)
   uint8_t ncode[BR3];
   int cs[BR3 + 1];
   int maxcodes;
+  int nbcode;
 };
 
-// Coalesced load of a brick's particles into shared memory, transposed to
+// The brick's particles into shared memory, transposed to
 // [particle-in-cell][cell] so that the (cell, z-offset) threads read
-// consecutive words.  The caller provides the barrier that publishes it.
-// With pass > 0 only the particles of cells holding more than `pass` codes
-// are copied (the only ones that pass reads).
-template <int PPC>
-__device__ void stage_particles(const PPool &P, const int4 &bt, int c0x, int c0y, int c0z, K2S<PPC> &S,
-                                bool codes, int pass = 0) {
+// consecutive words: the fractional offset, v, and the P2G inputs A and J
+// that pre_particle computes from x, v, F, D, u_t and the codes.  The caller
+// provides the barrier that publishes it.
+template <int PPC, bool INELASTIC>
+__device__ void stage_particles(const World &w, const DevScene &sc, const int4 &bt, int c0x, int c0y, int c0z,
+                                K2S<PPC> &S, float wr[6], bool &clamped, bool &anyc) {
+  const PPool &P = w.P;
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
     int bx, by, bz;
     particle_base(P.base[p], bx, by, bz);
+    const float x[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
+    const float v[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
+    const uint32_t s1 = P.s1[p], s2 = P.s2[p];
+    const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
+    float A[9], J[3];
+    pre_particle<INELASTIC>(sc, P, p, x, v, s1, s2, A, J, wr, clamped, anyc);
     const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
-    if (pass > 0 && S.ncode[c] <= pass) continue;
     const int si = pic(i - S.cs[c], c);
-    S.part[0][si] = P.fx[0][p];
-    S.part[1][si] = P.fx[1][p];
-    S.part[2][si] = P.fx[2][p];
-    S.part[3][si] = P.v[0][p];
-    S.part[4][si] = P.v[1][p];
-    S.part[5][si] = P.v[2][p];
+    S.part[0][si] = f0;
+    S.part[1][si] = f1;
+    S.part[2][si] = f2;
+    S.part[3][si] = v[0];
+    S.part[4][si] = v[1];
+    S.part[5][si] = v[2];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) S.part[6 + k][si] = P.A[k][p];
-    S.part[15][si] = P.J[0][p];
-    S.part[16][si] = P.J[1][p];
-    S.part[17][si] = P.J[2][p];
-    if (codes) {
-      S.ps1[si] = P.s1[p];
-      S.ps2[si] = P.s2[p];
-    }
+    for (int k = 0; k < 9; ++k) S.part[6 + k][si] = A[k];
+    S.part[15][si] = J[0];
+    S.part[16][si] = J[1];
+    S.part[17][si] = J[2];
+    S.ps1[si] = s1;
+    S.ps2[si] = s2;
   }
 }
 
@@ -917,13 +963,54 @@ __device__ __forceinline__ void cell_codes(const uint32_t *s1, const uint32_t *s
   atomicMax(maxcodes, cnt);
 }
 
-template <int PPC, int MB>
+// Whether cell c holds particles with code (k1, k2), and whether they are
+// all of the cell's particles.
+template <int PPC>
+__device__ __forceinline__ bool cell_has_code(const uint32_t *ps1, const uint32_t *ps2,
+                                              const uint8_t (*ccode)[PPC], const uint8_t *ncode, int c,
+                                              uint32_t k1, uint32_t k2) {
+  for (int q = 0; q < ncode[c]; ++q) {
+    const int k = pic(ccode[c][q], c);
+    if (ps1[k] == k1 && ps2[k] == k2) return true;
+  }
+  return false;
+}
+
+// Tile slot of node t holding code (k1, k2) as an index into the node's
+// slots, or -1; `uniform`: one code in the brick and one slot per node.
+// tcodes: the tile's slot codes in shared memory (by tile slot), or null to
+// read them from the slot pool.
+__device__ __forceinline__ uint2 tile_code(const World &w, const Tile &T, const uint2 *tcodes, int t, int a) {
+  return tcodes ? tcodes[T.lo[t] + a] : w.S.code[T.goff[t] + a];
+}
+
+__device__ __forceinline__ int node_slot_of(const World &w, const Tile &T, const uint2 *tcodes, int t,
+                                            bool uniform, uint32_t k1, uint32_t k2) {
+  const int n = T.cnt[t];
+  if (uniform) return n > 0 ? 0 : -1;
+  for (int a = 0; a < n; ++a) {
+    const uint2 c = tile_code(w, T, tcodes, t, a);
+    if (c.x == k1 && c.y == k2) return a;
+  }
+  return -1;
+}
+
+// In the first pass over a multi-code brick, the tile slots whose code no
+// particle of the brick carries get zero partial sums (every other slot is
+// written by the pass of its code).
+__device__ __forceinline__ bool code_listed(const uint2 *bcode, int n, uint2 c) {
+  for (int q = 0; q < n; ++q)
+    if (bcode[q].x == c.x && bcode[q].y == c.y) return true;
+  return false;
+}
+
+template <int PPC, int MB, bool INELASTIC>
 __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   K2S<PPC> &S = *reinterpret_cast<K2S<PPC> *>(smraw);
   const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
-  const DevScene &sc = w.scenes[bt.x];
-  const PPool &P = w.P;
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
   const int tid = threadIdx.x;
   const int lb = bt.y - sc.brick_begin;
   int c0x, c0y, c0z;
@@ -932,45 +1019,55 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   for (int i = tid; i <= BR3; i += BT) S.cs[i] = csg[i] - bt.z;
   if (tid == 0) S.maxcodes = 0;
   __syncthreads();
-  // the particle copy and the tile descriptors load together (one barrier)
-  stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, true);
+  // the particles (with contact, labels and stress) and the tile descriptors
+  // load together
+  float wr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  bool clamped = false, anyc = false;
+  stage_particles<PPC, INELASTIC>(w, sc, bt, c0x, c0y, c0z, S, wr, clamped, anyc);
+  if (clamped) atomicOr(&scm.err, BM_ERRBIT_INVERTED);
   const bool single = tile_load(w, sc, bt.y, c0x, c0y, c0z, S.T);
+  if (sc.has_blade) brick_wrench(w, bt.y, wr, anyc, S.red);  // (its barriers publish the copy too)
   cell_codes<PPC>(S.ps1, S.ps2, S.cs, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
   // every tile node holds one logical grid (so all the brick's particles
-  // share one code): the gather needs no code tests
-  const bool uniform_brick = single && S.maxcodes <= 1;
+  // share one code): one pass, no code tests
+  const bool uniform = single && S.maxcodes <= 1;
+  if (!uniform) {
+    if (tid < 32) brick_codes<PPC>(S.ps1, S.ps2, S.ccode, S.ncode, S.bcode, &S.nbcode, &scm.err);
+    __syncthreads();
+  }
+  // a brick without particles still runs one pass: it writes zeros to its tile
+  const int nbc = uniform ? 1 : S.nbcode;
+  const int npass = max(nbc, 1);
 
-  // ---- per (cell, z-offset) sums over the cell's particles ----
+  // ---- one pass per code of the brick ----
   // Each thread sums, for its cell and one z-offset, m N, m v N and
-  // A grad N + N J over the cell's particles of one code (one pass per code
-  // present in the cell) into a staging area; then each tile node adds the
-  // <= 27 staged sums of the cells around it, in a fixed order, and writes
-  // its slots' partials.  Every float sum has one owner: no atomics.  The
-  // staging area shares its memory with the particle copy, so a brick with
-  // several codes in a cell copies its particles again for each pass.
+  // A grad N + N J over the cell's particles with the pass's code; the warp
+  // reduces the sums along x and y (xy_reduce), the z stage collects the
+  // layers, and each tile node adds its <= 3 layer sums and writes the slot
+  // of the pass's code.  Every float sum has one owner: no atomics, and each
+  // partial-sum entry is written exactly once.
   const int c = tid % BR3, oz = tid / BR3;
+  const int cx = c & 3, cy = (c >> 2) & 3, cz = c >> 4;
   const int n_c = S.cs[c + 1] - S.cs[c];
-  const int iters = S.maxcodes > 0 ? S.maxcodes : 1;  // one pass writes zeros for empty bricks
   const int pbase = w.B.poff[bt.y];  // this brick's partial-sum range (negative: pool overflow)
-  for (int it = 0; it < iters; ++it) {
-    if (it > 0) {
-      stage_particles<PPC>(P, bt, c0x, c0y, c0z, S, false, it);
-      __syncthreads();
-    }
-    const bool has = it < S.ncode[c];
-    const int kc = has ? pic(S.ccode[c][it], c) : 0;
-    const uint32_t k1 = has ? S.ps1[kc] : 0u, k2 = has ? S.ps2[kc] : 0u;
-    const bool uniform = S.ncode[c] == 1;
-    float a[9][7];
+  for (int b = 0; b < npass; ++b) {
+    const bool coded = b < nbc;  // false only in the single pass of a brick without particles
+    const uint32_t k1 = (uniform || !coded) ? 0u : S.bcode[b].x, k2 = (uniform || !coded) ? 0u : S.bcode[b].y;
+    const bool has = coded && n_c > 0 &&
+                     (uniform || cell_has_code<PPC>(S.ps1, S.ps2, S.ccode, S.ncode, c, k1, k2));
+    const bool filt = !uniform && S.ncode[c] > 1;
+    float a[3][3][7];
 #pragma unroll
-    for (int q = 0; q < 9; ++q)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int f = 0; f < 7; ++f) a[q][f] = 0.f;
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int f = 0; f < 7; ++f) a[i][j][f] = 0.f;
     if (has) {
       for (int j = 0; j < n_c; ++j) {
         const int si = pic(j, c);
-        if (!uniform && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
+        if (filt && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
         float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
         const float f0 = S.part[0][si], f1 = S.part[1][si], f2 = S.part[2][si];
         bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
@@ -993,7 +1090,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
           const float M0 = v0 * wyz, M1 = v1 * wyz, M2 = v2 * wyz;
 #pragma unroll
           for (int ox = 0; ox < 3; ++ox) {
-            float *q = a[oy * 3 + ox];
+            float *q = a[oy][ox];
             const float wxx = wx[ox], dxx = dwx[ox];
             q[0] += wxx * wyz;
             q[1] += wxx * M0;
@@ -1006,33 +1103,29 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
         }
       }
     }
-    __syncthreads();  // the particle copy is read: the staging area may overwrite it
-    // the gather reads a cell's sums only when the cell holds an it-th code
-    // (pass 0 also reads the zeros of empty cells)
-    if (it == 0 || has)
-#pragma unroll
-      for (int q = 0; q < 9; ++q)
-#pragma unroll
-        for (int f = 0; f < 7; ++f) S.stage[q * 7 + f][stg(tid)] = a[q][f];
+    xy_reduce<7>(a, cx, cy);
+    stage_layer<7>(S.sz, a, cx, cy, cz, oz);
     __syncthreads();
-    // tile nodes gather the staged sums of the cells around them: nodes
-    // 0..191 one per thread, the last 24 one (node, value) per thread
     if (pbase >= 0) {
-      auto put = [&](size_t e, const float *acc) {  // pm = (m, m v), pd = force sums
-        if (it == 0) {
-          w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-          w.B.pd[e] = make_float4(acc[4], acc[5], acc[6], 0.f);
-        } else {
-          const float4 pm = w.B.pm[e], pd = w.B.pd[e];
-          w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], pm.w + acc[3]);
-          w.B.pd[e] = make_float4(pd.x + acc[4], pd.y + acc[5], pd.z + acc[6], 0.f);
-        }
-      };
-      for (int t = tid; t < TN; t += BT)
-        gather_tile_node<PPC, 7>(w, S.T, S.stage, S.ncode, S.ccode, S.ps1, S.ps2, it, t, uniform_brick,
-                                 pbase, put);
+      for (int t = tid; t < TN; t += BT) {
+        const int n = S.T.cnt[t];
+        if (n == 0) continue;
+        const size_t e0 = (size_t)pbase + S.T.lo[t];
+        if (b == 0 && !uniform)
+          for (int q = 0; q < n; ++q)
+            if (!code_listed(S.bcode, S.nbcode, tile_code(w, S.T, nullptr, t, q))) {
+              w.B.pm[e0 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+              w.B.pd[e0 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        const int sl = coded ? node_slot_of(w, S.T, nullptr, t, uniform, k1, k2) : -1;
+        if (sl < 0) continue;
+        float acc[7];
+        gather_z<7>(S.sz, t, acc);
+        w.B.pm[e0 + sl] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        w.B.pd[e0 + sl] = make_float4(acc[4], acc[5], acc[6], 0.f);
+      }
     }
-    __syncthreads();
+    if (b + 1 < npass) __syncthreads();  // the next pass overwrites the z stage
   }
 }
 
@@ -1159,15 +1252,17 @@ struct K4S {
       float4 tvo[TSCAP];      // v_old xyz, m of the tile slots (G2P)
       float4 tvn[TSCAP];      // v_new xyz
     };
-    float stage[9 * 3][STG];  // then: per (cell, z-offset) MUSL sums for 9 nodes
+    float sz[3][3][TN];       // then: one MUSL pass's (node, z-offset) sums
   };
   float pf[3][PPC * BR3];
   float pv[3][PPC * BR3];
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
-  uint8_t ccode[BR3][PPC];  // as in K2S
+  uint2 bcode[BM_BRICK_CODES];  // as in K2S
+  uint8_t ccode[BR3][PPC];
   uint8_t ncode[BR3];
   int cs[BR3 + 1];
   int maxcodes;
+  int nbcode;
 };
 
 template <int PPC, int MB>
@@ -1200,7 +1295,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
     for (int t = tid; t < TN; t += BT) {
       const int n = S.T.cnt[t], lo = S.T.lo[t], g = S.T.goff[t];
       for (int a = 0; a < n; ++a) {
-        if (n > 1) S.codes[lo + a] = w.S.code[g + a];
+        S.codes[lo + a] = w.S.code[g + a];  // every slot: the MUSL passes look codes up by slot
         S.tvo[lo + a] = w.S.vold[g + a];
         S.tvn[lo + a] = w.S.vnew[g + a];
       }
@@ -1310,28 +1405,37 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
     S.ps2[si] = s2;
   }
   if (bad) atomicOr(&scm.err, BM_ERRBIT_NONFINITE);
-  // ---- phase 1: MUSL sums m v^{n+1} N per (cell, z-offset), staged, then
-  // gathered by the tile nodes in a fixed order (as in k_p2g_brick) ----
+  // ---- phase 1: MUSL sums m v^{n+1} N, one pass per code of the brick,
+  // reduced as in k_p2g_brick (xy_reduce, z stage, <= 3 layer sums per node) ----
   const int c = tid % BR3, oz = tid / BR3;
+  const int cx = c & 3, cy = (c >> 2) & 3, cz = c >> 4;
   const int n_c = S.cs[c + 1] - S.cs[c];
-  __syncthreads();  // G2P reads of the tile velocities are done: stage may reuse them
+  __syncthreads();  // G2P reads of the tile velocities are done: the z stage may reuse them
   cell_codes<PPC>(S.ps1, S.ps2, S.cs, S.ccode, S.ncode, &S.maxcodes);
   __syncthreads();
-  const bool uniform_brick = single && S.maxcodes <= 1;
-  const int iters = S.maxcodes > 0 ? S.maxcodes : 1;
+  const bool uniform = single && S.maxcodes <= 1;
+  if (!uniform) {
+    if (tid < 32) brick_codes<PPC>(S.ps1, S.ps2, S.ccode, S.ncode, S.bcode, &S.nbcode, &scm.err);
+    __syncthreads();
+  }
+  const int nbc = uniform ? 1 : S.nbcode;
+  const int npass = max(nbc, 1);  // a brick without particles writes zeros in one pass
   const int pbase = w.B.poff[bt.y];
-  for (int it = 0; it < iters; ++it) {
-    const bool has = it < S.ncode[c];
-    const int kc = has ? pic(S.ccode[c][it], c) : 0;
-    const uint32_t k1 = has ? S.ps1[kc] : 0u, k2 = has ? S.ps2[kc] : 0u;
-    const bool uniform = S.ncode[c] == 1;
-    float a[9][3];
+  for (int b = 0; b < npass; ++b) {
+    const bool coded = b < nbc;
+    const uint32_t k1 = (uniform || !coded) ? 0u : S.bcode[b].x, k2 = (uniform || !coded) ? 0u : S.bcode[b].y;
+    const bool has = coded && n_c > 0 &&
+                     (uniform || cell_has_code<PPC>(S.ps1, S.ps2, S.ccode, S.ncode, c, k1, k2));
+    const bool filt = !uniform && S.ncode[c] > 1;
+    float a[3][3][3];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) a[q][0] = a[q][1] = a[q][2] = 0.f;
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) a[i][j][0] = a[i][j][1] = a[i][j][2] = 0.f;
     if (has) {
       for (int j = 0; j < n_c; ++j) {
         const int si = pic(j, c);
-        if (!uniform && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
+        if (filt && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
         float wx[3], wy[3], wz, d;
         const float f0 = S.pf[0][si], f1 = S.pf[1][si], f2 = S.pf[2][si];
         bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
@@ -1344,33 +1448,33 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
 #pragma unroll
           for (int ox = 0; ox < 3; ++ox) {
             const float N = wx[ox] * wyz;
-            a[oy * 3 + ox][0] += N * v0;
-            a[oy * 3 + ox][1] += N * v1;
-            a[oy * 3 + ox][2] += N * v2;
+            a[oy][ox][0] += N * v0;
+            a[oy][ox][1] += N * v1;
+            a[oy][ox][2] += N * v2;
           }
         }
       }
     }
-    if (it == 0 || has)
-#pragma unroll
-      for (int q = 0; q < 9; ++q)
-#pragma unroll
-        for (int f = 0; f < 3; ++f) S.stage[q * 3 + f][stg(tid)] = a[q][f];
+    xy_reduce<3>(a, cx, cy);
+    stage_layer<3>(S.sz, a, cx, cy, cz, oz);
     __syncthreads();
     if (pbase >= 0) {
-      auto put = [&](size_t e, const float *acc) {  // pm = MUSL momentum sums
-        if (it == 0) {
-          w.B.pm[e] = make_float4(acc[0], acc[1], acc[2], 0.f);
-        } else {
-          const float4 pm = w.B.pm[e];
-          w.B.pm[e] = make_float4(pm.x + acc[0], pm.y + acc[1], pm.z + acc[2], 0.f);
-        }
-      };
-      for (int t = tid; t < TN; t += BT)
-        gather_tile_node<PPC, 3>(w, S.T, S.stage, S.ncode, S.ccode, S.ps1, S.ps2, it, t, uniform_brick,
-                                 pbase, put);
+      for (int t = tid; t < TN; t += BT) {
+        const int n = S.T.cnt[t];
+        if (n == 0) continue;
+        const size_t e0 = (size_t)pbase + S.T.lo[t];
+        if (b == 0 && !uniform)
+          for (int q = 0; q < n; ++q)
+            if (!code_listed(S.bcode, S.nbcode, tile_code(w, S.T, tcodes, t, q)))
+              w.B.pm[e0 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int sl = coded ? node_slot_of(w, S.T, tcodes, t, uniform, k1, k2) : -1;
+        if (sl < 0) continue;
+        float acc[3];
+        gather_z<3>(S.sz, t, acc);
+        w.B.pm[e0 + sl] = make_float4(acc[0], acc[1], acc[2], 0.f);
+      }
     }
-    __syncthreads();
+    if (b + 1 < npass) __syncthreads();  // the next pass overwrites the z stage
   }
 }
 
@@ -2254,9 +2358,12 @@ template <> struct Occ<2> { static constexpr int p2g = 4, g2p = 6, fupd = 8; };
 
 template <int PPC, int V>
 static cudaError_t set_smem_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC, Occ<V>::p2g>,
+  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC, Occ<V>::p2g, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(K2S<PPC>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_p2g_brick<PPC, Occ<V>::p2g, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(K2S<PPC>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_g2p_musl<PPC, Occ<V>::g2p>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K4S<PPC>));
@@ -2282,12 +2389,11 @@ cudaError_t bm_kernels_init() {
 
 template <int PPC, int V>
 static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
-  rec(ev, 18, 0, st);
-  if (ls.any_inelastic) k_pre<true><<<ls.n_btiles, 128, 0, st>>>(w, ls);
-  else k_pre<false><<<ls.n_btiles, 128, 0, st>>>(w, ls);
-  rec(ev, 18, 1, st);
   rec(ev, 0, 0, st);
-  k_p2g_brick<PPC, Occ<V>::p2g><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+  if (ls.any_inelastic)
+    k_p2g_brick<PPC, Occ<V>::p2g, true><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+  else
+    k_p2g_brick<PPC, Occ<V>::p2g, false><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
   rec(ev, 0, 1, st);
   rec(ev, 1, 0, st);
   k_p2g_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
