@@ -186,10 +186,12 @@ def dist_setup():
     return world, rank, local
 
 
-def rank_scenes(rank: int):
+def rank_scenes(rank: int, n_scenes: int = N_SCENES):
     """The batch of one rank: 256 uneven scenes seeded per rank (rank 0 uses
-    the workload's seed), so ranks hold independent shards of the work."""
-    return bi.batched_scenes(N_SCENES, seed=SEED + rank, n_substeps=100000)
+    the workload's seed), so ranks hold independent shards of the work.  A
+    smaller n_scenes takes the first scenes of the same stream (a slice of
+    the workload for profiling; the benchmark's value always uses all 256)."""
+    return bi.batched_scenes(N_SCENES, seed=SEED + rank, n_substeps=100000)[:n_scenes]
 
 
 def reduce_over_ranks(dist, ms: float, particles: int, device="cuda"):
@@ -218,7 +220,7 @@ def run_native(args):
     import paper_2609_27342_gb300 as pkg
     pkg.load()
 
-    scenes = rank_scenes(rank)
+    scenes = rank_scenes(rank, args.scenes)
     n_particles = sum(s.n for s in scenes)
     stream = torch.cuda.Stream()
     fps = [pkg.footprint(s) for s in scenes]
@@ -246,7 +248,7 @@ def run_native(args):
         log(f"plain path: {plain_rate:.3e} p-s/s ({plain_ms:.1f} ms for {plain_steps} substeps)")
 
     def make_batch(members):
-        b = pkg.Batch(max_particles=n_particles, max_nodes=sum(nodes), max_scenes=N_SCENES,
+        b = pkg.Batch(max_particles=n_particles, max_nodes=sum(nodes), max_scenes=len(scenes),
                       max_bricks=n_bricks, stream=stream)
         for o in members:
             b.add(o)
@@ -461,11 +463,29 @@ def run_native(args):
         e1.record(stream)
         torch.cuda.synchronize()
         r1 = sc1.n * 200 / (e0.elapsed_time(e1) * 1e-3)
+        # the same substeps through a one-scene batch (CUDA-graph launches)
+        fp1 = pkg.footprint(sc1)
+        b1 = pkg.Batch(max_particles=sc1.n, max_nodes=fp1[1], max_scenes=1, max_bricks=fp1[2],
+                       pair_contact=True, stream=stream)
+        g1b = pkg.Scene.in_batch(b1, sc1)
+        b1.step(100)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b1.step(200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r1b = sc1.n * 200 / (e0.elapsed_time(e1) * 1e-3)
+        builds = int(g1b.info().contact_list_builds)
+        g1b.close()
+        b1.close()
         configs["cylinder"] = {"workload": "cylinder 0.2 m x r 0.02 m, dx 2 mm, two intersecting "
                                            "cuts and a push, 0.2 kg two-way tool, pair contact",
                                "particles": sc1.n, "path": "plain (one scene per launch)",
                                "value": r1, "unit": UNIT, "substeps_timed": 200,
-                               "first_substep": 100, "error_bits": int(g1.info().error_bits)}
+                               "first_substep": 100, "error_bits": int(g1.info().error_bits),
+                               "graph_path_value": r1b,
+                               "graph_path": "one-scene batch (CUDA-graph launches), same substeps",
+                               "contact_list_builds_in_300_substeps": builds}
         # reference-grid surface of the cylinder mid-stroke (visual only; not
         # part of the substep): full rebuild from the codes + embedding, and
         # the embedding alone, each call timed by the wall clock (it
@@ -534,9 +554,14 @@ def run_native(args):
         serving = {"requests": st["requests"], "ranks": st["ranks"], "rate_hz": 50,
                    "budget_gb": args.serve_budget_gb,
                    "throughput": st["throughput"], "unit": UNIT, "wall_s": st["wall_s"],
+                   "offered_load": st.get("offered_load"),
+                   "over_batched": st["throughput"] / value if value else None,
                    "step_ms_p50": st["step_ms_p50"], "step_ms_p99": st["step_ms_p99"],
                    "request_latency_s_p50": st["request_latency_s_p50"],
-                   "request_latency_s_p99": st["request_latency_s_p99"]}
+                   "request_latency_s_p99": st["request_latency_s_p99"],
+                   "queue_latency_s_p50": st.get("queue_latency_s_p50"),
+                   "queue_latency_s_p99": st.get("queue_latency_s_p99"),
+                   "host_s": st.get("host_s")}
         log(f"serving: {serving}")
 
     cpu = None
@@ -561,7 +586,9 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scenes": N_SCENES, "particles": n_particles,
+            "config": {"workload": WORKLOAD if args.scenes == N_SCENES else
+                       f"first {args.scenes} of the 256 scenes of: {WORKLOAD} (profiling slice)",
+                       "scenes": len(scenes), "particles": n_particles,
                        "job_particles": job_particles, "seeds": f"{SEED}..{SEED + world - 1} (one per rank)",
                        "nodes": n_nodes, "slots": n_slots, "seed": SEED,
                        "bricks": n_bricks, "substeps_timed": args.steps,
@@ -636,6 +663,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cylinder_profile(args):
+    """Per-kernel CUDA-event times of the cylinder program (252,800 particles,
+    two-way tool, pair contact) in a one-scene batch, at four points of the
+    program; one JSON line."""
+    import torch
+    from paper_2609_27342_gb300 import build as B
+    B.build()
+    import paper_2609_27342_gb300 as pkg
+    pkg.load()
+    sc = bi.cylinder_cuts_push()
+    fp = pkg.footprint(sc)
+    stream = torch.cuda.Stream()
+    b = pkg.Batch(max_particles=sc.n, max_nodes=fp[1], max_scenes=1, max_bricks=fp[2], pair_contact=True,
+                  stream=stream)
+    g = pkg.Scene.in_batch(b, sc)
+    out = {"workload": "cylinder program (two intersecting cuts and a push, two-way tool, pair contact)",
+           "particles": sc.n, "points": {}}
+    done = 0
+    for at in (300, 900, 2200, 2850):
+        b.step(at - done)
+        done = at
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        done += 20
+        builds0 = int(g.info().contact_list_builds)
+        prof = b.profile(10)
+        done += 10
+        out["points"][str(at)] = {
+            "ms_per_substep": e0.elapsed_time(e1) / 20,
+            "list_builds_in_10_profiled": int(g.info().contact_list_builds) - builds0,
+            "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items() if v[1]}}
+    out["error_bits"] = int(g.info().error_bits)
+    b.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint_only(args):
+    """The calibration workload (32,000 particles, 200 substeps, checkpoint
+    every 20): one forward + backward after a warm-up; one JSON line."""
+    import torch
+    from paper_2609_27342_gb300 import build as B
+    B.build()
+    import paper_2609_27342_gb300 as pkg
+    pkg.load()
+    from paper_2609_27342_gb300.calibration import force_loss_and_grad, forces
+    na = 200
+    target = forces(bi.calibration_scene(E=1.5e5), na)
+    spec = bi.calibration_scene()
+    force_loss_and_grad(spec, target, na, every=20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, g = force_loss_and_grad(spec, target, na, every=20)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": "calibration cuboid, 32,000 particles, 200 substeps, checkpoint every 20",
+                      "forward_backward_s": time.perf_counter() - t0, "loss": loss,
+                      "grad": {"E": g["E"], "nu": g["nu"], "speed": -float(g["v_seg"][0, 2])}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -649,16 +740,26 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-configs", dest="configs", action="store_false")
     ap.add_argument("--no-late-window", dest="late_window", action="store_false")
+    ap.add_argument("--scenes", type=int, default=N_SCENES,
+                    help="take the first scenes of the workload only (profiling slices)")
+    ap.add_argument("--cylinder-profile", action="store_true",
+                    help="only the per-kernel times of the cylinder program")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only one forward + backward of the calibration workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.cylinder_profile:
+        run_cylinder_profile(args)
+    elif args.adjoint_only:
+        run_adjoint_only(args)
     else:
         run_native(args)
 

@@ -174,6 +174,7 @@ typedef struct {
   uint32_t error_bits;       /* sticky BM_ERRBIT_* word */
   int grid_lo[3], grid_dim[3];
   int32_t current_cut;       /* id of the cut in progress (the last cut-creating segment), -1 before any */
+  int64_t contact_list_builds; /* material-material contact: candidate-list builds so far */
 } bm_scene_info;
 
 /* ---- scene ------------------------------------------------------------- */
@@ -197,6 +198,17 @@ int bm_get_tool_state(bm_scene_t s, int blade_id, double pose[12], double twist[
 /* Advance n_substeps substeps on the scene's stream (one launch per kernel
  * per substep: the plain one-scene-per-launch path). */
 int bm_step(bm_scene_t s, int n_substeps);
+
+/* Stop substep of a scene (a serving control; the paper has no counterpart):
+ * once the scene has taken `stop_at` substeps it stops advancing -- every
+ * kernel of later substeps, alone or in a batch, leaves it untouched until
+ * the stop is moved -- so a batch can step its members by whole chunks while
+ * each request still ends after exactly its own number of substeps, with
+ * the same result as a run of that length alone.  stop_at = -1 (the
+ * default) never stops.  A stop at or below the current substep freezes the
+ * scene at once.  Synchronises the scene's stream.  Errors: BM_E_INVALID
+ * (bad handle, stop_at < -1). */
+int bm_scene_set_stop(bm_scene_t s, int64_t stop_at);
 
 /* Copy the fields in field_mask into dst[i] (one pointer per set bit, in bit
  * order).  dst_on_device != 0: dst are device pointers.  Synchronises the
@@ -355,8 +367,10 @@ const char *bm_kernel_name(int i);
 /* Launch shape used by subsequent bm_batch_step calls (set by the
  * autotuner): substeps per captured CUDA graph (1..256), nodes per CTA of the
  * per-node kernels (multiple of 32 in 64..512) and the brick-kernel
- * occupancy variant (0: 3/5/7 resident CTAs per SM for P2G, G2P+MUSL and the
- * F update; 1: 2/4/5, more registers per thread; 2: 4/6/8).  Results do not
+ * occupancy variant v in 0..26, one choice per brick kernel: v % 3 for P2G
+ * (3, 2 or 4 resident CTAs per SM), (v / 3) % 3 for G2P+MUSL (5, 4 or 6) and
+ * v / 9 for the F update (7, 5 or 8); fewer CTAs leave more registers per
+ * thread, more hide more latency; 0 is every kernel's default.  Results do not
  * depend on any of them: every sum is taken in a fixed order and the
  * variants share their arithmetic.  Synchronises the batch stream; captured
  * graphs are rebuilt on the next step.  BM_E_INVALID on an out-of-range

@@ -75,7 +75,8 @@ class BladeDesc(C.Structure):
 class SceneInfo(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("n_nodes", C.c_int64), ("n_slots", C.c_int64),
                 ("slot_capacity", C.c_int64), ("step", C.c_int64), ("error_bits", C.c_uint32),
-                ("grid_lo", C.c_int * 3), ("grid_dim", C.c_int * 3), ("current_cut", C.c_int32)]
+                ("grid_lo", C.c_int * 3), ("grid_dim", C.c_int * 3), ("current_cut", C.c_int32),
+                ("contact_list_builds", C.c_int64)]
 
 
 class BatchDesc(C.Structure):
@@ -103,6 +104,7 @@ SIGNATURES = {
     "bm_set_tool_state": (C.c_int, [VP, C.c_int, PD, PD]),
     "bm_get_tool_state": (C.c_int, [VP, C.c_int, PD, PD]),
     "bm_step": (C.c_int, [VP, C.c_int]),
+    "bm_scene_set_stop": (C.c_int, [VP, C.c_int64]),
     "bm_read_state": (C.c_int, [VP, C.c_uint32, PVP, C.c_int]),
     "bm_write_state": (C.c_int, [VP, C.c_uint32, PVP, C.c_int]),
     "bm_read_state_noalloc": (C.c_int, [VP, C.c_uint32, PVP]),

@@ -1,24 +1,26 @@
 """Launch-shape autotuner for a batch of scenes.
 
-The batched substep has three launch parameters that do not change its
-results (every sum is taken in a fixed order, and the kernel variants share
-their arithmetic): the brick-kernel occupancy variant (resident CTAs per SM of
-the per-brick P2G, G2P+MUSL and F-update kernels, i.e. registers per thread
-against latency hiding), the node tile (threads per CTA of the per-node
-kernels) and the number of substeps captured in one CUDA graph.  The tuner
-times candidate shapes on the batch itself with CUDA events on the batch's
-stream and keeps the fastest.
+The batched substep has launch parameters that do not change its results
+(every sum is taken in a fixed order, and the kernel variants share their
+arithmetic): the occupancy of each brick kernel (resident CTAs per SM of the
+per-brick P2G, G2P+MUSL and F-update kernels, i.e. registers per thread
+against latency hiding; one of three choices each, encoded in the brick
+variant as p2g + 3 g2p + 9 fupd), the node tile (threads per CTA of the
+per-node kernels) and the number of substeps captured in one CUDA graph.  The
+tuner times candidate shapes on the batch itself with CUDA events on the
+batch's stream and keeps the fastest: one brick kernel's occupancy at a time
+(the kernels run one after the other, so their choices are independent),
+then the node tile, then the graph chunk.
 
 Every probe advances the simulation: tuning is a warm-up of the batch, not a
 side computation.
 """
 from __future__ import annotations
 
-import itertools
 import math
 from typing import Dict, Iterable, List, Optional
 
-VARIANTS = (0, 1, 2)
+OCC_CHOICES = (0, 1, 2)   # per brick kernel
 NODE_TILES = (64, 128, 256, 512)
 GRAPH_CHUNKS = (4, 8, 16, 32)
 
@@ -45,11 +47,17 @@ def _time_shape(batch, stream, chunk: int, ntile: int, variant: int, substeps: i
     return best, chunk + rounds * n
 
 
+def variant(p2g: int, g2p: int, fupd: int) -> int:
+    """Brick variant of one occupancy choice per brick kernel."""
+    return p2g + 3 * g2p + 9 * fupd
+
+
 def autotune(batch, stream, key: Optional[tuple] = None, substeps: int = 16, rounds: int = 1,
-             variants: Iterable[int] = VARIANTS, node_tiles: Iterable[int] = NODE_TILES,
+             occ_choices: Iterable[int] = OCC_CHOICES, node_tiles: Iterable[int] = NODE_TILES,
              graph_chunks: Iterable[int] = GRAPH_CHUNKS, baseline=(16, 128, 0)) -> dict:
-    """Pick (brick variant, node tile) on a full grid at a 16-substep graph,
-    then the graph chunk for the winner; set it on ``batch`` and return
+    """Pick each brick kernel's occupancy in turn (the others held at their
+    best so far) at a 16-substep graph, then the node tile, then the graph
+    chunk; set the winner on ``batch`` and return
     ``{"best": {...}, "trials": [...], "substeps_advanced": n}``.
 
     The probes advance the scenes, and the cost of a substep drifts as cuts
@@ -83,8 +91,18 @@ def autotune(batch, stream, key: Optional[tuple] = None, substeps: int = 16, rou
     trials.append({"brick_variant": baseline[2], "node_tile": baseline[1],
                    "graph_chunk": baseline[0], "ms": ref_ms, "relative": 1.0})
     seen.add(tuple(baseline))
-    for v, t in itertools.product(variants, node_tiles):
-        probe(16, t, v)
+    occ = [0, 0, 0]
+    for k in range(3):          # P2G, G2P+MUSL, F update
+        for c in occ_choices:
+            o = list(occ)
+            o[k] = c
+            probe(16, baseline[1], variant(*o))
+        best = min((r for r in trials if r["graph_chunk"] == 16 and r["node_tile"] == baseline[1]),
+                   key=lambda r: r["relative"])
+        v = best["brick_variant"]
+        occ = [v % 3, (v // 3) % 3, v // 9]
+    for t in node_tiles:
+        probe(16, t, variant(*occ))
     best = min(trials, key=lambda r: r["relative"])
     for c in graph_chunks:
         probe(c, best["node_tile"], best["brick_variant"])

@@ -22,6 +22,7 @@
 #define BM_TILE_NODES 216    // 6 x 6 x 6 nodes touched by a brick of 4 x 4 x 4 base cells
 #define BM_BRICK_CELLS 64
 #define BM_HIST 16           // pair-contact history entries per particle
+#define BM_NBR 64            // pair-contact candidates kept per particle (Verlet list)
 #define BM_WRENCH_W 6
 
 struct DevSeg {
@@ -55,8 +56,13 @@ struct DevScene {
   float s_n, gamma_k, gamma_c;
   float pair_mu_s, pair_mu_d;
   float floor_z;
-  float pair_h, pair_inv_h;  // pair-contact cell size of this substep
+  float pair_h, pair_inv_h;  // pair-contact hash cell size of the last list build
   int pair_vmax_bits;        // max particle speed of this substep (float bits)
+  int pair_disp_bits;        // max over particles of displacement since the last list
+                             // build + dt |v| (float bits)
+  int pair_valid;            // the candidate lists match this scene's pool (0: rebuild)
+  int pair_build;            // the lists are rebuilt this substep
+  long long pair_builds;     // candidate-list builds so far
   int floor_on, pair_on, tool_contact_on, has_blade;
   // float64 copies used by the exact label path and the tool integrator
   double dt_d, h_d, L_d, b_back_d, b_lead_d;
@@ -84,11 +90,14 @@ struct DevScene {
   unsigned int cutpl_set;
   // counters and flags
   long long step;
+  long long stop_at;        // >= 0: the scene stops advancing once step reaches it
+  int frozen;               // set by the tool kernel when step reaches stop_at; every
+                            // substep kernel then leaves the scene untouched
   unsigned int err;
   int label_pending;
   int need_rebuild;
   int n_slots;
-  int pad_[2];
+  int pad_[1];
 };
 
 struct PPool {
@@ -98,16 +107,18 @@ struct PPool {
   float *Fpi[9];            // inverse plastic deformation Fp^-1 (identity without plasticity)
   float *Fdot[9];           // dF/dt of the last substep (viscosity)
   uint32_t *s1, *s2;        // bit k: digit k == 1 (s1) or == 2 (s2)
-  float *A[9];              // -dt V0 P(F) / dx of this substep (k_pre -> k_p2g_brick)
-  float *J[3];              // impulse of this substep: pair contact, then the total
+  float *J[3];              // pair-contact impulse of this substep (k_pair -> k_p2g_brick)
   uint8_t *pend;            // side digit assigned this substep (0: none), committed by k_fupd
   int *perm;                // pool index -> caller's particle index
   // pair contact
   int *hkey;                // bucket of each particle's current-configuration cell
-  long long *hcell;         // that cell's packed coordinates (exact match on lookup)
   int *horder;              // particles ordered by bucket, by pool index inside a bucket
+  float4 *hent;             // the same order: position and pool index (int bits in w)
   int *hist_partner[2];     // pair history (partner pool index, -1 ends), by step parity
   float *hist_u[2];         // [(p * BM_HIST + k) * 3]: tangential spring displacement
+  int *nbr;                 // [p * BM_NBR + k]: contact candidates (pool index, ascending)
+  uint8_t *nbr_n;           // candidates of each particle
+  float *xb[3];             // positions at the last candidate-list build
 };
 
 struct NPool {
@@ -133,12 +144,14 @@ struct BPool {              // brick-tile partial sums
   int *poff;                // first entry of each brick's partial sums (-1: pool overflow)
   int *ptot;                // slots in each brick's tile
   int *tdesc;               // [brick * BM_TILE_NODES]: first tile slot | slot count << 16
+  int *tgoff;               // [brick * BM_TILE_NODES]: first pool slot of each tile node
 };
 
 struct HashPool {           // pair-contact spatial hash (world-wide table)
   int *bucket_start;        // [n_buckets + 1]: counts, then exclusive offsets
   int *bucket_fill;         // [n_buckets]
   int *block_sum;           // [n_buckets / 1024 + 1]
+  int *build;               // some scene rebuilds its candidate lists this substep
   int n_buckets;            // power of two
 };
 
@@ -203,7 +216,7 @@ cudaError_t bm_launch_surface_embed(const World &w, const SurfParams &sp, int n_
 
 // kernel launchers (bm_kernels.cu)
 #define BM_NUM_KERNELS 19
-#define BM_NUM_VARIANTS 3
+#define BM_NUM_VARIANTS 27  // 3 occupancy choices for each of the 3 brick kernels
 extern const char *const bm_kernel_names[BM_NUM_KERNELS];
 cudaError_t bm_kernels_init();  // per device: shared-memory limits of the brick kernels
 

@@ -575,11 +575,7 @@ __device__ bool tile_load(const World &w, const DevScene &sc, int brick, int c0x
   for (int t = threadIdx.x; t < TN; t += blockDim.x) {
     const int d = w.B.tdesc[(size_t)brick * TN + t];
     const int cnt = d >> 16;
-    int off = 0;
-    if (cnt) {
-      const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
-      off = w.N.slot_off[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
-    }
+    const int off = w.B.tgoff[(size_t)brick * TN + t];  // valid where cnt > 0
     T.lo[t] = (uint16_t)(d & 0xffff);
     T.cnt[t] = (uint8_t)cnt;
     T.goff[t] = off;
@@ -1011,6 +1007,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];  // scene, pool brick, first particle, count
   DevScene &scm = w.scenes[bt.x];
   const DevScene &sc = scm;
+  if (sc.frozen) return;
   const int tid = threadIdx.x;
   const int lb = bt.y - sc.brick_begin;
   int c0x, c0y, c0z;
@@ -1170,6 +1167,7 @@ __global__ void k_p2g_node(World w, LaunchSet ls) {
   const int i = threadIdx.x;
   if (i >= t.z) return;
   const DevScene &sc = w.scenes[t.x];
+  if (sc.frozen) return;
   const int node = t.y + i;
   const int ns = w.N.slot_cnt[node];
   if (ns == 0) return;
@@ -1272,6 +1270,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
   const DevScene &sc = scm;
+  if (sc.frozen) return;
   const PPool &P = w.P;
   const int tid = threadIdx.x;
   const int lb = bt.y - sc.brick_begin;
@@ -1486,6 +1485,7 @@ __global__ void k_musl_node(World w, LaunchSet ls) {
   const int i = threadIdx.x;
   if (i >= t.z) return;
   const DevScene &sc = w.scenes[t.x];
+  if (sc.frozen) return;
   const int node = t.y + i;
   const int ns = w.N.slot_cnt[node];
   if (ns == 0) return;
@@ -1558,6 +1558,7 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
   const DevScene &sc = scm;
+  if (sc.frozen) return;
   const PPool &P = w.P;
   const int tid = threadIdx.x;
   const int lb = bt.y - sc.brick_begin;
@@ -1652,63 +1653,97 @@ __global__ void __launch_bounds__(BT, MB) k_fupd(World w, LaunchSet ls) {
 }
 
 // --------------------------------------------------------------------------
-// Material-material contact (Eq. 10-13).  Particles are binned by their
-// current-configuration cell into a world-wide hash; the cell edge is
-// 2 R_p + 2 dt max|v| + R_p/2, so every pair that can overlap this substep
-// (distance < 2 R_p + dt |v_p - v_q|) lies in neighbouring cells.  Each
-// bucket lists its particles by pool index, so every particle meets its
-// neighbours in a fixed order.  A pair is always evaluated in canonical
-// (lower, higher) pool-index order by both of its particles, so the two
-// impulses are exact negatives; the lower index owns the pair's tangential
-// history (double-buffered by substep parity).
+// Material-material contact (Eq. 10-13) with per-particle candidate lists.
+// Every particle keeps the particles of its scene that were within
+// r_l = 2 R_p + skin (skin = 1.5 R_p) at the lists' last build.  A pair in
+// contact this substep satisfies dist < 2 R_p + dt (|v_p| + |v_q|) (Eq. 10),
+// and a pair missing from the lists was farther than r_l at the build, so
+// its distance is at least r_l - d_p - d_q (d: displacement since the
+// build).  Hence the lists hold every pair that can touch while every
+// particle keeps d_p + dt |v_p| <= skin / 2; they are rebuilt (spatial hash
+// of the current configuration, cell = r_l) when one does not, or when the
+// state was written from outside.  A list is in (neighbour cell, pool index)
+// order, the same alone and in any batch.  A pair is always evaluated in
+// canonical (lower, higher) pool-index order by both of its particles, so
+// the two impulses are exact negatives; the lower index owns the pair's
+// tangential history (double-buffered by substep parity).
 // --------------------------------------------------------------------------
-__device__ __forceinline__ long long pack_cell(int cx, int cy, int cz) {
-  return ((long long)(cx + (1 << 20)) << 42) | ((long long)(cy + (1 << 20)) << 21) |
-         (long long)(cz + (1 << 20));
-}
-
 __device__ __forceinline__ int hash_cell(int scene, int cx, int cy, int cz, int nb) {
   const unsigned h = ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^
                      ((unsigned)cz * 83492791u) ^ ((unsigned)scene * 2654435761u);
   return (int)(h & (unsigned)(nb - 1));
 }
 
-__global__ void k_pair_clear(World w, LaunchSet ls) {
-  const int nb = w.H.n_buckets;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nb; i += gridDim.x * blockDim.x) {
-    w.H.bucket_start[i] = 0;
-    if (i < nb) w.H.bucket_fill[i] = 0;
-    if (i < ls.n_scenes) w.scenes[ls.scene_ids[i]].pair_vmax_bits = 0;
+// per-substep reset of the scenes' reductions and of the world's build flag
+__global__ void k_pair_reset(World w, LaunchSet ls) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *w.H.build = 0;
+  if (i < ls.n_scenes) {
+    DevScene &sc = w.scenes[ls.scene_ids[i]];
+    sc.pair_vmax_bits = 0;
+    sc.pair_disp_bits = 0;
   }
 }
 
-// per scene: largest particle speed (non-negative floats order like their bits)
+// per scene: largest particle speed, and largest displacement since the
+// candidate lists were built (non-negative floats order like their bits)
 __global__ void k_pair_vmax(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &sc = w.scenes[bt.x];
-  if (!sc.pair_on) return;
-  float m = 0.f;
+  if (!sc.pair_on || sc.frozen) return;
+  float m = 0.f, dm = 0.f;
+  const bool valid = sc.pair_valid != 0;
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
     const float a = w.P.v[0][p], b = w.P.v[1][p], c = w.P.v[2][p];
-    m = fmaxf(m, sqrtf(a * a + b * b + c * c));
+    const float sp = sqrtf(a * a + b * b + c * c);
+    m = fmaxf(m, sp);
+    if (valid) {
+      const float d0 = w.P.x[0][p] - w.P.xb[0][p], d1 = w.P.x[1][p] - w.P.xb[1][p],
+                  d2 = w.P.x[2][p] - w.P.xb[2][p];
+      dm = fmaxf(dm, sqrtf(d0 * d0 + d1 * d1 + d2 * d2) + sc.dt * sp);
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(FULL, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&sc.pair_vmax_bits, __float_as_int(m));
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_down_sync(FULL, m, o));
+    dm = fmaxf(dm, __shfl_down_sync(FULL, dm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (m > 0.f) atomicMax(&sc.pair_vmax_bits, __float_as_int(m));
+    if (dm > 0.f) atomicMax(&sc.pair_disp_bits, __float_as_int(dm));
+  }
 }
 
-__device__ __forceinline__ float pair_inv_h(const DevScene &sc) {
-  const float vmax = __int_as_float(sc.pair_vmax_bits);
-  return 1.0f / (2.5f * sc.Rp + 2.0f * sc.dt * vmax);
+// per scene: whether the candidate lists are rebuilt this substep
+__global__ void k_pair_decide(World w, LaunchSet ls) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ls.n_scenes) return;
+  DevScene &sc = w.scenes[ls.scene_ids[i]];
+  if (!sc.pair_on || sc.frozen) {
+    sc.pair_build = 0;
+    return;
+  }
+  const float reach = __int_as_float(sc.pair_disp_bits);  // max of d_p + dt |v_p|
+  const float skin = 1.5f * sc.Rp;
+  // 10% margin against rounding in the distances
+  const bool build = !sc.pair_valid || !(reach <= 0.45f * skin);
+  sc.pair_build = build ? 1 : 0;
+  if (build) {
+    sc.pair_h = 1.001f * (2.0f * sc.Rp + skin);
+    sc.pair_inv_h = 1.0f / sc.pair_h;
+    sc.pair_valid = 1;
+    sc.pair_builds++;
+    atomicOr(w.H.build, 1);
+  }
 }
 
 __global__ void k_pair_hash(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   const DevScene &sc = w.scenes[bt.x];
-  if (!sc.pair_on) return;
+  if (!sc.pair_on || !sc.pair_build) return;
   const PPool &P = w.P;
-  const float ih = pair_inv_h(sc);
+  const float ih = sc.pair_inv_h;
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
     const int cx = (int)floorf(P.x[0][p] * ih);
@@ -1716,12 +1751,12 @@ __global__ void k_pair_hash(World w, LaunchSet ls) {
     const int cz = (int)floorf(P.x[2][p] * ih);
     const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
     P.hkey[p] = b;
-    P.hcell[p] = pack_cell(cx, cy, cz);
     atomicAdd(&w.H.bucket_start[b], 1);
   }
 }
 
 __global__ void k_scan_local(World w) {
+  if (!*w.H.build) return;
   __shared__ int sm[33];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = i < w.H.n_buckets ? w.H.bucket_start[i] : 0;
@@ -1732,6 +1767,7 @@ __global__ void k_scan_local(World w) {
 }
 
 __global__ void k_scan_top(World w, int nblocks) {
+  if (!*w.H.build) return;
   __shared__ int sm[33];
   int carry = 0;
   for (int base = 0; base < nblocks; base += blockDim.x) {
@@ -1747,6 +1783,7 @@ __global__ void k_scan_top(World w, int nblocks) {
 }
 
 __global__ void k_scan_add(World w) {
+  if (!*w.H.build) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < w.H.n_buckets) w.H.bucket_start[i] += w.H.block_sum[blockIdx.x];
 }
@@ -1754,7 +1791,7 @@ __global__ void k_scan_add(World w) {
 __global__ void k_pair_fill(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   const DevScene &sc = w.scenes[bt.x];
-  if (!sc.pair_on) return;
+  if (!sc.pair_on || !sc.pair_build) return;
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
     const int b = w.P.hkey[p];
@@ -1762,8 +1799,10 @@ __global__ void k_pair_fill(World w, LaunchSet ls) {
   }
 }
 
-// order each bucket by pool index (buckets are short)
+// order each bucket by pool index (buckets are short), then lay out its
+// entries (position, pool index) for the list build
 __global__ void k_pair_sort(World w) {
+  if (!*w.H.build) return;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < w.H.n_buckets; b += gridDim.x * blockDim.x) {
     const int s0 = w.H.bucket_start[b], s1 = w.H.bucket_start[b + 1];
     for (int i = s0 + 1; i < s1; ++i) {
@@ -1775,20 +1814,112 @@ __global__ void k_pair_sort(World w) {
       }
       w.P.horder[j + 1] = key;
     }
+    for (int i = s0; i < s1; ++i) {
+      const int q = w.P.horder[i];
+      w.P.hent[i] = make_float4(w.P.x[0][q], w.P.x[1][q], w.P.x[2][q], __int_as_float(q));
+    }
   }
 }
 
+// candidate lists: every particle of the scene within r_l = 2 R_p + skin,
+// one warp per particle, lane l < 27 walking neighbour cell l (dz, dy, dx in
+// -1..1, x fastest) through the bucket's (position, index) entries; an entry
+// belongs to the cell when its position falls in it (the bucket's hash may
+// be shared).  Each lane keeps its first NKEEP candidates in registers (a
+// second walk writes the rest), a warp scan places them: the list is in
+// (cell, pool index) order.  The positions of the build are kept.
+#define NKEEP 8
+__global__ void k_pair_list(World w, LaunchSet ls) {
+  const int4 bt = ls.btiles[blockIdx.x];
+  DevScene &scm = w.scenes[bt.x];
+  const DevScene &sc = scm;
+  if (!sc.pair_on || !sc.pair_build) return;
+  const PPool &P = w.P;
+  const float ih = sc.pair_inv_h;
+  const float rl = 2.0f * sc.Rp + 1.5f * sc.Rp, rl2 = rl * rl;
+  const int pend = sc.p_begin + sc.n_p;
+  // the brick's particles are spread over gridDim.y CTAs of blockDim.x / 32 warps
+  const int lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.y;
+  const int wid = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+  bool over = false;
+  for (int i = wid; i < bt.w; i += nw) {
+    const int p = bt.z + i;
+    const float xp[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
+    const int cx = (int)floorf(xp[0] * ih) + dx, cy = (int)floorf(xp[1] * ih) + dy,
+              cz = (int)floorf(xp[2] * ih) + dz;
+    int k0 = 0, k1 = 0;
+    if (lane < 27) {
+      const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
+      k0 = w.H.bucket_start[b];
+      k1 = w.H.bucket_start[b + 1];
+    }
+    auto accept = [&](const float4 e) {
+      const int q = __float_as_int(e.w);
+      if (q == p || q < sc.p_begin || q >= pend) return false;
+      if ((int)floorf(e.x * ih) != cx || (int)floorf(e.y * ih) != cy || (int)floorf(e.z * ih) != cz)
+        return false;
+      const float d0 = xp[0] - e.x, d1 = xp[1] - e.y, d2 = xp[2] - e.z;
+      return d0 * d0 + d1 * d1 + d2 * d2 <= rl2;
+    };
+    int keep[NKEEP];
+    int cnt = 0;
+    // entries four at a time: the loads of a group are issued together
+    for (int k = k0; k < k1; k += 4) {
+      float4 e[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = k + u < k1 ? P.hent[k + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k + u >= k1 || !accept(e[u])) continue;
+#pragma unroll
+        for (int j = 0; j < NKEEP; ++j)
+          if (j == cnt) keep[j] = __float_as_int(e[u].w);
+        ++cnt;
+      }
+    }
+    int off = cnt;  // inclusive scan over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, off, o);
+      if (lane >= o) off += y;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= cnt;
+    int *lst = P.nbr + (size_t)p * BM_NBR;
+#pragma unroll
+    for (int j = 0; j < NKEEP; ++j)
+      if (j < cnt && off + j < BM_NBR) lst[off + j] = keep[j];
+    if (cnt > NKEEP) {  // the rest, by a second walk
+      int m = 0;
+      for (int k = k0; k < k1; ++k) {
+        const float4 e = P.hent[k];
+        if (!accept(e)) continue;
+        if (m >= NKEEP && off + m < BM_NBR) lst[off + m] = __float_as_int(e.w);
+        ++m;
+      }
+    }
+    if (lane == 0) {
+      P.nbr_n[p] = (uint8_t)min(total, BM_NBR);
+      P.xb[0][p] = xp[0];
+      P.xb[1][p] = xp[1];
+      P.xb[2][p] = xp[2];
+    }
+    over |= total > BM_NBR;
+  }
+  if (over) atomicOr(&scm.err, BM_ERRBIT_CONTACT_OVERFLOW);
+}
+
+// Pair impulses (Eq. 10-13), one thread per particle walking its list.
 __global__ void k_pair(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
   const DevScene &sc = scm;
-  if (!sc.pair_on) return;
+  if (!sc.pair_on || sc.frozen) return;
   const PPool &P = w.P;
   const int rb = (int)(sc.step & 1), wb = rb ^ 1;
   const float dt = sc.dt, R2 = 2.0f * sc.Rp;
   const float meff = sc.mp * sc.mp / (sc.mp + sc.mp);
-  const int pend = sc.p_begin + sc.n_p;
-  const float ih = pair_inv_h(sc);
   bool over = false;
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
@@ -1797,76 +1928,67 @@ __global__ void k_pair(World w, LaunchSet ls) {
     const uint32_t a1 = P.s1[p], a2 = P.s2[p];
     int bpx, bpy, bpz;
     particle_base(P.base[p], bpx, bpy, bpz);
-    const int cx = (int)floorf(xp[0] * ih);
-    const int cy = (int)floorf(xp[1] * ih);
-    const int cz = (int)floorf(xp[2] * ih);
     float J[3] = {0.f, 0.f, 0.f};
     int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const long long key = pack_cell(cx + dx, cy + dy, cz + dz);
-          const int b = hash_cell(bt.x, cx + dx, cy + dy, cz + dz, w.H.n_buckets);
-          const int e1 = w.H.bucket_start[b + 1];
-          for (int k = w.H.bucket_start[b]; k < e1; ++k) {
-            const int q = P.horder[k];
-            if (q == p || q < sc.p_begin || q >= pend || P.hcell[q] != key) continue;
-            const int lo = p < q ? p : q, hi = p < q ? q : p;
-            const float xl[3] = {P.x[0][lo], P.x[1][lo], P.x[2][lo]};
-            const float xh[3] = {P.x[0][hi], P.x[1][hi], P.x[2][hi]};
-            const float vl[3] = {P.v[0][lo], P.v[1][lo], P.v[2][lo]};
-            const float vh[3] = {P.v[0][hi], P.v[1][hi], P.v[2][hi]};
-            const float d[3] = {xl[0] - xh[0], xl[1] - xh[1], xl[2] - xh[2]};
-            const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (!(dist > 0.f)) continue;
-            const float id = 1.0f / dist;
-            const float n[3] = {d[0] * id, d[1] * id, d[2] * id};
-            const float vr[3] = {vl[0] - vh[0], vl[1] - vh[1], vl[2] - vh[2]};
-            const float vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
-            const float dhat = R2 - (dist + fminf(dt * vn, 0.0f));  // Eq. 10
-            if (!(dhat > 0.f)) continue;
-            int bqx, bqy, bqz;
-            particle_base(P.base[q], bqx, bqy, bqz);
-            const bool share = abs(bpx - bqx) <= 2 && abs(bpy - bqy) <= 2 && abs(bpz - bqz) <= 2;
-            if (share && !conflict(a1, a2, P.s1[q], P.s2[q])) continue;  // self-contact exclusion
-            const float fn = sc.s_n * meff / (dt * dt) * dhat;            // Eq. 11
-            float uh[3] = {0.f, 0.f, 0.f};
-            for (int h = 0; h < BM_HIST; ++h) {
-              const int pt = P.hist_partner[rb][(size_t)lo * BM_HIST + h];
-              if (pt < 0) break;
-              if (pt == hi) {
-                const float *u = P.hist_u[rb] + ((size_t)lo * BM_HIST + h) * 3;
-                uh[0] = u[0];
-                uh[1] = u[1];
-                uh[2] = u[2];
-                break;
-              }
-            }
-            float ft[3], un[3];
-            friction(uh, n, vr, fn, meff, dt, sc.gamma_k, sc.gamma_c, sc.pair_mu_s, sc.pair_mu_d, ft, un);
-            const float Jv[3] = {dt * (fn * n[0] + ft[0]), dt * (fn * n[1] + ft[1]),
-                                 dt * (fn * n[2] + ft[2])};
-            if (p == lo) {  // Eq. 13: +J on the lower index, -J on the higher
-              J[0] += Jv[0];
-              J[1] += Jv[1];
-              J[2] += Jv[2];
-              if (cnt < BM_HIST) {
-                P.hist_partner[wb][(size_t)p * BM_HIST + cnt] = hi;
-                float *u = P.hist_u[wb] + ((size_t)p * BM_HIST + cnt) * 3;
-                u[0] = un[0];
-                u[1] = un[1];
-                u[2] = un[2];
-                ++cnt;
-              } else {
-                over = true;
-              }
-            } else {
-              J[0] -= Jv[0];
-              J[1] -= Jv[1];
-              J[2] -= Jv[2];
-            }
-          }
+    const int n = P.nbr_n[p];
+    const int *lst = P.nbr + (size_t)p * BM_NBR;
+    for (int k = 0; k < n; ++k) {
+      const int q = lst[k];
+      const float xq[3] = {P.x[0][q], P.x[1][q], P.x[2][q]};
+      const float vq[3] = {P.v[0][q], P.v[1][q], P.v[2][q]};
+      const bool plo = p < q;
+      const int lo = plo ? p : q, hi = plo ? q : p;
+      const float *xl = plo ? xp : xq, *xh = plo ? xq : xp;
+      const float *vl = plo ? vp : vq, *vh = plo ? vq : vp;
+      const float d[3] = {xl[0] - xh[0], xl[1] - xh[1], xl[2] - xh[2]};
+      const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (!(dist > 0.f)) continue;
+      const float id = 1.0f / dist;
+      const float nn[3] = {d[0] * id, d[1] * id, d[2] * id};
+      const float vr[3] = {vl[0] - vh[0], vl[1] - vh[1], vl[2] - vh[2]};
+      const float vn = vr[0] * nn[0] + vr[1] * nn[1] + vr[2] * nn[2];
+      const float dhat = R2 - (dist + fminf(dt * vn, 0.0f));  // Eq. 10
+      if (!(dhat > 0.f)) continue;
+      int bqx, bqy, bqz;
+      particle_base(P.base[q], bqx, bqy, bqz);
+      const bool share = abs(bpx - bqx) <= 2 && abs(bpy - bqy) <= 2 && abs(bpz - bqz) <= 2;
+      if (share && !conflict(a1, a2, P.s1[q], P.s2[q])) continue;  // self-contact exclusion
+      const float fn = sc.s_n * meff / (dt * dt) * dhat;            // Eq. 11
+      float uh[3] = {0.f, 0.f, 0.f};
+      for (int h = 0; h < BM_HIST; ++h) {
+        const int pt = P.hist_partner[rb][(size_t)lo * BM_HIST + h];
+        if (pt < 0) break;
+        if (pt == hi) {
+          const float *u = P.hist_u[rb] + ((size_t)lo * BM_HIST + h) * 3;
+          uh[0] = u[0];
+          uh[1] = u[1];
+          uh[2] = u[2];
+          break;
         }
+      }
+      float ft[3], un[3];
+      friction(uh, nn, vr, fn, meff, dt, sc.gamma_k, sc.gamma_c, sc.pair_mu_s, sc.pair_mu_d, ft, un);
+      const float Jv[3] = {dt * (fn * nn[0] + ft[0]), dt * (fn * nn[1] + ft[1]), dt * (fn * nn[2] + ft[2])};
+      if (plo) {  // Eq. 13: +J on the lower index, -J on the higher
+        J[0] += Jv[0];
+        J[1] += Jv[1];
+        J[2] += Jv[2];
+        if (cnt < BM_HIST) {
+          P.hist_partner[wb][(size_t)p * BM_HIST + cnt] = hi;
+          float *u = P.hist_u[wb] + ((size_t)p * BM_HIST + cnt) * 3;
+          u[0] = un[0];
+          u[1] = un[1];
+          u[2] = un[2];
+          ++cnt;
+        } else {
+          over = true;
+        }
+      } else {
+        J[0] -= Jv[0];
+        J[1] -= Jv[1];
+        J[2] -= Jv[2];
+      }
+    }
     if (cnt < BM_HIST) P.hist_partner[wb][(size_t)p * BM_HIST + cnt] = -1;
     P.J[0][p] = J[0];
     P.J[1][p] = J[1];
@@ -2013,6 +2135,10 @@ __global__ void k_get_wrenches(World w, const int *ids, int n, double *out) {
 __global__ void k_tool(World w, LaunchSet ls) {
   const int sid = ls.scene_ids[blockIdx.x];
   DevScene &sc = w.scenes[sid];
+  if (sc.frozen) {  // a scene that has taken its substeps: nothing moves, nothing to rebuild
+    if (threadIdx.x == 0) sc.need_rebuild = 0;
+    return;
+  }
   __shared__ double sm[32];
   // reduce this substep's per-brick wrench partials in brick order
   double W[6];
@@ -2076,6 +2202,7 @@ __global__ void k_tool(World w, LaunchSet ls) {
     if (sc.cut >= 0) sc.cur_cut = sc.cut;
   }
   sc.step++;
+  if (sc.stop_at >= 0 && sc.step >= sc.stop_at) sc.frozen = 1;
   prepare_substep(sc);
 }
 
@@ -2084,53 +2211,82 @@ __global__ void k_tool(World w, LaunchSet ls) {
 // --------------------------------------------------------------------------
 
 
+// Distinct codes at every node of a node tile.  Nodes next to a newly
+// labelled particle (dirty) are recounted, the others keep their distinct
+// codes from the last rebuild.  A recount takes one warp per node: lane l <
+// 27 holds base cell (i - l % 3, j - l / 3 % 3, k - l / 9) of the node's
+// stencil, and the node's codes are found in ascending order of the key
+// (mask2 << 32 | mask1) as repeated warp-wide minima over the lanes' particles
+// of the keys above the last one found.
 __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   const int4 t = ls.ntiles[blockIdx.x];
   DevScene &sc = w.scenes[t.x];
   if (!force && !sc.need_rebuild) return;
   __shared__ int sm[33];
+  __shared__ int dlist[512];   // node tile <= 512 nodes
+  __shared__ int dcnt[512];
+  __shared__ int ndirty;
   const int i = threadIdx.x;
-  int cnt = 0;
   const int node = t.y + i;
-  int ix = 0, iy = 0, iz = 0;
-  bool recount = force != 0;
-  if (i < t.z) {
-    node_coords(sc, node - sc.node_begin, ix, iy, iz);
-    // only nodes next to a newly labelled particle are recounted; the others
-    // keep their distinct codes from the last rebuild
-    recount |= w.N.dirty[node] != 0;
-  }
-  if (i < t.z && !recount) cnt = w.N.ncodes[node];
-  else if (i < t.z) {
-    const int *cs = w.N.cell_start + sc.cell_begin;
-    unsigned long long keys[BM_MAXS];
+  bool recount = false;
+  if (i < t.z) recount = force != 0 || w.N.dirty[node] != 0;
+  if (i == 0) ndirty = 0;
+  __syncthreads();
+  if (recount) dlist[atomicAdd(&ndirty, 1)] = i;
+  __syncthreads();
+  const int lane = i & 31, wid = i >> 5, nw = blockDim.x >> 5;
+  const int *cs = w.N.cell_start + sc.cell_begin;
+  for (int j = wid; j < ndirty; j += nw) {
+    const int li = dlist[j];
+    const int nd = t.y + li;
+    int ix, iy, iz;
+    node_coords(sc, nd - sc.node_begin, ix, iy, iz);
+    int p0 = 0, p1 = 0;
+    if (lane < 27) {
+      const int bx = ix - lane % 3, by = iy - (lane / 3) % 3, bz = iz - lane / 9;
+      if (bx >= 0 && by >= 0 && bz >= 0 && bx < sc.nb[0] && by < sc.nb[1] && bz < sc.nb[2]) {
+        const int c = cell_index(sc, bx, by, bz);
+        p0 = cs[c];
+        p1 = cs[c + 1];
+      }
+    }
+    int cnt = 0;
     bool over = false;
-    for (int oz = 0; oz < 3; ++oz)
-      for (int oy = 0; oy < 3; ++oy)
-        for (int ox = 0; ox < 3; ++ox) {
-          const int bx = ix - ox, by = iy - oy, bz = iz - oz;
-          if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) continue;
-          const int c = cell_index(sc, bx, by, bz);
-          for (int p = cs[c]; p < cs[c + 1]; ++p) {
-            const unsigned long long k = ((unsigned long long)w.P.s2[p] << 32) | w.P.s1[p];
-            int j = 0;
-            while (j < cnt && keys[j] < k) ++j;
-            if (j < cnt && keys[j] == k) continue;
-            if (cnt == BM_MAXS) {
-              over = true;
-              continue;
-            }
-            for (int q = cnt; q > j; --q) keys[q] = keys[q - 1];
-            keys[j] = k;
-            ++cnt;
-          }
-        }
-    if (over) atomicOr(&sc.err, BM_ERRBIT_SLOT_OVERFLOW);
-    w.N.ncodes[node] = (uint8_t)cnt;
-    w.N.dirty[node] = 0;
-    for (int a = 0; a < cnt; ++a)
-      w.N.tmp_codes[(size_t)node * BM_MAXS + a] = make_uint2((uint32_t)keys[a], (uint32_t)(keys[a] >> 32));
+    unsigned long long last = 0;
+    bool first = true;
+    for (;;) {
+      unsigned long long m = ~0ull;
+      for (int p = p0; p < p1; ++p) {
+        const unsigned long long k = ((unsigned long long)w.P.s2[p] << 32) | w.P.s1[p];
+        if ((first || k > last) && k < m) m = k;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(FULL, m, o);
+        m = y < m ? y : m;
+      }
+      if (m == ~0ull) break;
+      if (cnt < BM_MAXS) {
+        if (lane == 0)
+          w.N.tmp_codes[(size_t)nd * BM_MAXS + cnt] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+        ++cnt;
+      } else {
+        over = true;
+        break;
+      }
+      last = m;
+      first = false;
+    }
+    if (lane == 0) {
+      if (over) atomicOr(&sc.err, BM_ERRBIT_SLOT_OVERFLOW);
+      w.N.ncodes[nd] = (uint8_t)cnt;
+      w.N.dirty[nd] = 0;
+      dcnt[li] = cnt;
+    }
   }
+  __syncthreads();
+  int cnt = 0;
+  if (i < t.z) cnt = recount ? dcnt[i] : w.N.ncodes[node];
   if (i < t.z) w.N.slot_cnt[node] = (uint8_t)cnt;
   int total;
   block_excl_scan(cnt, sm, total);
@@ -2207,15 +2363,29 @@ __global__ void k_slot_fill(World w, LaunchSet ls, int force) {
   int total;
   const int ex = block_excl_scan(cnt, sm, total);
   if (i < t.z) {
-    const int off = w.N.tile_sum[t.w] + ex;
-    if (off + cnt > sc.slot_cap) {
+    int off = w.N.tile_sum[t.w] + ex;
+    const bool fits = off + cnt <= sc.slot_cap;
+    if (!fits) {
       w.N.slot_cnt[node] = 0;
-      w.N.slot_off[node] = sc.slot_begin;
-      return;
+      off = 0;
+    } else {
+      for (int a = 0; a < cnt; ++a)
+        w.S.code[sc.slot_begin + off + a] = w.N.tmp_codes[(size_t)node * BM_MAXS + a];
     }
     w.N.slot_off[node] = sc.slot_begin + off;
-    for (int a = 0; a < cnt; ++a)
-      w.S.code[sc.slot_begin + off + a] = w.N.tmp_codes[(size_t)node * BM_MAXS + a];
+    // the node's first slot in the tile table of every brick whose tile covers it
+    int ix, iy, iz, x0, x1, y0, y1, z0, z1;
+    node_coords(sc, node - sc.node_begin, ix, iy, iz);
+    covering(ix, sc.nbr[0], x0, x1);
+    covering(iy, sc.nbr[1], y0, y1);
+    covering(iz, sc.nbr[2], z0, z1);
+    for (int Bz = z0; Bz <= z1; ++Bz)
+      for (int By = y0; By <= y1; ++By)
+        for (int Bx = x0; Bx <= x1; ++Bx) {
+          const int b = sc.brick_begin + (Bz * sc.nbr[1] + By) * sc.nbr[0] + Bx;
+          const int tt = ((iz - Bz * BR) * TE + (iy - By * BR)) * TE + (ix - Bx * BR);
+          w.B.tgoff[(size_t)b * TN + tt] = sc.slot_begin + off;
+        }
   }
 }
 
@@ -2318,7 +2488,7 @@ const char *const bm_kernel_names[BM_NUM_KERNELS] = {
     "k_p2g_brick", "k_p2g_node", "k_g2p_musl", "k_musl_node", "k_fupd",
     "k_tool", "k_slot_count", "k_slot_scan", "k_slot_fill", "k_brick_tiles",
     "k_pair_clear", "k_pair_hash", "k_scan_local", "k_scan_top", "k_scan_add", "k_pair_fill",
-    "k_pair_sort", "k_pair", "k_pre"};
+    "k_pair_sort", "k_pair", "k_pair_list"};
 
 // ev (optional): 2 * BM_NUM_KERNELS events recorded around each launch
 static inline void rec(cudaEvent_t *ev, int k, int after, cudaStream_t st) {
@@ -2347,25 +2517,35 @@ cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t 
   return launch_rebuild(w, ls, st, force, nullptr);
 }
 
-// Brick-kernel occupancy variants (minimum resident CTAs per SM of
-// k_p2g_brick, k_g2p_musl, k_fupd): fewer CTAs leave more registers per
-// thread, more CTAs hide more latency.  The arithmetic is the same in every
+// Brick-kernel occupancy: the minimum resident CTAs per SM each brick kernel
+// is compiled for (launch bounds), chosen per kernel (fewer CTAs leave more
+// registers per thread, more CTAs hide more latency).  A launch variant v in [0, 27) picks choice
+// v % 3 for k_p2g_brick, (v / 3) % 3 for k_g2p_musl and v / 9 for k_fupd;
+// choice 0 is each kernel's default.  The arithmetic is the same in every
 // variant, so results are bit-identical; the batch autotuner picks one.
-template <int V> struct Occ;
-template <> struct Occ<0> { static constexpr int p2g = 3, g2p = 5, fupd = 7; };
-template <> struct Occ<1> { static constexpr int p2g = 2, g2p = 4, fupd = 5; };
-template <> struct Occ<2> { static constexpr int p2g = 4, g2p = 6, fupd = 8; };
+template <int C> struct OccP2G;
+template <> struct OccP2G<0> { static constexpr int v = 3; };
+template <> struct OccP2G<1> { static constexpr int v = 2; };
+template <> struct OccP2G<2> { static constexpr int v = 4; };
+template <int C> struct OccG2P;
+template <> struct OccG2P<0> { static constexpr int v = 5; };
+template <> struct OccG2P<1> { static constexpr int v = 4; };
+template <> struct OccG2P<2> { static constexpr int v = 6; };
+template <int C> struct OccFupd;
+template <> struct OccFupd<0> { static constexpr int v = 7; };
+template <> struct OccFupd<1> { static constexpr int v = 5; };
+template <> struct OccFupd<2> { static constexpr int v = 8; };
 
-template <int PPC, int V>
+template <int PPC, int C>
 static cudaError_t set_smem_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC, Occ<V>::p2g, false>,
+  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC, OccP2G<C>::v, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(K2S<PPC>));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_p2g_brick<PPC, Occ<V>::p2g, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_p2g_brick<PPC, OccP2G<C>::v, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(K2S<PPC>));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_g2p_musl<PPC, Occ<V>::g2p>,
+  return cudaFuncSetAttribute(k_g2p_musl<PPC, OccG2P<C>::v>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K4S<PPC>));
 }
 
@@ -2387,26 +2567,48 @@ cudaError_t bm_kernels_init() {
   return e;
 }
 
-template <int PPC, int V>
-static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
-  rec(ev, 0, 0, st);
+template <int PPC, int C>
+static void launch_p2g(const World &w, const LaunchSet &ls, cudaStream_t st) {
   if (ls.any_inelastic)
-    k_p2g_brick<PPC, Occ<V>::p2g, true><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+    k_p2g_brick<PPC, OccP2G<C>::v, true><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
   else
-    k_p2g_brick<PPC, Occ<V>::p2g, false><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+    k_p2g_brick<PPC, OccP2G<C>::v, false><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+}
+
+template <int PPC, int C>
+static void launch_g2p(const World &w, const LaunchSet &ls, cudaStream_t st) {
+  k_g2p_musl<PPC, OccG2P<C>::v><<<ls.n_btiles, BT, sizeof(K4S<PPC>), st>>>(w, ls);
+}
+
+template <int C>
+static void launch_fupd(const World &w, const LaunchSet &ls, cudaStream_t st) {
+  if (ls.any_inelastic) k_fupd<OccFupd<C>::v, true><<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  else k_fupd<OccFupd<C>::v, false><<<ls.n_btiles, BT, 0, st>>>(w, ls);
+}
+
+template <int PPC>
+static void launch_bricks(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
+  const int cp = ls.variant % 3, cg = (ls.variant / 3) % 3, cf = ls.variant / 9;
+  rec(ev, 0, 0, st);
+  if (cp == 0) launch_p2g<PPC, 0>(w, ls, st);
+  else if (cp == 1) launch_p2g<PPC, 1>(w, ls, st);
+  else launch_p2g<PPC, 2>(w, ls, st);
   rec(ev, 0, 1, st);
   rec(ev, 1, 0, st);
   k_p2g_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 1, 1, st);
   rec(ev, 2, 0, st);
-  k_g2p_musl<PPC, Occ<V>::g2p><<<ls.n_btiles, BT, sizeof(K4S<PPC>), st>>>(w, ls);
+  if (cg == 0) launch_g2p<PPC, 0>(w, ls, st);
+  else if (cg == 1) launch_g2p<PPC, 1>(w, ls, st);
+  else launch_g2p<PPC, 2>(w, ls, st);
   rec(ev, 2, 1, st);
   rec(ev, 3, 0, st);
   k_musl_node<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls);
   rec(ev, 3, 1, st);
   rec(ev, 4, 0, st);
-  if (ls.any_inelastic) k_fupd<Occ<V>::fupd, true><<<ls.n_btiles, BT, 0, st>>>(w, ls);
-  else k_fupd<Occ<V>::fupd, false><<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  if (cf == 0) launch_fupd<0>(w, ls, st);
+  else if (cf == 1) launch_fupd<1>(w, ls, st);
+  else launch_fupd<2>(w, ls, st);
   rec(ev, 4, 1, st);
 }
 
@@ -2414,8 +2616,11 @@ static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, c
   const int nb = w.H.n_buckets;
   const int nblk = (nb + 1023) / 1024;
   rec(ev, 10, 0, st);
-  k_pair_clear<<<(nb + 1 + 255) / 256, 256, 0, st>>>(w, ls);
+  k_pair_reset<<<(ls.n_scenes + 255) / 256, 256, 0, st>>>(w, ls);
   k_pair_vmax<<<ls.n_btiles, BT, 0, st>>>(w, ls);
+  k_pair_decide<<<(ls.n_scenes + 63) / 64, 64, 0, st>>>(w, ls);
+  cudaMemsetAsync(w.H.bucket_start, 0, sizeof(int) * ((size_t)nb + 1), st);
+  cudaMemsetAsync(w.H.bucket_fill, 0, sizeof(int) * (size_t)nb, st);
   rec(ev, 10, 1, st);
   rec(ev, 11, 0, st);
   k_pair_hash<<<ls.n_btiles, BT, 0, st>>>(w, ls);
@@ -2435,6 +2640,9 @@ static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, c
   rec(ev, 16, 0, st);
   k_pair_sort<<<(nb + 255) / 256, 256, 0, st>>>(w);
   rec(ev, 16, 1, st);
+  rec(ev, 18, 0, st);
+  k_pair_list<<<dim3(ls.n_btiles, 4), 128, 0, st>>>(w, ls);
+  rec(ev, 18, 1, st);
   rec(ev, 17, 0, st);
   k_pair<<<ls.n_btiles, 128, 0, st>>>(w, ls);
   rec(ev, 17, 1, st);
@@ -2443,14 +2651,8 @@ static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, c
 cudaError_t bm_launch_substep_ev(const World &w, const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
   if (ls.n_btiles == 0) return cudaSuccess;
   if (ls.any_pair && w.H.n_buckets > 0) launch_pairs(w, ls, st, ev);
-  switch (ls.variant * 2 + (ls.ppc16 ? 1 : 0)) {
-    case 0: launch_bricks<8, 0>(w, ls, st, ev); break;
-    case 1: launch_bricks<16, 0>(w, ls, st, ev); break;
-    case 2: launch_bricks<8, 1>(w, ls, st, ev); break;
-    case 3: launch_bricks<16, 1>(w, ls, st, ev); break;
-    case 4: launch_bricks<8, 2>(w, ls, st, ev); break;
-    default: launch_bricks<16, 2>(w, ls, st, ev); break;
-  }
+  if (ls.ppc16) launch_bricks<16>(w, ls, st, ev);
+  else launch_bricks<8>(w, ls, st, ev);
   rec(ev, 5, 0, st);
   k_tool<<<ls.n_scenes, 256, 0, st>>>(w, ls);
   rec(ev, 5, 1, st);

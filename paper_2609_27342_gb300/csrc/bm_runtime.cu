@@ -201,7 +201,6 @@ int world_alloc(WorldH *W) {
   }
   for (int k = 0; k < 9; ++k) {
     F(pp.F[k], P);
-    F(pp.A[k], P);
     F(pp.Fpi[k], P);
     F(pp.Fdot[k], P);
   }
@@ -214,13 +213,17 @@ int world_alloc(WorldH *W) {
   ok &= pp.pend != nullptr;
   if (W->pair) {
     I(pp.hkey, P);
-    pp.hcell = W->get<long long>(P);
-    ok &= pp.hcell != nullptr;
     I(pp.horder, P);
+    pp.hent = W->get<float4>(P);
+    ok &= pp.hent != nullptr;
     for (int b = 0; b < 2; ++b) {
       I(pp.hist_partner[b], P * BM_HIST);
       F(pp.hist_u[b], P * BM_HIST * 3);
     }
+    I(pp.nbr, P * BM_NBR);
+    pp.nbr_n = W->get<uint8_t>(P);
+    ok &= pp.nbr_n != nullptr;
+    for (int a = 0; a < 3; ++a) F(pp.xb[a], P);
     int nb = 1024;
     while (nb < 2 * P && nb < (1 << 28)) nb <<= 1;
     HashPool &H = W->w.H;
@@ -228,6 +231,7 @@ int world_alloc(WorldH *W) {
     I(H.bucket_start, (int64_t)nb + 1);
     I(H.bucket_fill, nb);
     I(H.block_sum, nb / 1024 + 1);
+    I(H.build, 1);
   }
   NPool &np = W->w.N;
   I(np.cell_start, W->cap_cell);
@@ -251,7 +255,8 @@ int world_alloc(WorldH *W) {
   bp.poff = W->get<int>(W->cap_brick);
   bp.ptot = W->get<int>(W->cap_brick);
   bp.tdesc = W->get<int>(W->cap_brick * BM_TILE_NODES);
-  ok &= bp.pm && bp.pd && bp.poff && bp.ptot && bp.tdesc;
+  bp.tgoff = W->get<int>(W->cap_brick * BM_TILE_NODES);
+  ok &= bp.pm && bp.pd && bp.poff && bp.ptot && bp.tdesc && bp.tgoff;
   W->w.scenes = W->get<DevScene>(W->cap_scenes);
   W->w.wpart = W->get<double>(W->cap_brick * 6);
   W->w.whist = W->get<double>(std::max<int64_t>(W->cap_hist, 1) * 6);
@@ -364,6 +369,7 @@ void fill_template(bm_scene_s *s) {
   const bm_scene_desc &d = s->desc;
   DevScene &t = s->tmpl;
   std::memset(&t, 0, sizeof t);
+  t.stop_at = -1;  // no stop substep: the scene advances with every step call
   t.nb[0] = s->nb[0]; t.nb[1] = s->nb[1]; t.nb[2] = s->nb[2];
   t.nn[0] = s->nn[0]; t.nn[1] = s->nn[1]; t.nn[2] = s->nn[2];
   t.nbr[0] = s->nbr[0]; t.nbr[1] = s->nbr[1]; t.nbr[2] = s->nbr[2];
@@ -650,12 +656,18 @@ int move_scene(bm_scene_s *s, WorldH *W) {
         CK(cudaMemsetAsync(B.hist_partner[b] + pd * BM_HIST, 0xff, sizeof(int) * n * BM_HIST, st));
       }
     }
+    if (S->pair) {  // the contact candidate lists move along (rebased below)
+      CK(cp(B.nbr + pd * BM_NBR, A.nbr + ps * BM_NBR, sizeof(int) * n * BM_NBR));
+      CK(cp(B.nbr_n + pd, A.nbr_n + ps, n));
+      for (int a = 0; a < 3; ++a) CK(cp(B.xb[a] + pd, A.xb[a] + ps, sizeof(float) * n));
+    }
   }
   if (s->hist_cap) CK(cp(W->w.whist + s->hist_begin * 6, S->w.whist + old.hist_begin * 6, sizeof(double) * 6 * s->hist_cap));
   CK(cudaStreamSynchronize(st));
   int r = upload_cell_start(W, s);
   if (r) return r;
-  // partner indices of the pair history are pool indices: rebase them
+  // partner indices of the pair history and the contact candidates are pool
+  // indices: rebase them
   if (W->pair && S->pair && pd != ps) {
     std::vector<int> h((size_t)n * BM_HIST);
     for (int b = 0; b < 2; ++b) {
@@ -664,10 +676,15 @@ int move_scene(bm_scene_s *s, WorldH *W) {
         if (q >= 0) q = q - (int)ps + (int)pd;
       CK(cudaMemcpy(B.hist_partner[b] + pd * BM_HIST, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice));
     }
+    std::vector<int> nb((size_t)n * BM_NBR);
+    CK(cudaMemcpy(nb.data(), B.nbr + pd * BM_NBR, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
+    for (auto &q : nb) q = q - (int)ps + (int)pd;  // entries beyond a count are never read
+    CK(cudaMemcpy(B.nbr + pd * BM_NBR, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
   }
   set_ranges(s, cur);
   cur.slot_cap = (int)s->slot_cap;
   cur.label_pending = 0;
+  if (!(W->pair && S->pair)) cur.pair_valid = 0;  // no lists came along: build them on the next substep
   CK(cudaMemcpy(W->w.scenes + s->slot, &cur, sizeof cur, cudaMemcpyHostToDevice));
   // leave the old world
   auto &mem = S->members;
@@ -947,6 +964,8 @@ int bm_add_blade(bm_scene_t s, const bm_blade_desc *b, int *blade_id) {
   t.err = cur.err;
   t.n_slots = cur.n_slots;
   t.need_rebuild = cur.need_rebuild;
+  t.stop_at = cur.stop_at;
+  t.frozen = cur.frozen;
   CK(cudaMemcpy(W->w.scenes + s->slot, &t, sizeof t, cudaMemcpyHostToDevice));
   LaunchSet ls = scene_set(W, s);
   CK(bm_launch_prepare(W->w, ls, W->st));
@@ -990,6 +1009,24 @@ int bm_step(bm_scene_t s, int n_substeps) {
   }
   LaunchSet ls = scene_set(W, s);
   for (int k = 0; k < n_substeps; ++k) CK(bm_launch_substep(W->w, ls, W->st));
+  return BM_OK;
+}
+
+int bm_scene_set_stop(bm_scene_t s, int64_t stop_at) {
+  if (!valid_scene(s) || stop_at < -1) return fail(BM_E_INVALID, "bad scene or stop substep");
+  WorldH *W = s->world;
+  CK(cudaStreamSynchronize(W->st));
+  long long step = 0;
+  CK(cudaMemcpy(&step, (char *)(W->w.scenes + s->slot) + offsetof(DevScene, step), sizeof step,
+                cudaMemcpyDeviceToHost));
+  struct {
+    long long stop_at;
+    int frozen;
+  } v{(long long)stop_at, (stop_at >= 0 && step >= stop_at) ? 1 : 0};
+  static_assert(offsetof(DevScene, frozen) == offsetof(DevScene, stop_at) + sizeof(long long),
+                "stop_at and frozen are adjacent");
+  CK(cudaMemcpy((char *)(W->w.scenes + s->slot) + offsetof(DevScene, stop_at), &v,
+                sizeof(long long) + sizeof(int), cudaMemcpyHostToDevice));
   return BM_OK;
 }
 
@@ -1057,6 +1094,11 @@ int bm_write_state(bm_scene_t s, uint32_t field_mask, const void *const *src, in
     CK(e);
     if (f == 7 || f == 8) masks = true;
   }
+  if (s->desc.pair_contact && (field_mask & BM_FIELD_x)) {  // positions moved: rebuild the contact candidates
+    const int zero = 0;
+    CK(cudaMemcpy((char *)(W->w.scenes + s->slot) + offsetof(DevScene, pair_valid), &zero, sizeof zero,
+                  cudaMemcpyHostToDevice));
+  }
   if (masks) {
     CK(bm_launch_rebuild(W->w, scene_set(W, s), W->st, 1));
     CK(cudaStreamSynchronize(W->st));
@@ -1102,11 +1144,17 @@ std::vector<CkSection> ck_layout(const bm_scene_s *s, size_t *total) {
   for (int a = 0; a < 3; ++a) add(P.ut[a] + pb, sizeof(float) * n);
   add(P.s1 + pb, sizeof(uint32_t) * n);
   add(P.s2 + pb, sizeof(uint32_t) * n);
-  if (s->desc.pair_contact)
+  if (s->desc.pair_contact) {
     for (int b = 0; b < 2; ++b) {
       add(P.hist_partner[b] + pb * BM_HIST, sizeof(int) * n * BM_HIST);
       add(P.hist_u[b] + pb * BM_HIST * 3, sizeof(float) * n * BM_HIST * 3);
     }
+    // the contact candidate lists and their build positions: a restore then
+    // continues with the same lists, so the next substeps repeat bit for bit
+    add(P.nbr + pb * BM_NBR, sizeof(int) * n * BM_NBR);
+    add(P.nbr_n + pb, n);
+    for (int a = 0; a < 3; ++a) add(P.xb[a] + pb, sizeof(float) * n);
+  }
   if (s->hist_cap) add(s->world->w.whist + s->hist_begin * 6, sizeof(double) * 6 * s->hist_cap);
   *total = off;
   return v;
@@ -1158,7 +1206,8 @@ int bm_checkpoint_restore(bm_scene_t s, const void *src, int src_on_device) {
   const PPool &P = W->w.P;
   CK(cudaMemsetAsync(P.pend + s->p_begin, 0, s->n, W->st));
   CK(cudaStreamSynchronize(W->st));
-  // pair-history partners are pool indices of the world the save was made in
+  // pair-history partners and contact candidates are pool indices of the
+  // world the save was made in
   if (s->desc.pair_contact && h.p_begin != s->p_begin) {
     std::vector<int> q((size_t)s->n * BM_HIST);
     for (int b = 0; b < 2; ++b) {
@@ -1168,11 +1217,18 @@ int bm_checkpoint_restore(bm_scene_t s, const void *src, int src_on_device) {
         if (v >= 0) v = v - (int)h.p_begin + (int)s->p_begin;
       CK(cudaMemcpy(ptr, q.data(), sizeof(int) * q.size(), cudaMemcpyHostToDevice));
     }
+    std::vector<int> nb((size_t)s->n * BM_NBR);
+    int *np = P.nbr + s->p_begin * BM_NBR;
+    CK(cudaMemcpy(nb.data(), np, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
+    for (auto &v : nb) v = v - (int)h.p_begin + (int)s->p_begin;  // entries beyond a count are never read
+    CK(cudaMemcpy(np, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
   }
   set_ranges(s, sv);
   sv.slot_cap = cur.slot_cap;
   sv.label_pending = 0;
   sv.need_rebuild = 0;
+  sv.stop_at = cur.stop_at;  // the stop substep is a control of the caller's, not state
+  sv.frozen = (sv.stop_at >= 0 && sv.step >= sv.stop_at) ? 1 : 0;
   CK(cudaMemcpy(W->w.scenes + s->slot, &sv, sizeof sv, cudaMemcpyHostToDevice));
   CK(bm_launch_rebuild(W->w, scene_set(W, s), W->st, 1));
   CK(cudaStreamSynchronize(W->st));
@@ -1365,6 +1421,7 @@ int bm_scene_info_get(bm_scene_t s, bm_scene_info *out) {
   out->step = cur.step;
   out->error_bits = cur.err;
   out->current_cut = cur.cur_cut;
+  out->contact_list_builds = cur.pair_builds;
   for (int a = 0; a < 3; ++a) {
     out->grid_lo[a] = s->lo[a];
     out->grid_dim[a] = s->nn[a];
@@ -1425,10 +1482,13 @@ int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
   if (particles) *particles = n;
   if (nodes) *nodes = s.n_node;
   if (bricks) *bricks = s.n_brick;
-  // fx, x, v, u_t, J (3 each); F, A, Fp^-1, dF/dt (9 each); D; base, masks, perm; pending label
-  const int64_t per_p = 4 * (3 * 5 + 9 * 4 + 1) + 4 * 4 + 1 + (desc->pair_contact ? (3 * 4 + 2 * BM_HIST * 16) : 0);
+  // fx, x, v, u_t, J (3 each); F, Fp^-1, dF/dt (9 each); D; base, masks, perm; pending label;
+  // with pair contact: hash key, order and entries, the double-buffered history,
+  // the candidate list and the positions at its build
+  const int64_t per_p = 4 * (3 * 5 + 9 * 3 + 1) + 4 * 4 + 1 +
+                        (desc->pair_contact ? (4 + 4 + 16 + 2 * BM_HIST * 16 + 4 * BM_NBR + 1 + 12) : 0);
   const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (3 * 16 + 8) + 6 * 32;
-  const int64_t per_brick = 2 * BM_TILE_NODES + 48 + 16 + 8;
+  const int64_t per_brick = 3 * BM_TILE_NODES + 48 + 16 + 8;
   if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.n_brick * per_brick + s.hist_cap * 48;
   return BM_OK;
 }
@@ -1534,7 +1594,7 @@ int bm_batch_set_tiles(bm_batch_t b, int graph_chunk, int node_tile, int brick_v
   if (graph_chunk < 1 || graph_chunk > 256 || node_tile < 64 || node_tile > 512 || node_tile % 32 ||
       brick_variant < 0 || brick_variant >= BM_NUM_VARIANTS)
     return fail(BM_E_INVALID, "graph chunk in [1, 256]; node tile a multiple of 32 in [64, 512]; "
-                              "brick variant in [0, 2]");
+                              "brick variant in [0, 26]");
   WorldH *W = b->world;
   CK(cudaStreamSynchronize(W->st));
   W->graph_chunk = graph_chunk;

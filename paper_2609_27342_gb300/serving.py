@@ -56,10 +56,18 @@ class Server:
 
     ``budget_bytes`` bounds the device memory of admitted scenes (footprints
     from bm_scene_footprint); the batch pools are sized from it once.
-    ``max_chunk`` bounds the substeps run between admission points;
-    ``node_tile`` and ``brick_variant`` are the launch shape (for instance an
-    autotuned one; results do not depend on it).  ``allocator`` (a
-    ``TorchAllocator``) makes PyTorch's caching allocator own the batch pools.
+    ``max_chunk`` is the number of substeps the batch advances between
+    admission points: every admitted scene carries a stop substep
+    (bm_scene_set_stop) at its request's length, so a request that ends
+    inside a chunk stops there on the device, exactly, and is retired at the
+    chunk's end while the others run the whole chunk.  ``node_tile`` and
+    ``brick_variant`` are the launch shape (for instance an autotuned one;
+    results do not depend on it).  ``allocator`` (a ``TorchAllocator``) makes
+    PyTorch's caching allocator own the batch pools.
+
+    While a chunk runs on the GPU the host computes the footprints of queued
+    requests (the admission test) in a worker thread, so admission at the
+    next chunk boundary only places the scene.
     """
 
     # pool capacity per budget byte (particles, nodes): a scene's footprint is
@@ -86,7 +94,11 @@ class Server:
         self.step_ms: List[float] = []      # ms per batched substep, one sample per chunk
         self.step_weight: List[int] = []    # substeps in that chunk
         self.particle_substeps = 0
+        self.offered = 0                    # particle-substeps of every submitted request
+        self.host_s = {"admit": 0.0, "retire": 0.0, "wait": 0.0}
+        self._fp: Dict[int, int] = {}       # request id -> footprint bytes
         self._next_id = 0
+        self._pool = None
 
     # -- requests ----------------------------------------------------------
     def submit(self, scene, n_substeps: int, arrival_s: float = 0.0) -> int:
@@ -94,25 +106,44 @@ class Server:
         self._next_id += 1
         self.queue.append((arrival_s, rid, scene, int(n_substeps)))
         self.queue.sort(key=lambda t: (t[0], t[1]))
+        self.offered += scene.n * int(n_substeps)
         return rid
 
+    def _footprint(self, rid: int, sc) -> int:
+        nb = self._fp.get(rid)
+        if nb is None:
+            nb = self._fp[rid] = footprint(sc)[3]
+        return nb
+
+    def _prefetch(self, now: float, horizon_s: float = 0.25) -> None:
+        """Footprints of the requests that arrive soon (worker thread)."""
+        for arrival, rid, sc, _ in self.queue[:32]:
+            if arrival > now + horizon_s:
+                break
+            self._footprint(rid, sc)
+
     def _admit(self, now: float) -> None:
+        t0 = time.perf_counter()
         while self.queue and self.queue[0][0] <= now:
             arrival, rid, sc, n = self.queue[0]
-            nbytes = footprint(sc)[3]
+            nbytes = self._footprint(rid, sc)
             if self.used + nbytes > self.budget:
-                return
+                break
             try:
                 s = Scene.in_batch(self.batch, sc)
             except A.BMError as e:
                 if e.code == A.E_CAPACITY:
-                    return
+                    break
                 raise
+            s.set_stop(n)
             self.queue.pop(0)
+            self._fp.pop(rid, None)
             self.used += nbytes
             self.active.append(_Active(rid, s, n, n, nbytes, arrival, now))
+        self.host_s["admit"] += time.perf_counter() - t0
 
     def _retire(self, now: float) -> None:
+        t0 = time.perf_counter()
         keep = []
         for a in self.active:
             if a.remaining > 0:
@@ -122,58 +153,81 @@ class Server:
             # the other scenes' work) out of the serving loop
             r = a.scene.read_noalloc("x") if a.scene.n * 12 <= (16 << 20) else a.scene.read("x")
             info = a.scene.info()
+            assert info.step == a.total, (info.step, a.total)
             self.results[a.rid] = Result(a.rid, a.scene.n, a.total, a.arrival_s, a.admitted_s, now,
                                          r["x"], a.scene.tool_wrench() if a.scene.spec.blade else
                                          np.zeros(6), int(info.error_bits))
             a.scene.close()
             self.used -= a.bytes
         self.active = keep
+        self.host_s["retire"] += time.perf_counter() - t0
 
     # -- main loop -----------------------------------------------------------
     def run(self, realtime: bool = True, timeout_s: float = 3600.0) -> dict:
         """Serve until every submitted request has finished.  With realtime
         the arrival times are honoured against the wall clock; otherwise every
         request counts as already arrived."""
+        from concurrent.futures import ThreadPoolExecutor
         torch = self._torch
         t0 = time.perf_counter()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        while self.queue or self.active:
-            now = time.perf_counter() - t0
-            if now > timeout_s:
-                raise TimeoutError("serving loop exceeded its time limit")
-            self._admit(now if realtime else float("inf"))
-            if not self.active:
-                if self.queue and realtime:
-                    time.sleep(max(0.0, min(0.05, self.queue[0][0] - now)))
-                    continue
-                if self.queue:
-                    raise RuntimeError("a request does not fit the budget or the pools")
-                break
-            k = min(self.max_chunk, min(a.remaining for a in self.active))
-            e0.record(self.stream)
-            self.batch.step(k)
-            e1.record(self.stream)
-            e1.synchronize()
-            self.step_ms.append(e0.elapsed_time(e1) / k)
-            self.step_weight.append(k)
-            self.particle_substeps += k * sum(a.scene.n for a in self.active)
-            for a in self.active:
-                a.remaining -= k
-            self._retire(time.perf_counter() - t0)
+        self._pool = ThreadPoolExecutor(max_workers=1)
+        try:
+            while self.queue or self.active:
+                now = time.perf_counter() - t0
+                if now > timeout_s:
+                    raise TimeoutError("serving loop exceeded its time limit")
+                self._admit(now if realtime else float("inf"))
+                if not self.active:
+                    if self.queue and realtime:
+                        self._prefetch(now)
+                        time.sleep(max(0.0, min(0.05, self.queue[0][0] - now)))
+                        continue
+                    if self.queue:
+                        raise RuntimeError("a request does not fit the budget or the pools")
+                    break
+                k = self.max_chunk
+                e0.record(self.stream)
+                self.batch.step(k)
+                e1.record(self.stream)
+                # host work that overlaps the chunk: footprints of what arrives next
+                fut = self._pool.submit(self._prefetch, now if realtime else float("inf"))
+                tw = time.perf_counter()
+                e1.synchronize()
+                fut.result()
+                self.host_s["wait"] += time.perf_counter() - tw
+                self.step_ms.append(e0.elapsed_time(e1) / k)
+                self.step_weight.append(k)
+                for a in self.active:
+                    d = min(k, a.remaining)
+                    self.particle_substeps += d * a.scene.n
+                    a.remaining -= d
+                self._retire(time.perf_counter() - t0)
+        finally:
+            self._pool.shutdown()
+            self._pool = None
         wall = time.perf_counter() - t0
         return self.stats(wall)
 
     def stats(self, wall_s: float) -> dict:
         ms = np.repeat(np.array(self.step_ms), np.array(self.step_weight)) if self.step_ms else \
             np.zeros(1)
-        lat = np.array([r.latency_s for r in self.results.values()]) if self.results else np.zeros(1)
-        return {"requests": len(self.results), "wall_s": wall_s,
+        res = list(self.results.values())
+        lat = np.array([r.latency_s for r in res]) if res else np.zeros(1)
+        queued = np.array([r.admitted_s - r.arrival_s for r in res]) if res else np.zeros(1)
+        arrivals = [r.arrival_s for r in res]
+        span = (max(arrivals) - min(arrivals)) if len(arrivals) > 1 else 0.0
+        return {"requests": len(res), "wall_s": wall_s,
                 "throughput": self.particle_substeps / wall_s if wall_s > 0 else 0.0,
+                "offered_load": self.offered / span if span > 0 else None,
                 "step_ms_p50": float(np.percentile(ms, 50)),
                 "step_ms_p99": float(np.percentile(ms, 99)),
                 "request_latency_s_p50": float(np.percentile(lat, 50)),
                 "request_latency_s_p99": float(np.percentile(lat, 99)),
+                "queue_latency_s_p50": float(np.percentile(queued, 50)),
+                "queue_latency_s_p99": float(np.percentile(queued, 99)),
+                "host_s": dict(self.host_s),
                 "particle_substeps": self.particle_substeps}
 
     def close(self):
@@ -236,4 +290,7 @@ def combine_stats(st: dict, dist=None, n_requests: Optional[int] = None) -> dict
             "step_ms_p50": max(s["step_ms_p50"] for s in allst),
             "step_ms_p99": max(s["step_ms_p99"] for s in allst),
             "request_latency_s_p50": max(s["request_latency_s_p50"] for s in allst),
-            "request_latency_s_p99": max(s["request_latency_s_p99"] for s in allst)}
+            "request_latency_s_p99": max(s["request_latency_s_p99"] for s in allst),
+            "queue_latency_s_p50": max(s.get("queue_latency_s_p50", 0.0) for s in allst),
+            "queue_latency_s_p99": max(s.get("queue_latency_s_p99", 0.0) for s in allst),
+            "offered_load": (sum(s["offered_load"] for s in allst if s.get("offered_load")) or None)}

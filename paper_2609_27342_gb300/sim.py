@@ -197,6 +197,11 @@ class Scene:
     def step(self, n: int = 1) -> None:
         A.check(self._L.bm_step(self._h, int(n)))
 
+    def set_stop(self, substep: int) -> None:
+        """Stop advancing once `substep` substeps are taken (-1: never); the
+        scene is then left untouched by later steps, alone or in a batch."""
+        A.check(self._L.bm_scene_set_stop(self._h, int(substep)))
+
     def read(self, *names: str) -> Dict[str, np.ndarray]:
         names = names or ("x", "v")
         order = sorted(names, key=lambda k: A.FIELDS[k][0])

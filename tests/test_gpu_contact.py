@@ -125,3 +125,35 @@ def test_cylinder_cuts_two_way_tool_and_contact(pkg):
     assert np.sum(codes_o != codes_g) <= max(1, 1e-4 * sc.n)
     assert len(np.unique(codes_g)) >= 3
     assert g.info().error_bits == 0
+
+
+def test_pair_contact_checkpoint_and_batch_move_are_bitwise(pkg):
+    """With material-material contact on, a checkpoint restore and a move into
+    a batch mid-run both continue bit for bit: the candidate lists of the
+    contact search travel with the particle state."""
+    sc, x, v, nA = colliding_blocks(speed=0.8)
+    fields = ("x", "v", "F", "pair_partner", "pair_u")
+    g = pkg.Scene(sc)
+    g.write(x=x, v=v)
+    g.step(10)
+    ck = g.checkpoint()
+    g.step(15)
+    ref = g.read(*fields)
+    assert np.any(ref["pair_partner"] >= 0), "the blocks must be in contact"
+    g.restore(ck)
+    g.step(15)
+    got = g.read(*fields)
+    for k in fields:
+        assert np.array_equal(got[k], ref[k]), k
+    h = pkg.Scene(sc)
+    h.write(x=x, v=v)
+    h.step(10)
+    fp = pkg.footprint(sc)
+    b = pkg.Batch(max_particles=sc.n + 64, max_nodes=fp[1] + 64, max_scenes=2, pair_contact=True)
+    b.add(h)
+    b.step(15)
+    got = h.read(*fields)
+    for k in fields:
+        assert np.array_equal(got[k], ref[k]), ("moved", k)
+    b.close()
+    g.close()

@@ -202,7 +202,7 @@ def test_batched_equals_plain_bitwise(pkg):
     for p in plain:
         p.step(24)
     ref = [p.read("x", "v", "F", "mask1", "mask2") for p in plain]
-    for chunk, ntile, variant in [(8, 128, 0), (3, 64, 1), (16, 256, 2), (5, 96, 1)]:
+    for chunk, ntile, variant in [(8, 128, 0), (3, 64, 1), (16, 256, 2), (5, 96, 22)]:
         b = pkg.Batch(max_particles=sum(s.n for s in scenes) + 1000, max_nodes=200000,
                       max_scenes=8, graph_chunk=chunk, node_tile=ntile)
         b.set_tiles(chunk, ntile, variant)
@@ -234,12 +234,15 @@ def test_autotune_keeps_the_trajectory(pkg):
     gs = [pkg.Scene(s, stream=st) for s in scenes]
     for s in gs:
         b.add(s)
-    r = autotune(b, st, substeps=2, rounds=1, variants=(0, 2), node_tiles=(64, 256),
+    r = autotune(b, st, substeps=2, rounds=1, occ_choices=(0, 2), node_tiles=(64, 256),
                  graph_chunks=(2, 16), baseline=(4, 128, 0))
     shapes = {(t["graph_chunk"], t["node_tile"], t["brick_variant"]) for t in r["trials"]}
-    # the baseline, the 2 x 2 grid at a 16-substep graph, then the winner's
-    # other graph chunks (one more shape when the baseline itself won the grid)
-    assert len(shapes) == len(r["trials"]) in (6, 7)
+    # the baseline; each brick kernel's two occupancy choices in turn at a
+    # 16-substep graph (2 to 4 new shapes: a kernel's current choice is
+    # already timed); the two node tiles; the winner's other graph chunks
+    assert len(shapes) == len(r["trials"])
+    assert 6 <= len(shapes) <= 9, len(shapes)
+    assert any(t["brick_variant"] not in (0, 1, 2) for t in r["trials"]), "mixed occupancy probed"
     assert r["best"]["relative_to_baseline"] == min(t["relative"] for t in r["trials"])
     assert all(t["ms"] > 0 for t in r["trials"])
     b.step(3)

@@ -80,3 +80,36 @@ def test_budget_admission_serialises_but_keeps_results(pkg):
         x, _ = _alone(pkg, r)
         assert np.array_equal(srv.results[rid].x, x)
     srv.close()
+
+
+def test_stop_substep_freezes_a_scene_exactly(pkg):
+    """bm_scene_set_stop: a scene stopped at n substeps inside a batch that
+    keeps stepping equals the same scene run alone for n substeps, bit for
+    bit; moving the stop lets it continue, again equal to a run alone."""
+    reqs = _requests()[:3]
+    fps = [pkg.footprint(r.scene) for r in reqs]
+    b = pkg.Batch(max_particles=sum(f[0] for f in fps), max_nodes=sum(f[1] for f in fps), max_scenes=3,
+                  graph_chunk=8)
+    members = [pkg.Scene.in_batch(b, r.scene) for r in reqs]
+    members[0].set_stop(13)
+    members[1].set_stop(0)  # frozen from the start
+    b.step(24)
+    assert members[0].info().step == 13 and members[1].info().step == 0 and members[2].info().step == 24
+
+    def alone(sc, n):
+        g = pkg.Scene(sc)
+        g.step(n)
+        out = g.read("x", "v", "F", "code")
+        g.close()
+        return out
+
+    for m, r, n in zip(members, reqs, (13, 0, 24)):
+        got, want = m.read("x", "v", "F", "code"), alone(r.scene, n)
+        for k in want:
+            assert np.array_equal(got[k], want[k]), (n, k)
+    members[0].set_stop(-1)
+    b.step(5)
+    got, want = members[0].read("x", "v", "F", "code"), alone(reqs[0].scene, 18)
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+    b.close()

@@ -65,9 +65,11 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world)
     st = [{"requests": 3, "wall_s": 2.0, "particle_substeps": 100, "step_ms_p50": 0.5,
-           "step_ms_p99": 0.7, "request_latency_s_p50": 0.4, "request_latency_s_p99": 1.0},
+           "step_ms_p99": 0.7, "request_latency_s_p50": 0.4, "request_latency_s_p99": 1.0,
+           "queue_latency_s_p50": 0.01, "queue_latency_s_p99": 0.2, "offered_load": 60.0},
           {"requests": 5, "wall_s": 4.0, "particle_substeps": 300, "step_ms_p50": 0.6,
-           "step_ms_p99": 0.9, "request_latency_s_p50": 0.3, "request_latency_s_p99": 1.2}][rank]
+           "step_ms_p99": 0.9, "request_latency_s_p50": 0.3, "request_latency_s_p99": 1.2,
+           "queue_latency_s_p50": 0.02, "queue_latency_s_p99": 0.1, "offered_load": 90.0}][rank]
     q.put((rank, combine_stats(st, dist)))
     dist.barrier()
     dist.destroy_process_group()
@@ -90,3 +92,4 @@ def test_combine_stats_gloo_world2():
         assert s["ranks"] == 2 and s["requests"] == 8 and s["wall_s"] == 4.0
         assert s["throughput"] == pytest.approx(400 / 4.0)
         assert s["step_ms_p99"] == 0.9 and s["request_latency_s_p99"] == 1.2
+        assert s["queue_latency_s_p99"] == 0.2 and s["offered_load"] == pytest.approx(150.0)

@@ -27,6 +27,8 @@ class FakeBatch:
 
     def step(self, n):
         self.steps.append(n)
+        for sc in self.scenes:  # members advance up to their stop substep
+            sc.step_count = sc.step_count + n if sc.stop < 0 else min(sc.stop, sc.step_count + n)
 
     def set_tiles(self, chunk, ntile, variant):
         self.shape = (chunk, ntile, variant)
@@ -42,6 +44,11 @@ class FakeScene:
         self.batch = batch
         batch.scenes.append(self)
         self.closed = False
+        self.step_count = 0
+        self.stop = -1
+
+    def set_stop(self, n):
+        self.stop = n
 
     def read_noalloc(self, *names):
         return {"x": np.full((self.n, 3), float(self.n), np.float32)}
@@ -49,7 +56,7 @@ class FakeScene:
     read = read_noalloc
 
     def info(self):
-        return types.SimpleNamespace(error_bits=0)
+        return types.SimpleNamespace(error_bits=0, step=self.step_count)
 
     def tool_wrench(self):
         return np.zeros(6)
@@ -82,21 +89,23 @@ def test_budget_limits_resident_scenes(server_mod):
     st = srv.run(realtime=False)
     assert st["requests"] == 3
     # two scenes of 100 fit the 250-particle budget; the third waits
-    assert srv.batch.steps[0] == 10
-    assert all(k <= 10 for k in srv.batch.steps)
+    assert all(k == 10 for k in srv.batch.steps)
     r = srv.results
     assert r[2].admitted_s >= min(r[0].finished_s, r[1].finished_s)
     assert st["particle_substeps"] == 100 * (20 + 35 + 10)
 
 
-def test_chunks_stop_exactly_at_each_request_length(server_mod):
+def test_requests_stop_exactly_inside_whole_chunks(server_mod):
     srv = server_mod.Server(budget_bytes=10 ** 9, max_scenes=8, max_chunk=16)
     srv.submit(_sc(10), 7)
     srv.submit(_sc(20), 30)
-    srv.run(realtime=False)
-    # the first chunk ends where the shorter request ends
-    assert srv.batch.steps[0] == 7
-    assert sum(srv.batch.steps) == 30
+    st = srv.run(realtime=False)
+    # the batch always advances whole chunks; each scene stops on the device at
+    # its own length (the server checks the substep count when it retires it)
+    assert srv.batch.steps == [16, 16]
+    assert srv.results[0].n_substeps == 7 and srv.results[1].n_substeps == 30
+    assert st["particle_substeps"] == 10 * 7 + 20 * 30
+    assert st["offered_load"] is None  # both arrived at once: no span to divide by
 
 
 def test_request_larger_than_budget_is_reported(server_mod):
