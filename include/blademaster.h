@@ -369,7 +369,7 @@ const char *bm_kernel_name(int i);
  * per-node kernels (multiple of 32 in 64..512) and the brick-kernel
  * occupancy variant v in 0..26, one choice per brick kernel: v % 3 for P2G
  * (3, 2 or 4 resident CTAs per SM), (v / 3) % 3 for G2P+MUSL (5, 4 or 6) and
- * v / 9 for the F update (7, 5 or 8); fewer CTAs leave more registers per
+ * v / 9 for the F update (7, 5 or 6); fewer CTAs leave more registers per
  * thread, more hide more latency; 0 is every kernel's default.  Results do not
  * depend on any of them: every sum is taken in a fixed order and the
  * variants share their arithmetic.  Synchronises the batch stream; captured

@@ -114,9 +114,11 @@ struct PPool {
   int *hkey;                // bucket of each particle's current-configuration cell
   int *horder;              // particles ordered by bucket, by pool index inside a bucket
   float4 *hent;             // the same order: position and pool index (int bits in w)
+  uint32_t *hbase;          // the same order: packed base cell of the entry's particle
   int *hist_partner[2];     // pair history (partner pool index, -1 ends), by step parity
   float *hist_u[2];         // [(p * BM_HIST + k) * 3]: tangential spring displacement
-  int *nbr;                 // [p * BM_NBR + k]: contact candidates (pool index, ascending)
+  int *nbr;                 // [p * BM_NBR + k]: contact candidates (pool index in bits 0-30;
+                            // bit 31: the pair shares a reference stencil)
   uint8_t *nbr_n;           // candidates of each particle
   float *xb[3];             // positions at the last candidate-list build
 };

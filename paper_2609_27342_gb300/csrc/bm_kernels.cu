@@ -1800,7 +1800,7 @@ __global__ void k_pair_fill(World w, LaunchSet ls) {
 }
 
 // order each bucket by pool index (buckets are short), then lay out its
-// entries (position, pool index) for the list build
+// entries (position, pool index, base cell) for the list build
 __global__ void k_pair_sort(World w) {
   if (!*w.H.build) return;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < w.H.n_buckets; b += gridDim.x * blockDim.x) {
@@ -1817,18 +1817,29 @@ __global__ void k_pair_sort(World w) {
     for (int i = s0; i < s1; ++i) {
       const int q = w.P.horder[i];
       w.P.hent[i] = make_float4(w.P.x[0][q], w.P.x[1][q], w.P.x[2][q], __int_as_float(q));
+      w.P.hbase[i] = w.P.base[q];
     }
   }
 }
 
+// Whether two particles' reference stencils overlap (base cells at most two
+// cells apart on every axis): such a pair interacts through the grid, and is
+// a contact pair only once a cut separates it (self-contact exclusion).
+__device__ __forceinline__ bool share_stencil(uint32_t bp, uint32_t bq) {
+  int px, py, pz, qx, qy, qz;
+  particle_base(bp, px, py, pz);
+  particle_base(bq, qx, qy, qz);
+  return abs(px - qx) <= 2 && abs(py - qy) <= 2 && abs(pz - qz) <= 2;
+}
+
 // candidate lists: every particle of the scene within r_l = 2 R_p + skin,
-// one warp per particle, lane l < 27 walking neighbour cell l (dz, dy, dx in
-// -1..1, x fastest) through the bucket's (position, index) entries; an entry
-// belongs to the cell when its position falls in it (the bucket's hash may
-// be shared).  Each lane keeps its first NKEEP candidates in registers (a
-// second walk writes the rest), a warp scan places them: the list is in
-// (cell, pool index) order.  The positions of the build are kept.
-#define NKEEP 8
+// one thread per particle walking the 27 neighbour cells (dz, dy, dx in
+// -1..1, x fastest) through their buckets' (position, index) entries; an
+// entry belongs to the cell when its position falls in it (a bucket's hash
+// may be shared).  The list is in (cell, pool index) order; bit 31 of an
+// entry marks a pair whose reference stencils overlap.  Threads of a warp
+// hold neighbouring particles, which mostly read the same buckets.  The
+// positions of the build are kept.
 __global__ void k_pair_list(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
@@ -1838,79 +1849,56 @@ __global__ void k_pair_list(World w, LaunchSet ls) {
   const float ih = sc.pair_inv_h;
   const float rl = 2.0f * sc.Rp + 1.5f * sc.Rp, rl2 = rl * rl;
   const int pend = sc.p_begin + sc.n_p;
-  // the brick's particles are spread over gridDim.y CTAs of blockDim.x / 32 warps
-  const int lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.y;
-  const int wid = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
   bool over = false;
-  for (int i = wid; i < bt.w; i += nw) {
+  // the brick's particles are spread over gridDim.y CTAs
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < bt.w; i += blockDim.x * gridDim.y) {
     const int p = bt.z + i;
     const float xp[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
-    const int cx = (int)floorf(xp[0] * ih) + dx, cy = (int)floorf(xp[1] * ih) + dy,
-              cz = (int)floorf(xp[2] * ih) + dz;
-    int k0 = 0, k1 = 0;
-    if (lane < 27) {
-      const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
-      k0 = w.H.bucket_start[b];
-      k1 = w.H.bucket_start[b + 1];
-    }
-    auto accept = [&](const float4 e) {
-      const int q = __float_as_int(e.w);
-      if (q == p || q < sc.p_begin || q >= pend) return false;
-      if ((int)floorf(e.x * ih) != cx || (int)floorf(e.y * ih) != cy || (int)floorf(e.z * ih) != cz)
-        return false;
-      const float d0 = xp[0] - e.x, d1 = xp[1] - e.y, d2 = xp[2] - e.z;
-      return d0 * d0 + d1 * d1 + d2 * d2 <= rl2;
-    };
-    int keep[NKEEP];
-    int cnt = 0;
-    // entries four at a time: the loads of a group are issued together
-    for (int k = k0; k < k1; k += 4) {
-      float4 e[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) e[u] = k + u < k1 ? P.hent[k + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (k + u >= k1 || !accept(e[u])) continue;
-#pragma unroll
-        for (int j = 0; j < NKEEP; ++j)
-          if (j == cnt) keep[j] = __float_as_int(e[u].w);
-        ++cnt;
-      }
-    }
-    int off = cnt;  // inclusive scan over the lanes
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(FULL, off, o);
-      if (lane >= o) off += y;
-    }
-    const int total = __shfl_sync(FULL, off, 31);
-    off -= cnt;
+    const uint32_t bp = P.base[p];
+    const int cx0 = (int)floorf(xp[0] * ih), cy0 = (int)floorf(xp[1] * ih), cz0 = (int)floorf(xp[2] * ih);
     int *lst = P.nbr + (size_t)p * BM_NBR;
+    int cnt = 0;
+    for (int l = 0; l < 27; ++l) {
+      const int cx = cx0 + l % 3 - 1, cy = cy0 + (l / 3) % 3 - 1, cz = cz0 + l / 9 - 1;
+      const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
+      const int k0 = w.H.bucket_start[b], k1 = w.H.bucket_start[b + 1];
+      // entries four at a time: the loads of a group are issued together
+      for (int k = k0; k < k1; k += 4) {
+        float4 e[4];
+        uint32_t eb[4];
 #pragma unroll
-    for (int j = 0; j < NKEEP; ++j)
-      if (j < cnt && off + j < BM_NBR) lst[off + j] = keep[j];
-    if (cnt > NKEEP) {  // the rest, by a second walk
-      int m = 0;
-      for (int k = k0; k < k1; ++k) {
-        const float4 e = P.hent[k];
-        if (!accept(e)) continue;
-        if (m >= NKEEP && off + m < BM_NBR) lst[off + m] = __float_as_int(e.w);
-        ++m;
+        for (int u = 0; u < 4; ++u) {
+          e[u] = k + u < k1 ? P.hent[k + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+          eb[u] = k + u < k1 ? P.hbase[k + u] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (k + u >= k1) continue;
+          const int q = __float_as_int(e[u].w);
+          if (q == p || q < sc.p_begin || q >= pend) continue;
+          if ((int)floorf(e[u].x * ih) != cx || (int)floorf(e[u].y * ih) != cy ||
+              (int)floorf(e[u].z * ih) != cz)
+            continue;
+          const float d0 = xp[0] - e[u].x, d1 = xp[1] - e[u].y, d2 = xp[2] - e[u].z;
+          if (!(d0 * d0 + d1 * d1 + d2 * d2 <= rl2)) continue;
+          if (cnt < BM_NBR) lst[cnt] = share_stencil(bp, eb[u]) ? (int)((uint32_t)q | 0x80000000u) : q;
+          ++cnt;
+        }
       }
     }
-    if (lane == 0) {
-      P.nbr_n[p] = (uint8_t)min(total, BM_NBR);
-      P.xb[0][p] = xp[0];
-      P.xb[1][p] = xp[1];
-      P.xb[2][p] = xp[2];
-    }
-    over |= total > BM_NBR;
+    P.nbr_n[p] = (uint8_t)min(cnt, BM_NBR);
+    P.xb[0][p] = xp[0];
+    P.xb[1][p] = xp[1];
+    P.xb[2][p] = xp[2];
+    over |= cnt > BM_NBR;
   }
   if (over) atomicOr(&scm.err, BM_ERRBIT_CONTACT_OVERFLOW);
 }
 
-// Pair impulses (Eq. 10-13), one thread per particle walking its list.
+// Pair impulses (Eq. 10-13), one thread per particle walking its list
+// (gridDim.y CTAs per brick).  A candidate sharing p's reference stencil is
+// skipped unless the two are on opposite sides of a cut, before its state
+// is read.
 __global__ void k_pair(World w, LaunchSet ls) {
   const int4 bt = ls.btiles[blockIdx.x];
   DevScene &scm = w.scenes[bt.x];
@@ -1921,19 +1909,19 @@ __global__ void k_pair(World w, LaunchSet ls) {
   const float dt = sc.dt, R2 = 2.0f * sc.Rp;
   const float meff = sc.mp * sc.mp / (sc.mp + sc.mp);
   bool over = false;
-  for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < bt.w; i += blockDim.x * gridDim.y) {
     const int p = bt.z + i;
     const float xp[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
     const float vp[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
     const uint32_t a1 = P.s1[p], a2 = P.s2[p];
-    int bpx, bpy, bpz;
-    particle_base(P.base[p], bpx, bpy, bpz);
     float J[3] = {0.f, 0.f, 0.f};
     int cnt = 0;
     const int n = P.nbr_n[p];
     const int *lst = P.nbr + (size_t)p * BM_NBR;
     for (int k = 0; k < n; ++k) {
-      const int q = lst[k];
+      const int ent = lst[k];
+      const int q = ent & 0x7fffffff;
+      if (ent < 0 && !conflict(a1, a2, P.s1[q], P.s2[q])) continue;  // self-contact exclusion
       const float xq[3] = {P.x[0][q], P.x[1][q], P.x[2][q]};
       const float vq[3] = {P.v[0][q], P.v[1][q], P.v[2][q]};
       const bool plo = p < q;
@@ -1949,11 +1937,7 @@ __global__ void k_pair(World w, LaunchSet ls) {
       const float vn = vr[0] * nn[0] + vr[1] * nn[1] + vr[2] * nn[2];
       const float dhat = R2 - (dist + fminf(dt * vn, 0.0f));  // Eq. 10
       if (!(dhat > 0.f)) continue;
-      int bqx, bqy, bqz;
-      particle_base(P.base[q], bqx, bqy, bqz);
-      const bool share = abs(bpx - bqx) <= 2 && abs(bpy - bqy) <= 2 && abs(bpz - bqz) <= 2;
-      if (share && !conflict(a1, a2, P.s1[q], P.s2[q])) continue;  // self-contact exclusion
-      const float fn = sc.s_n * meff / (dt * dt) * dhat;            // Eq. 11
+      const float fn = sc.s_n * meff / (dt * dt) * dhat;  // Eq. 11
       float uh[3] = {0.f, 0.f, 0.f};
       for (int h = 0; h < BM_HIST; ++h) {
         const int pt = P.hist_partner[rb][(size_t)lo * BM_HIST + h];
@@ -2534,7 +2518,7 @@ template <> struct OccG2P<2> { static constexpr int v = 6; };
 template <int C> struct OccFupd;
 template <> struct OccFupd<0> { static constexpr int v = 7; };
 template <> struct OccFupd<1> { static constexpr int v = 5; };
-template <> struct OccFupd<2> { static constexpr int v = 8; };
+template <> struct OccFupd<2> { static constexpr int v = 6; };
 
 template <int PPC, int C>
 static cudaError_t set_smem_attrs() {
@@ -2644,7 +2628,7 @@ static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, c
   k_pair_list<<<dim3(ls.n_btiles, 4), 128, 0, st>>>(w, ls);
   rec(ev, 18, 1, st);
   rec(ev, 17, 0, st);
-  k_pair<<<ls.n_btiles, 128, 0, st>>>(w, ls);
+  k_pair<<<dim3(ls.n_btiles, 4), 128, 0, st>>>(w, ls);
   rec(ev, 17, 1, st);
 }
 

@@ -174,6 +174,15 @@ struct bm_batch_s {
 
 namespace {
 
+// A contact-candidate entry moved from pool range [from, ...) to [to, ...):
+// the pool index (bits 0-30) is rebased, the shared-stencil flag (bit 31) is
+// kept.  Entries beyond a particle's count are never read.
+int rebase_candidate(int e, int from, int to) {
+  const uint32_t u = (uint32_t)e;
+  const uint32_t q = ((u & 0x7fffffffu) - (uint32_t)from + (uint32_t)to) & 0x7fffffffu;
+  return (int)((u & 0x80000000u) | q);
+}
+
 int world_alloc(WorldH *W) {
   const int64_t P = W->cap_p;
   PPool &pp = W->w.P;
@@ -216,6 +225,7 @@ int world_alloc(WorldH *W) {
     I(pp.horder, P);
     pp.hent = W->get<float4>(P);
     ok &= pp.hent != nullptr;
+    U(pp.hbase, P);
     for (int b = 0; b < 2; ++b) {
       I(pp.hist_partner[b], P * BM_HIST);
       F(pp.hist_u[b], P * BM_HIST * 3);
@@ -678,7 +688,7 @@ int move_scene(bm_scene_s *s, WorldH *W) {
     }
     std::vector<int> nb((size_t)n * BM_NBR);
     CK(cudaMemcpy(nb.data(), B.nbr + pd * BM_NBR, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
-    for (auto &q : nb) q = q - (int)ps + (int)pd;  // entries beyond a count are never read
+    for (auto &q : nb) q = rebase_candidate(q, (int)ps, (int)pd);
     CK(cudaMemcpy(B.nbr + pd * BM_NBR, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
   }
   set_ranges(s, cur);
@@ -1220,7 +1230,7 @@ int bm_checkpoint_restore(bm_scene_t s, const void *src, int src_on_device) {
     std::vector<int> nb((size_t)s->n * BM_NBR);
     int *np = P.nbr + s->p_begin * BM_NBR;
     CK(cudaMemcpy(nb.data(), np, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost));
-    for (auto &v : nb) v = v - (int)h.p_begin + (int)s->p_begin;  // entries beyond a count are never read
+    for (auto &v : nb) v = rebase_candidate(v, (int)h.p_begin, (int)s->p_begin);
     CK(cudaMemcpy(np, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice));
   }
   set_ranges(s, sv);
@@ -1483,10 +1493,10 @@ int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
   if (nodes) *nodes = s.n_node;
   if (bricks) *bricks = s.n_brick;
   // fx, x, v, u_t, J (3 each); F, Fp^-1, dF/dt (9 each); D; base, masks, perm; pending label;
-  // with pair contact: hash key, order and entries, the double-buffered history,
+  // with pair contact: hash key, order, entries and their base cells, the double-buffered history,
   // the candidate list and the positions at its build
   const int64_t per_p = 4 * (3 * 5 + 9 * 3 + 1) + 4 * 4 + 1 +
-                        (desc->pair_contact ? (4 + 4 + 16 + 2 * BM_HIST * 16 + 4 * BM_NBR + 1 + 12) : 0);
+                        (desc->pair_contact ? (4 + 4 + 16 + 4 + 2 * BM_HIST * 16 + 4 * BM_NBR + 1 + 12) : 0);
   const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (3 * 16 + 8) + 6 * 32;
   const int64_t per_brick = 3 * BM_TILE_NODES + 48 + 16 + 8;
   if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.n_brick * per_brick + s.hist_cap * 48;

@@ -271,6 +271,51 @@ def test_batch_remove_keeps_state(pkg):
     b.close()
 
 
+def test_reads_checkpoints_and_moves_leave_the_trajectory_bitwise(pkg):
+    """Reading F between substeps, saving a checkpoint, stepping on and
+    restoring it, and moving the scene into a batch, all in the middle of a
+    cut (label commits and slot-table rebuilds on most substeps), leave the
+    run bit-identical to an uninterrupted one."""
+    sc = bi.single_cut_cuboid(size=(0.05, 0.02, 0.025), edge_z0=0.026, speed=0.8)
+    fields = ("x", "v", "F", "D", "mask1", "mask2")
+    n = 40
+    a = pkg.Scene(sc)
+    a.step(n)
+    ref = a.read(*fields)
+    assert np.count_nonzero(ref["mask1"] | ref["mask2"]) > 0, "the blade must have cut"
+    # reads of F between substeps
+    b = pkg.Scene(sc)
+    done = 0
+    for k in (3, 7, 1, 9, 5):
+        b.step(k)
+        done += k
+        b.read("F")
+    b.step(n - done)
+    got = b.read(*fields)
+    for k in fields:
+        assert np.array_equal(got[k], ref[k]), ("reads", k)
+    # a checkpoint mid-run, restored and continued
+    c = pkg.Scene(sc)
+    c.step(17)
+    ck = c.checkpoint()
+    c.step(6)
+    c.restore(ck)
+    c.step(n - 17)
+    got = c.read(*fields)
+    for k in fields:
+        assert np.array_equal(got[k], ref[k]), ("checkpoint", k)
+    # moved into a batch mid-run
+    d = pkg.Scene(sc)
+    d.step(22)
+    bt = pkg.Batch(max_particles=sc.n + 1000, max_nodes=200000, max_scenes=2)
+    bt.add(d)
+    bt.step(n - 22)
+    got = d.read(*fields)
+    for k in fields:
+        assert np.array_equal(got[k], ref[k]), ("moved", k)
+    bt.close()
+
+
 # --------------------------------------------------------------------------
 # edge cases
 # --------------------------------------------------------------------------
