@@ -115,6 +115,8 @@ struct PPool {
   int *horder;              // particles ordered by bucket, by pool index inside a bucket
   float4 *hent;             // the same order: position and pool index (int bits in w)
   uint32_t *hbase;          // the same order: packed base cell of the entry's particle
+  unsigned long long *hcell;  // per particle: scene and current-configuration cell (cell_key)
+  unsigned long long *hentk;  // hent order: the entry's cell key
   int *hist_partner[2];     // pair history (partner pool index, -1 ends), by step parity
   float *hist_u[2];         // [(p * BM_HIST + k) * 3]: tangential spring displacement
   int *nbr;                 // [p * BM_NBR + k]: contact candidates (pool index in bits 0-30;

@@ -1674,6 +1674,14 @@ __device__ __forceinline__ int hash_cell(int scene, int cx, int cy, int cz, int 
   return (int)(h & (unsigned)(nb - 1));
 }
 
+// scene and hash-cell coordinates in one word (16 bits each, coordinates
+// wrapped): equal for the entries of one cell; two cells with equal words
+// are at least 65,536 cells apart
+__device__ __forceinline__ unsigned long long cell_key(int scene, int cx, int cy, int cz) {
+  return ((unsigned long long)(scene & 0xffff) << 48) | ((unsigned long long)(cx & 0xffff) << 32) |
+         ((unsigned long long)(cy & 0xffff) << 16) | (unsigned long long)(cz & 0xffff);
+}
+
 // per-substep reset of the scenes' reductions and of the world's build flag
 __global__ void k_pair_reset(World w, LaunchSet ls) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1751,6 +1759,7 @@ __global__ void k_pair_hash(World w, LaunchSet ls) {
     const int cz = (int)floorf(P.x[2][p] * ih);
     const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
     P.hkey[p] = b;
+    P.hcell[p] = cell_key(bt.x, cx, cy, cz);
     atomicAdd(&w.H.bucket_start[b], 1);
   }
 }
@@ -1800,7 +1809,7 @@ __global__ void k_pair_fill(World w, LaunchSet ls) {
 }
 
 // order each bucket by pool index (buckets are short), then lay out its
-// entries (position, pool index, base cell) for the list build
+// entries (position, pool index, base cell, cell key) for the list build
 __global__ void k_pair_sort(World w) {
   if (!*w.H.build) return;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < w.H.n_buckets; b += gridDim.x * blockDim.x) {
@@ -1818,6 +1827,7 @@ __global__ void k_pair_sort(World w) {
       const int q = w.P.horder[i];
       w.P.hent[i] = make_float4(w.P.x[0][q], w.P.x[1][q], w.P.x[2][q], __int_as_float(q));
       w.P.hbase[i] = w.P.base[q];
+      w.P.hentk[i] = w.P.hcell[q];
     }
   }
 }
@@ -1832,67 +1842,129 @@ __device__ __forceinline__ bool share_stencil(uint32_t bp, uint32_t bq) {
   return abs(px - qx) <= 2 && abs(py - qy) <= 2 && abs(pz - qz) <= 2;
 }
 
-// candidate lists: every particle of the scene within r_l = 2 R_p + skin,
-// one thread per particle walking the 27 neighbour cells (dz, dy, dx in
-// -1..1, x fastest) through their buckets' (position, index) entries; an
-// entry belongs to the cell when its position falls in it (a bucket's hash
-// may be shared).  The list is in (cell, pool index) order; bit 31 of an
-// entry marks a pair whose reference stencils overlap.  Threads of a warp
-// hold neighbouring particles, which mostly read the same buckets.  The
-// positions of the build are kept.
-__global__ void k_pair_list(World w, LaunchSet ls) {
-  const int4 bt = ls.btiles[blockIdx.x];
-  DevScene &scm = w.scenes[bt.x];
-  const DevScene &sc = scm;
-  if (!sc.pair_on || !sc.pair_build) return;
+// Candidate lists of the particles in entries [c0, c1) of one bucket (at most
+// 32, lane i holding entry c0 + i), by one warp.  The particles are taken in
+// groups of one cell (and scene); a group shares its 27 neighbour cells
+// (dz, dy, dx in -1..1, x fastest), whose bucket entries are laid end to end
+// and tested 32 at a time, one per lane, against each member in turn: an
+// entry counts when it belongs to the neighbour cell (its key; a bucket's
+// hash may be shared), is another particle and lies within r_l = 2 R_p +
+// skin.  A ballot gives each accepted entry its place, so every list is in
+// (cell, pool index) order, as a walk of the cells in order would give;
+// bit 31 of an entry marks a pair whose reference stencils overlap.
+__device__ __forceinline__ void bucket_lists(const World &w, int c0, int c1, int lane) {
   const PPool &P = w.P;
-  const float ih = sc.pair_inv_h;
-  const float rl = 2.0f * sc.Rp + 1.5f * sc.Rp, rl2 = rl * rl;
-  const int pend = sc.p_begin + sc.n_p;
-  bool over = false;
-  // the brick's particles are spread over gridDim.y CTAs
-  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < bt.w; i += blockDim.x * gridDim.y) {
-    const int p = bt.z + i;
-    const float xp[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
-    const uint32_t bp = P.base[p];
-    const int cx0 = (int)floorf(xp[0] * ih), cy0 = (int)floorf(xp[1] * ih), cz0 = (int)floorf(xp[2] * ih);
-    int *lst = P.nbr + (size_t)p * BM_NBR;
-    int cnt = 0;
-    for (int l = 0; l < 27; ++l) {
-      const int cx = cx0 + l % 3 - 1, cy = cy0 + (l / 3) % 3 - 1, cz = cz0 + l / 9 - 1;
-      const int b = hash_cell(bt.x, cx, cy, cz, w.H.n_buckets);
-      const int k0 = w.H.bucket_start[b], k1 = w.H.bucket_start[b + 1];
-      // entries four at a time: the loads of a group are issued together
-      for (int k = k0; k < k1; k += 4) {
-        float4 e[4];
-        uint32_t eb[4];
+  const bool mine = lane < c1 - c0;
+  const float4 me = mine ? P.hent[c0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const unsigned long long mkey = mine ? P.hentk[c0 + lane] : ~0ull;
+  const uint32_t mbase = mine ? P.hbase[c0 + lane] : 0u;
+  const int mscene = (int)(mkey >> 48);
+  int mx = 0, my = 0, mz = 0;
+  if (mine) {
+    const float ih = w.scenes[mscene].pair_inv_h;
+    mx = (int)floorf(me.x * ih);
+    my = (int)floorf(me.y * ih);
+    mz = (int)floorf(me.z * ih);
+  }
+  int cnt = 0;
+  unsigned todo = __ballot_sync(FULL, mine);
+  while (todo) {
+    const int lead = __ffs(todo) - 1;
+    const unsigned long long K = __shfl_sync(FULL, mkey, lead);
+    const int cx0 = __shfl_sync(FULL, mx, lead), cy0 = __shfl_sync(FULL, my, lead),
+              cz0 = __shfl_sync(FULL, mz, lead);
+    const unsigned grp = __ballot_sync(FULL, mine && mkey == K && mx == cx0 && my == cy0 && mz == cz0) & todo;
+    todo &= ~grp;
+    const int scene = (int)(K >> 48);
+    const DevScene &sc = w.scenes[scene];
+    const float rl = 2.0f * sc.Rp + 1.5f * sc.Rp, rl2 = rl * rl;
+    int a0 = 0, sz = 0;
+    unsigned long long nk = 0;
+    if (lane < 27) {
+      const int cx = cx0 + lane % 3 - 1, cy = cy0 + (lane / 3) % 3 - 1, cz = cz0 + lane / 9 - 1;
+      const int hb = hash_cell(scene, cx, cy, cz, w.H.n_buckets);
+      a0 = w.H.bucket_start[hb];
+      sz = w.H.bucket_start[hb + 1] - a0;
+      nk = cell_key(scene, cx, cy, cz);
+    }
+    int incl = sz;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          e[u] = k + u < k1 ? P.hent[k + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-          eb[u] = k + u < k1 ? P.hbase[k + u] : 0u;
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int T = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - sz;
+    for (int base = 0; base < T; base += 32) {
+      const int j = base + lane;
+      // neighbour cell of candidate j: the last cell whose entries start at or before j
+      int L = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (k + u >= k1) continue;
-          const int q = __float_as_int(e[u].w);
-          if (q == p || q < sc.p_begin || q >= pend) continue;
-          if ((int)floorf(e[u].x * ih) != cx || (int)floorf(e[u].y * ih) != cy ||
-              (int)floorf(e[u].z * ih) != cz)
-            continue;
-          const float d0 = xp[0] - e[u].x, d1 = xp[1] - e[u].y, d2 = xp[2] - e[u].z;
-          if (!(d0 * d0 + d1 * d1 + d2 * d2 <= rl2)) continue;
-          if (cnt < BM_NBR) lst[cnt] = share_stencil(bp, eb[u]) ? (int)((uint32_t)q | 0x80000000u) : q;
-          ++cnt;
+      for (int step = 16; step > 0; step >>= 1) {
+        const int t = L + step;
+        const int ex = __shfl_sync(FULL, excl, t < 27 ? t : 26);
+        if (t < 27 && ex <= j) L = t;
+      }
+      const int aL = __shfl_sync(FULL, a0, L), exL = __shfl_sync(FULL, excl, L);
+      const unsigned long long kL = __shfl_sync(FULL, nk, L);
+      const bool inr = j < T;
+      const int k = aL + (j - exL);
+      const float4 e = inr ? P.hent[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const unsigned long long ek = inr ? P.hentk[k] : 0ull;
+      const uint32_t eb = inr ? P.hbase[k] : 0u;
+      const bool valid = inr && ek == kL;
+      const int q = __float_as_int(e.w);
+      unsigned g = grp;
+      while (g) {
+        const int m = __ffs(g) - 1;
+        g &= g - 1;
+        const float px = __shfl_sync(FULL, me.x, m), py = __shfl_sync(FULL, me.y, m),
+                    pz = __shfl_sync(FULL, me.z, m);
+        const int p = __float_as_int(__shfl_sync(FULL, me.w, m));
+        const uint32_t bp = __shfl_sync(FULL, mbase, m);
+        const float d0 = px - e.x, d1 = py - e.y, d2 = pz - e.z;
+        const bool acc = valid && q != p && d0 * d0 + d1 * d1 + d2 * d2 <= rl2;
+        const unsigned am = __ballot_sync(FULL, acc);
+        const int c = __shfl_sync(FULL, cnt, m);
+        if (acc) {
+          const int pos = c + __popc(am & ((1u << lane) - 1u));
+          if (pos < BM_NBR)
+            P.nbr[(size_t)p * BM_NBR + pos] = share_stencil(bp, eb) ? (int)((uint32_t)q | 0x80000000u) : q;
         }
+        if (lane == m) cnt += __popc(am);
       }
     }
-    P.nbr_n[p] = (uint8_t)min(cnt, BM_NBR);
-    P.xb[0][p] = xp[0];
-    P.xb[1][p] = xp[1];
-    P.xb[2][p] = xp[2];
-    over |= cnt > BM_NBR;
   }
-  if (over) atomicOr(&scm.err, BM_ERRBIT_CONTACT_OVERFLOW);
+  if (mine) {
+    const int p = __float_as_int(me.w);
+    P.nbr_n[p] = (uint8_t)min(cnt, BM_NBR);
+    P.xb[0][p] = me.x;
+    P.xb[1][p] = me.y;
+    P.xb[2][p] = me.z;
+    if (cnt > BM_NBR) atomicOr(&w.scenes[mscene].err, BM_ERRBIT_CONTACT_OVERFLOW);
+  }
+}
+
+// candidate lists of every particle of the scenes that rebuild them: each
+// warp takes groups of 32 buckets (grid-stride) and builds the lists of the
+// particles of each non-empty one, 32 entries at a time.  The positions of
+// the build are kept.
+__global__ void __launch_bounds__(256) k_pair_list(World w) {
+  if (!*w.H.build) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int nb = w.H.n_buckets;
+  for (int b0 = warp * 32; b0 < nb; b0 += nwarps * 32) {
+    const int b = b0 + lane;
+    const int e0 = b < nb ? w.H.bucket_start[b] : 0, e1 = b < nb ? w.H.bucket_start[b + 1] : 0;
+    unsigned todo = __ballot_sync(FULL, e1 > e0);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int k0 = __shfl_sync(FULL, e0, src), k1 = __shfl_sync(FULL, e1, src);
+      for (int c = k0; c < k1; c += 32) bucket_lists(w, c, min(k1, c + 32), lane);
+    }
+  }
 }
 
 // Pair impulses (Eq. 10-13), one thread per particle walking its list
@@ -2625,7 +2697,8 @@ static void launch_pairs(const World &w, const LaunchSet &ls, cudaStream_t st, c
   k_pair_sort<<<(nb + 255) / 256, 256, 0, st>>>(w);
   rec(ev, 16, 1, st);
   rec(ev, 18, 0, st);
-  k_pair_list<<<dim3(ls.n_btiles, 4), 128, 0, st>>>(w, ls);
+  const int lgrid = (nb / 32 + 7) / 8;  // 8 warps per CTA, a warp per 32 buckets, at most 8 CTAs per SM
+  k_pair_list<<<lgrid < 152 * 8 ? lgrid : 152 * 8, 256, 0, st>>>(w);
   rec(ev, 18, 1, st);
   rec(ev, 17, 0, st);
   k_pair<<<dim3(ls.n_btiles, 4), 128, 0, st>>>(w, ls);

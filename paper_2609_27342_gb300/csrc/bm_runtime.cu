@@ -226,6 +226,9 @@ int world_alloc(WorldH *W) {
     pp.hent = W->get<float4>(P);
     ok &= pp.hent != nullptr;
     U(pp.hbase, P);
+    pp.hcell = W->get<unsigned long long>(P);
+    pp.hentk = W->get<unsigned long long>(P);
+    ok &= pp.hcell && pp.hentk;
     for (int b = 0; b < 2; ++b) {
       I(pp.hist_partner[b], P * BM_HIST);
       F(pp.hist_u[b], P * BM_HIST * 3);
@@ -1493,10 +1496,10 @@ int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
   if (nodes) *nodes = s.n_node;
   if (bricks) *bricks = s.n_brick;
   // fx, x, v, u_t, J (3 each); F, Fp^-1, dF/dt (9 each); D; base, masks, perm; pending label;
-  // with pair contact: hash key, order, entries and their base cells, the double-buffered history,
+  // with pair contact: hash key, order, entries with their base cells and cell keys, the double-buffered history,
   // the candidate list and the positions at its build
   const int64_t per_p = 4 * (3 * 5 + 9 * 3 + 1) + 4 * 4 + 1 +
-                        (desc->pair_contact ? (4 + 4 + 16 + 4 + 2 * BM_HIST * 16 + 4 * BM_NBR + 1 + 12) : 0);
+                        (desc->pair_contact ? (4 + 4 + 16 + 4 + 16 + 2 * BM_HIST * 16 + 4 * BM_NBR + 1 + 12) : 0);
   const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (3 * 16 + 8) + 6 * 32;
   const int64_t per_brick = 3 * BM_TILE_NODES + 48 + 16 + 8;
   if (bytes) *bytes = n * per_p + s.n_node * per_node + (s.n_cell + 1) * 4 + s.n_brick * per_brick + s.hist_cap * 48;
