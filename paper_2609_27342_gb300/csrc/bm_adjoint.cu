@@ -14,10 +14,10 @@
 // forward kernels' float32 expressions.
 //
 // Kernels of one adjoint substep (scene-local launches):
-//   k_adj_musl    per node: slot masses; adjoint of v* from the F update;
+//   k_adj_musl    per node (a warp each): slot masses; adjoint of v* from the F update;
 //                 through v* = C p* / m (transpose of Eq. 8)
 //   k_adj_v1      per particle: adjoint of the G2P velocity v^{n+1} (MUSL)
-//   k_adj_g2p     per node: adjoints of the coupled momentum and momentum
+//   k_adj_g2p     per node (a warp each): adjoints of the coupled momentum and momentum
 //                 change (Eq. 17 and x update), through Eq. 8 transposed
 //   k_adj_part    per particle: P2G (Eq. 2) transposed, stress, blade and
 //                 floor contact; block partials of the parameter adjoints
@@ -114,63 +114,86 @@ __device__ __forceinline__ void couple_T(int ns, const uint2 *codes, const float
     for (int c = 0; c < NC; ++c) S[b][c] = out[b][c];
 }
 
-// Visit every (particle, weight, gradient) pair of scene-local node li in a
-// fixed order (cells by offset, particles by pool index).
+// Visit the (particle, weight, gradient) pairs of scene-local node li whose
+// particle lies in stencil cell l (< 27: ox = l % 3, oy = l / 3 % 3,
+// oz = l / 9, the base cell li - (ox, oy, oz)), in pool order.
 template <class Fn>
-__device__ __forceinline__ void for_node_particles(const World &w, const DevScene &sc, int li, Fn fn) {
+__device__ __forceinline__ void for_cell_particles(const World &w, const DevScene &sc, int li, int l, Fn fn) {
   const int ix = li % sc.nn[0], iy = (li / sc.nn[0]) % sc.nn[1], iz = li / (sc.nn[0] * sc.nn[1]);
+  const int ox = l % 3, oy = (l / 3) % 3, oz = l / 9;
+  const int bx = ix - ox, by = iy - oy, bz = iz - oz;
+  if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) return;
   const int *cs = w.N.cell_start + sc.cell_begin;
-  for (int oz = 0; oz < 3; ++oz)
-    for (int oy = 0; oy < 3; ++oy)
-      for (int ox = 0; ox < 3; ++ox) {
-        const int bx = ix - ox, by = iy - oy, bz = iz - oz;
-        if (bx < 0 || by < 0 || bz < 0 || bx >= sc.nb[0] || by >= sc.nb[1] || bz >= sc.nb[2]) continue;
-        const int c = cell_at(sc, bx, by, bz);
-        for (int p = cs[c]; p < cs[c + 1]; ++p) {
-          float wx, wy, wz, dx, dy, dz;
-          wgt(ox, w.P.fx[0][p], wx, dx);
-          wgt(oy, w.P.fx[1][p], wy, dy);
-          wgt(oz, w.P.fx[2][p], wz, dz);
-          const float N = wx * wy * wz;
-          const float gN[3] = {dx * wy * wz * sc.inv_dx, wx * dy * wz * sc.inv_dx, wx * wy * dz * sc.inv_dx};
-          fn(p, N, gN);
-        }
-      }
+  const int c = cell_at(sc, bx, by, bz);
+  for (int p = cs[c]; p < cs[c + 1]; ++p) {
+    float wx, wy, wz, dx, dy, dz;
+    wgt(ox, w.P.fx[0][p], wx, dx);
+    wgt(oy, w.P.fx[1][p], wy, dy);
+    wgt(oz, w.P.fx[2][p], wz, dz);
+    const float N = wx * wy * wz;
+    const float gN[3] = {dx * wy * wz * sc.inv_dx, wx * dy * wz * sc.inv_dx, wx * wy * dz * sc.inv_dx};
+    fn(p, N, gN);
+  }
 }
+
+// sum over the warp's lanes in a fixed butterfly order (every lane gets it)
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The per-node adjoint kernels run one warp per node: lane l < 27 walks the
+// node's particles in stencil cell l, the lanes' sums are combined by
+// warp_sum, one pass per logical grid of the node (codes fixed), and lane 0
+// applies the transposed coupling to the node's slot sums.
+constexpr int kAdjNodesPerBlock = kAdjBlock / 32;
 
 // per node: slot masses, adjoint of v* from F' = F + dt sum v* (x) grad N,
 // then through v* = C p* / m
 __global__ void __launch_bounds__(kAdjBlock) k_adj_musl(World w, AdjWork aw) {
+  __shared__ float red[kAdjNodesPerBlock][BM_MAXS][4];
   const DevScene &sc = w.scenes[aw.slot];
-  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int li = blockIdx.x * kAdjNodesPerBlock + wid;
   if (li >= sc.n_node) return;
   const int node = sc.node_begin + li;
   const int off = w.N.slot_off[node], ns = w.N.slot_cnt[node];
   if (ns == 0) return;
+  const int pb = sc.p_begin;
+  const float dt = sc.dt, mp = sc.mp;
+  for (int a = 0; a < ns; ++a) {
+    const uint2 ca = w.S.code[off + a];
+    float m = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+    if (lane < 27)
+      for_cell_particles(w, sc, li, lane, [&](int p, float N, const float *gN) {
+        if (w.P.s1[p] != ca.x || w.P.s2[p] != ca.y) return;
+        m += N * mp;
+        const int i = p - pb;
+        S0 += dt * (aw.Fb[0][i] * gN[0] + aw.Fb[1][i] * gN[1] + aw.Fb[2][i] * gN[2]);
+        S1 += dt * (aw.Fb[3][i] * gN[0] + aw.Fb[4][i] * gN[1] + aw.Fb[5][i] * gN[2]);
+        S2 += dt * (aw.Fb[6][i] * gN[0] + aw.Fb[7][i] * gN[1] + aw.Fb[8][i] * gN[2]);
+      });
+    m = warp_sum(m);
+    S0 = warp_sum(S0);
+    S1 = warp_sum(S1);
+    S2 = warp_sum(S2);
+    if (lane == 0) {
+      red[wid][a][0] = m;
+      red[wid][a][1] = S0;
+      red[wid][a][2] = S1;
+      red[wid][a][3] = S2;
+    }
+  }
+  if (lane != 0) return;
   uint2 codes[BM_MAXS];
   float m[BM_MAXS], S[BM_MAXS][3];
   for (int a = 0; a < ns; ++a) {
     codes[a] = w.S.code[off + a];
-    m[a] = 0.f;
-    S[a][0] = S[a][1] = S[a][2] = 0.f;
-  }
-  const int pb = sc.p_begin;
-  const float dt = sc.dt, mp = sc.mp;
-  for_node_particles(w, sc, li, [&](int p, float N, const float *gN) {
-    const uint2 c = make_uint2(w.P.s1[p], w.P.s2[p]);
-    int a = 0;
-    while (a < ns && (codes[a].x != c.x || codes[a].y != c.y)) ++a;
-    if (a == ns) return;
-    m[a] += N * mp;
-    const int i = p - pb;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-      S[a][r] += dt * (aw.Fb[3 * r][i] * gN[0] + aw.Fb[3 * r + 1][i] * gN[1] + aw.Fb[3 * r + 2][i] * gN[2]);
-  });
-  for (int a = 0; a < ns; ++a) {
+    m[a] = red[wid][a][0];
     const float im = m[a] > 0.f ? 1.0f / m[a] : 0.f;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) S[a][r] *= im;
+    for (int r = 0; r < 3; ++r) S[a][r] = red[wid][a][1 + r] * im;
   }
   couple_T<3>(ns, codes, m, S);
   const int rel = off - sc.slot_begin;
@@ -214,37 +237,48 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_v1(World w, AdjWork aw) {
 // from v^{n+1} = beta v + sum N/m ((1-beta) p + dp) and x^{n+1} = x + dt sum
 // N (p + dp)/m, then through Eq. 8 transposed
 __global__ void __launch_bounds__(kAdjBlock) k_adj_g2p(World w, AdjWork aw) {
+  __shared__ float red[kAdjNodesPerBlock][BM_MAXS][6];
   const DevScene &sc = w.scenes[aw.slot];
-  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int li = blockIdx.x * kAdjNodesPerBlock + wid;
   if (li >= sc.n_node) return;
   const int node = sc.node_begin + li;
   const int off = w.N.slot_off[node], ns = w.N.slot_cnt[node];
   if (ns == 0) return;
   const int rel = off - sc.slot_begin;
+  const int pb = sc.p_begin;
+  const float dt = sc.dt, beta = sc.beta;
+  for (int a = 0; a < ns; ++a) {
+    const uint2 ca = w.S.code[off + a];
+    const float ma = aw.sm[rel + a];
+    float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (lane < 27 && ma > 0.f)
+      for_cell_particles(w, sc, li, lane, [&](int p, float N, const float *) {
+        if (w.P.s1[p] != ca.x || w.P.s2[p] != ca.y) return;
+        const float q = N / ma;
+        const int i = p - pb;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float v1 = aw.v1b[r][i], xx = dt * aw.xb[r][i];
+          S[r] += q * ((1.0f - beta) * v1 + xx);
+          S[3 + r] += q * (v1 + xx);
+        }
+      });
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      const float t = warp_sum(S[r]);
+      if (lane == 0) red[wid][a][r] = t;
+    }
+  }
+  if (lane != 0) return;
   uint2 codes[BM_MAXS];
   float m[BM_MAXS], S[BM_MAXS][6];
   for (int a = 0; a < ns; ++a) {
     codes[a] = w.S.code[off + a];
     m[a] = aw.sm[rel + a];
 #pragma unroll
-    for (int r = 0; r < 6; ++r) S[a][r] = 0.f;
+    for (int r = 0; r < 6; ++r) S[a][r] = red[wid][a][r];
   }
-  const int pb = sc.p_begin;
-  const float dt = sc.dt, beta = sc.beta;
-  for_node_particles(w, sc, li, [&](int p, float N, const float *) {
-    const uint2 c = make_uint2(w.P.s1[p], w.P.s2[p]);
-    int a = 0;
-    while (a < ns && (codes[a].x != c.x || codes[a].y != c.y)) ++a;
-    if (a == ns || !(m[a] > 0.f)) return;
-    const float q = N / m[a];
-    const int i = p - pb;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float v1 = aw.v1b[r][i], xx = dt * aw.xb[r][i];
-      S[a][r] += q * ((1.0f - beta) * v1 + xx);
-      S[a][3 + r] += q * (v1 + xx);
-    }
-  });
   couple_T<6>(ns, codes, m, S);
   for (int a = 0; a < ns; ++a)
 #pragma unroll
@@ -657,7 +691,8 @@ cudaError_t bm_launch_adjoint_substep(const World &w, const void *work, const do
   aw.fbar[1] = fbar[1];
   aw.fbar[2] = fbar[2];
   if (n_p == 0) return cudaSuccess;
-  const int gn = (n_node + kAdjBlock - 1) / kAdjBlock, gp = (n_p + kAdjBlock - 1) / kAdjBlock;
+  // per-node kernels: a warp per node; per-particle kernels: a thread per particle
+  const int gn = (n_node + kAdjNodesPerBlock - 1) / kAdjNodesPerBlock, gp = (n_p + kAdjBlock - 1) / kAdjBlock;
   k_adj_musl<<<gn, kAdjBlock, 0, st>>>(w, aw);
   k_adj_v1<<<gp, kAdjBlock, 0, st>>>(w, aw);
   k_adj_g2p<<<gn, kAdjBlock, 0, st>>>(w, aw);
