@@ -418,20 +418,24 @@ __device__ __noinline__ int side_label_exact(const DevScene &sc, const float xf[
 __device__ __forceinline__ int side_label(const DevScene &sc, const float x[3], const float v[3]) {
   const float r0 = x[0] - sc.fxe[0], r1 = x[1] - sc.fxe[1], r2 = x[2] - sc.fxe[2];
   const float s = r0 * sc.fn[0] + r1 * sc.fn[1] + r2 * sc.fn[2];
+  // forward-error bounds (2^-20 = 16 u, generous over the ~5 u analysis)
+  const float k = 9.5367431640625e-07f;
+  const float mag = fabsf(x[0]) + fabsf(x[1]) + fabsf(x[2]) +
+                    2.0f * (fabsf(sc.fxe[0]) + fabsf(sc.fxe[1]) + fabsf(sc.fxe[2]));
+  const float E = k * mag + 1e-30f;
+  const float as = fabsf(s);
+  // beyond the band's half-width by more than the bound: outside the band
+  // in float64 too (the decision below and the exact path both give 0)
+  if (as > sc.h + (E + k * sc.h)) return 0;
   const float l = r0 * sc.fe[0] + r1 * sc.fe[1] + r2 * sc.fe[2];
   const float f = r0 * sc.fd[0] + r1 * sc.fd[1] + r2 * sc.fd[2];
   const float uc = (sc.fve[0] - v[0]) * sc.fd[0] + (sc.fve[1] - v[1]) * sc.fd[1] +
                    (sc.fve[2] - v[2]) * sc.fd[2];
   const float ucdt = uc * sc.dt;
   const float lowb = -sc.b_back - fmaxf(ucdt, 0.0f);
-  // forward-error bounds (2^-20 = 16 u, generous over the ~5 u analysis)
-  const float k = 9.5367431640625e-07f;
-  const float mag = fabsf(x[0]) + fabsf(x[1]) + fabsf(x[2]) +
-                    2.0f * (fabsf(sc.fxe[0]) + fabsf(sc.fxe[1]) + fabsf(sc.fxe[2]));
-  const float E = k * mag + 1e-30f;
   const float Eu = k * ((fabsf(sc.fve[0]) + fabsf(sc.fve[1]) + fabsf(sc.fve[2]) + fabsf(v[0]) +
                          fabsf(v[1]) + fabsf(v[2])) * sc.dt + sc.b_back + fabsf(ucdt));
-  const float as = fabsf(s), al = fabsf(l);
+  const float al = fabsf(l);
   const bool near = as <= E || fabsf(as - sc.h) <= E + k * sc.h || fabsf(al - sc.fL) <= E + k * sc.fL ||
                     fabsf(f) <= E || fabsf(f - sc.b_lead) <= E + k * sc.b_lead ||
                     fabsf(f - lowb) <= E + Eu;
@@ -637,6 +641,13 @@ __device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P,
     float vrel[3] = {v[0] - (sc.fvB[0] + wr3[0]), v[1] - (sc.fvB[1] + wr3[1]), v[2] - (sc.fvB[2] + wr3[2])};
     float vn = vrel[0] * nB[0] + vrel[1] * nB[1] + vrel[2] * nB[2];
     float phihat = phi + dt * fminf(vn, 0.0f);
+    // no predicted overlap: J_n = 0 below, and the impulse, reaction and
+    // friction history come out as on the no-contact branch
+    if (!(phihat < 0.0f)) {
+      uh[0] = uh[1] = uh[2] = 0.0f;
+      goto contact_done;
+    }
+    {
     float wB = 0.0f;
     if (sc.finv_mass > 0.0f) {
       float rn[3] = {rc[1] * nB[2] - rc[2] * nB[1], rc[2] * nB[0] - rc[0] * nB[2], rc[0] * nB[1] - rc[1] * nB[0]};
@@ -688,6 +699,8 @@ __device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P,
     J[0] += JB[0];
     J[1] += JB[1];
     J[2] += JB[2];
+    }
+  contact_done:;
   }
   if (sc.floor_on) {
     const float phi = x[2] - sc.floor_z - sc.Rp;
