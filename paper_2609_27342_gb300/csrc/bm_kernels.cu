@@ -619,6 +619,29 @@ __device__ __forceinline__ int tile_slot(const World &w, const Tile &T, const ui
 // label for the next substep (Eq. 3, 4, 6), and the P2G inputs
 // A = -dt V0 P(F) / dx and the particle's total impulse J.
 // --------------------------------------------------------------------------
+// Whether the blade box is farther from the particle than one substep of
+// relative motion can close: d > R_p + 2 dt (|v| + |v_B| + |w_B| r_max) (1-norms
+// bound the speeds; r_max bounds the reach of the box from the blade's
+// reference point), so that the predicted gap phi_hat = phi + dt min(v_n, 0)
+// of the contact test is positive with a margin far above rounding.
+__device__ __forceinline__ bool blade_out_of_reach(const DevScene &sc, const float x[3], const float v[3]) {
+  const float *ax[3] = {sc.fn, sc.fe, sc.fd};
+  const float r[3] = {x[0] - sc.fc[0], x[1] - sc.fc[1], x[2] - sc.fc[2]};
+  float d2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float q = r[0] * ax[a][0] + r[1] * ax[a][1] + r[2] * ax[a][2];
+    const float e = fmaxf(fabsf(q) - sc.fhext[a], 0.0f);
+    d2 += e * e;
+  }
+  const float rmax = fabsf(sc.fc[0] - sc.fxB[0]) + fabsf(sc.fc[1] - sc.fxB[1]) + fabsf(sc.fc[2] - sc.fxB[2]) +
+                     sc.fhext[0] + sc.fhext[1] + sc.fhext[2];
+  const float vb = fabsf(v[0]) + fabsf(v[1]) + fabsf(v[2]) + fabsf(sc.fvB[0]) + fabsf(sc.fvB[1]) +
+                   fabsf(sc.fvB[2]) + (fabsf(sc.fwB[0]) + fabsf(sc.fwB[1]) + fabsf(sc.fwB[2])) * rmax;
+  const float reach = sc.Rp * 1.0001f + 2.0f * sc.dt * vb;
+  return d2 > reach * reach;
+}
+
 // INELASTIC: the launch set holds a scene with plasticity or viscosity (the
 // elastic instantiation carries no trace of those paths)
 template <bool INELASTIC>
@@ -632,7 +655,9 @@ __device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P,
   float D = sc.reset_D ? 0.0f : D0;
   const float u00 = P.ut[0][p], u01 = P.ut[1][p], u02 = P.ut[2][p];
   float uh[3] = {u00, u01, u02};
-  if (sc.has_blade && sc.tool_contact_on) {
+  if (sc.has_blade && sc.tool_contact_on && blade_out_of_reach(sc, x, v)) {
+    uh[0] = uh[1] = uh[2] = 0.0f;  // as on the no-contact branch below
+  } else if (sc.has_blade && sc.tool_contact_on) {
     float xc[3], nB[3], phi;
     box_closest(sc, x, sc.Rp, xc, nB, phi);
     float rc[3] = {xc[0] - sc.fxB[0], xc[1] - sc.fxB[1], xc[2] - sc.fxB[2]};
