@@ -60,6 +60,20 @@ KERNEL_MODEL = {
     "k_musl_node": {"bytes": (0, 12, 86, 0), "flops": (0, 0, 20, 0)},
     "k_fupd": {"bytes": (97, 0, 54, 1080), "flops": (650, 0, 0, 0)},
 }
+# the substep's small kernels (bytes only): the tool step reads the bricks'
+# wrench partials (48 B per brick); the slot rebuild reads each node's dirty
+# flag and code count and writes its slot count (3 B per node), writes each
+# brick's tile descriptors (4 B per tile node) and partial-sum range, and,
+# per node, the slot offset and the first-slot entries of the <= 8 covering
+# bricks (36 B) and each slot's code (8 B); the recount of the dirty nodes'
+# codes (the particles of 27 cells each) comes on top
+SMALL_KERNEL_BYTES = {
+    "k_tool": (0, 0, 0, 48),
+    "k_slot_count": (0, 3, 0, 0),
+    "k_brick_tiles": (0, 0, 0, 4 * 216 + 8),
+    "k_slot_scan": (0, 0, 0, 8),
+    "k_slot_fill": (0, 37, 8, 0),
+}
 STEP_ALGORITHMIC_BYTES = 156  # per particle-substep: the state the method must move
 LATE_FIRST = 900              # first substep of the late timing window (of the 1,000-substep rollout)
 LAUNCHES_PER_SUBSTEP = 10     # kernels one batched substep launches (no pair contact)
@@ -334,6 +348,17 @@ def run_native(args):
                  "algorithmic_flops": alg_flops, "avg_launch_ms": round(ktimes[dom], 4),
                  "hbm_frac": round(hbm_frac, 4), "alu_frac": round(alu_frac, 4),
                  "kernel_ms": {k: round(v, 4) for k, v in ktimes.items()}})
+    # every kernel of the substep: algorithmic bytes per launch over its
+    # live CUDA-event time, against the measured HBM peak
+    per = {}
+    for k, mb in [(k, m["bytes"]) for k, m in KERNEL_MODEL.items()] + list(SMALL_KERNEL_BYTES.items()):
+        t = ktimes.get(k, 0.0)
+        if t <= 0.0:
+            continue
+        b = mb[0] * n_particles + mb[1] * n_nodes + mb[2] * n_slots + mb[3] * n_bricks
+        per[k] = {"ms": round(t, 4), "bytes": int(b), "gbs": round(b / (t * 1e-3) / 1e9, 1),
+                  "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)}
+    roof["kernels"] = per
     step_ms = ms / args.steps
     step_roof = STEP_ALGORITHMIC_BYTES * n_particles / (step_ms * 1e-3) / 1e9
 
