@@ -368,7 +368,8 @@ const char *bm_kernel_name(int i);
  * autotuner): substeps per captured CUDA graph (1..256), nodes per CTA of the
  * per-node kernels (multiple of 32 in 64..512) and the brick-kernel
  * occupancy variant v in 0..26, one choice per brick kernel: v % 3 for P2G
- * (3, 2 or 4 resident CTAs per SM), (v / 3) % 3 for G2P+MUSL (5, 4 or 6) and
+ * (4, 3 or 2 resident CTAs per SM; 3, 2 or 4 in launch sets with plasticity
+ * or viscosity), (v / 3) % 3 for G2P+MUSL (5, 4 or 6) and
  * v / 9 for the F update (7, 5 or 6); fewer CTAs leave more registers per
  * thread, more hide more latency; 0 is every kernel's default.  Results do not
  * depend on any of them: every sum is taken in a fixed order and the

@@ -837,35 +837,40 @@ __device__ __forceinline__ void xy_reduce(float (&a)[3][3][NV], int cx, int cy) 
     }
 }
 
-// The layer sums of xy_reduce into the z stage: sz[k][oz][t] is value k of
-// tile node t from the cells of z-layer t_z - oz.  Each (node, oz) entry that
-// the tile gather reads has exactly one writer.
-template <int NV>
-__device__ __forceinline__ void stage_layer(float (*sz)[3][TN], const float (&a)[3][3][NV], int cx, int cy,
+// The layer sums of xy_reduce into the z stage, value k of tile node (tx,
+// ty, cz + oz) from the cells of z-layer cz: with ZN = TN at sz[k][oz][t] (t
+// the tile node), with ZN = TZ at sz[k][oz][(cz * TE + ty) * TE + tx] (a
+// z-offset reaches 4 of the tile's 6 node layers, so each offset keeps
+// 4 x 36 entries; the compact stage lets P2G run 4 CTAs per SM).  Each (node,
+// oz) entry that the tile gather reads has exactly one writer.
+#define TZ (BR * TE * TE)
+template <int NV, int ZN>
+__device__ __forceinline__ void stage_layer(float (*sz)[3][ZN], const float (&a)[3][3][NV], int cx, int cy,
                                             int cz, int oz) {
-  const int tz = cz + oz;
+  const int lz = ZN == TN ? cz + oz : cz;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       if ((i > 0 && cy != 3) || (j > 0 && cx != 3)) continue;
-      const int t = (tz * TE + cy + i) * TE + cx + j;
+      const int e = (lz * TE + cy + i) * TE + cx + j;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) sz[k][oz][t] = a[i][j][k];
+      for (int k = 0; k < NV; ++k) sz[k][oz][e] = a[i][j][k];
     }
 }
 
 // Sums of tile node t over the z-offsets of the z stage (<= 3 terms, in
-// ascending offset order).
-template <int NV>
-__device__ __forceinline__ void gather_z(const float (*sz)[3][TN], int t, float (&acc)[NV]) {
+// ascending offset order); in the compact stage offset o holds node t at
+// entry t - o * 36.
+template <int NV, int ZN>
+__device__ __forceinline__ void gather_z(const float (*sz)[3][ZN], int t, float (&acc)[NV]) {
   const int tz = t / (TE * TE);
   const int o0 = max(0, tz - (BR - 1)), o1 = min(2, tz);
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.f;
   for (int o = o0; o <= o1; ++o)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += sz[k][o][t];
+    for (int k = 0; k < NV; ++k) acc[k] += sz[k][o][ZN == TN ? t : t - o * TE * TE];
 }
 
 #define BM_BRICK_CODES 64  // distinct codes kept per brick (more raise the slot-overflow flag)
@@ -921,7 +926,7 @@ template <int PPC>
 struct K2S {
   Tile T;
   float part[18][PPC * BR3];   // the brick's particles (fx, v, A, J), [particle-in-cell][cell]
-  float sz[7][3][TN];          // one pass's (node, z-offset) sums
+  float sz[7][3][TZ];          // one pass's (node, z-offset) sums
   uint32_t ps1[PPC * BR3], ps2[PPC * BR3];
   uint2 bcode[BM_BRICK_CODES]; // distinct codes of the brick's particles
   float red[6][BT / 32];       // wrench partials of the warps
@@ -1092,54 +1097,89 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
     const bool has = coded && n_c > 0 &&
                      (uniform || cell_has_code<PPC>(S.ps1, S.ps2, S.ccode, S.ncode, c, k1, k2));
     const bool filt = !uniform && S.ncode[c] > 1;
-    float a[3][3][7];
+    // two walks over the cell's particles, each reducing its own values, so
+    // that fewer sums are live at once: (m N, m v N), then A grad N + N J
+    {
+      float a[3][3][4];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int f = 0; f < 7; ++f) a[i][j][f] = 0.f;
-    if (has) {
-      for (int j = 0; j < n_c; ++j) {
-        const int si = pic(j, c);
-        if (filt && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
-        float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
-        const float f0 = S.part[0][si], f1 = S.part[1][si], f2 = S.part[2][si];
-        bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
-        bs<0>(f1, wy[0], dwy[0]); bs<1>(f1, wy[1], dwy[1]); bs<2>(f1, wy[2], dwy[2]);
-        bs_rt(oz, f2, wz, dwz);
-        const float v0 = S.part[3][si], v1 = S.part[4][si], v2 = S.part[5][si];
-        float A[9];
+          for (int f = 0; f < 4; ++f) a[i][j][f] = 0.f;
+      if (has) {
+        for (int j = 0; j < n_c; ++j) {
+          const int si = pic(j, c);
+          if (filt && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
+          float wx[3], wy[3], wz, d;
+          const float f0 = S.part[0][si], f1 = S.part[1][si], f2 = S.part[2][si];
+          bs<0>(f0, wx[0], d); bs<1>(f0, wx[1], d); bs<2>(f0, wx[2], d);
+          bs<0>(f1, wy[0], d); bs<1>(f1, wy[1], d); bs<2>(f1, wy[2], d);
+          bs_rt(oz, f2, wz, d);
+          const float v0 = S.part[3][si], v1 = S.part[4][si], v2 = S.part[5][si];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) A[k] = S.part[6 + k][si];
-        const float J0 = S.part[15][si], J1 = S.part[16][si], J2 = S.part[17][si];
+          for (int oy = 0; oy < 3; ++oy) {
+            const float wyz = wy[oy] * wz;
+            const float M0 = v0 * wyz, M1 = v1 * wyz, M2 = v2 * wyz;
 #pragma unroll
-        for (int oy = 0; oy < 3; ++oy) {
-          // with N = wx wyz and grad N = (dwx wyz, wx dyz, wx wyd):
-          // A grad N + N J = wx (A_:1 dyz + A_:2 wyd + J wyz) + dwx (A_:0 wyz)
-          const float wyz = wy[oy] * wz, dyz = dwy[oy] * wz, wyd = wy[oy] * dwz;
-          const float U0 = A[1] * dyz + A[2] * wyd + J0 * wyz;
-          const float U1 = A[4] * dyz + A[5] * wyd + J1 * wyz;
-          const float U2 = A[7] * dyz + A[8] * wyd + J2 * wyz;
-          const float V0 = A[0] * wyz, V1 = A[3] * wyz, V2 = A[6] * wyz;
-          const float M0 = v0 * wyz, M1 = v1 * wyz, M2 = v2 * wyz;
-#pragma unroll
-          for (int ox = 0; ox < 3; ++ox) {
-            float *q = a[oy][ox];
-            const float wxx = wx[ox], dxx = dwx[ox];
-            q[0] += wxx * wyz;
-            q[1] += wxx * M0;
-            q[2] += wxx * M1;
-            q[3] += wxx * M2;
-            q[4] += wxx * U0 + dxx * V0;
-            q[5] += wxx * U1 + dxx * V1;
-            q[6] += wxx * U2 + dxx * V2;
+            for (int ox = 0; ox < 3; ++ox) {
+              float *q = a[oy][ox];
+              const float wxx = wx[ox];
+              q[0] += wxx * wyz;
+              q[1] += wxx * M0;
+              q[2] += wxx * M1;
+              q[3] += wxx * M2;
+            }
           }
         }
       }
+      xy_reduce<4>(a, cx, cy);
+      stage_layer<4, TZ>(S.sz, a, cx, cy, cz, oz);
     }
-    xy_reduce<7>(a, cx, cy);
-    stage_layer<7>(S.sz, a, cx, cy, cz, oz);
+    {
+      float a[3][3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) a[i][j][f] = 0.f;
+      if (has) {
+        for (int j = 0; j < n_c; ++j) {
+          const int si = pic(j, c);
+          if (filt && (S.ps1[si] != k1 || S.ps2[si] != k2)) continue;
+          float wx[3], dwx[3], wy[3], dwy[3], wz, dwz;
+          const float f0 = S.part[0][si], f1 = S.part[1][si], f2 = S.part[2][si];
+          bs<0>(f0, wx[0], dwx[0]); bs<1>(f0, wx[1], dwx[1]); bs<2>(f0, wx[2], dwx[2]);
+          bs<0>(f1, wy[0], dwy[0]); bs<1>(f1, wy[1], dwy[1]); bs<2>(f1, wy[2], dwy[2]);
+          bs_rt(oz, f2, wz, dwz);
+          float A[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) A[k] = S.part[6 + k][si];
+          const float J0 = S.part[15][si], J1 = S.part[16][si], J2 = S.part[17][si];
+#pragma unroll
+          for (int oy = 0; oy < 3; ++oy) {
+            // with N = wx wyz and grad N = (dwx wyz, wx dyz, wx wyd):
+            // A grad N + N J = wx (A_:1 dyz + A_:2 wyd + J wyz) + dwx (A_:0 wyz)
+            const float wyz = wy[oy] * wz, dyz = dwy[oy] * wz, wyd = wy[oy] * dwz;
+            const float U0 = A[1] * dyz + A[2] * wyd + J0 * wyz;
+            const float U1 = A[4] * dyz + A[5] * wyd + J1 * wyz;
+            const float U2 = A[7] * dyz + A[8] * wyd + J2 * wyz;
+            const float V0 = A[0] * wyz, V1 = A[3] * wyz, V2 = A[6] * wyz;
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+              float *q = a[oy][ox];
+              const float wxx = wx[ox], dxx = dwx[ox];
+              q[0] += wxx * U0 + dxx * V0;
+              q[1] += wxx * U1 + dxx * V1;
+              q[2] += wxx * U2 + dxx * V2;
+            }
+          }
+        }
+      }
+      xy_reduce<3>(a, cx, cy);
+      stage_layer<3, TZ>(S.sz + 4, a, cx, cy, cz, oz);
+    }
     __syncthreads();
     if (pbase >= 0) {
       for (int t = tid; t < TN; t += BT) {
@@ -1155,7 +1195,7 @@ __global__ void __launch_bounds__(BT, MB) k_p2g_brick(World w, LaunchSet ls) {
         const int sl = coded ? node_slot_of(w, S.T, nullptr, t, uniform, k1, k2) : -1;
         if (sl < 0) continue;
         float acc[7];
-        gather_z<7>(S.sz, t, acc);
+        gather_z<7, TZ>(S.sz, t, acc);
         w.B.pm[e0 + sl] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         w.B.pd[e0 + sl] = make_float4(acc[4], acc[5], acc[6], 0.f);
       }
@@ -1493,7 +1533,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
       }
     }
     xy_reduce<3>(a, cx, cy);
-    stage_layer<3>(S.sz, a, cx, cy, cz, oz);
+    stage_layer<3, TN>(S.sz, a, cx, cy, cz, oz);
     __syncthreads();
     if (pbase >= 0) {
       for (int t = tid; t < TN; t += BT) {
@@ -1507,7 +1547,7 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
         const int sl = coded ? node_slot_of(w, S.T, tcodes, t, uniform, k1, k2) : -1;
         if (sl < 0) continue;
         float acc[3];
-        gather_z<3>(S.sz, t, acc);
+        gather_z<3, TN>(S.sz, t, acc);
         w.B.pm[e0 + sl] = make_float4(acc[0], acc[1], acc[2], 0.f);
       }
     }
@@ -2617,10 +2657,13 @@ cudaError_t bm_launch_rebuild(const World &w, const LaunchSet &ls, cudaStream_t 
 // v % 3 for k_p2g_brick, (v / 3) % 3 for k_g2p_musl and v / 9 for k_fupd;
 // choice 0 is each kernel's default.  The arithmetic is the same in every
 // variant, so results are bit-identical; the batch autotuner picks one.
-template <int C> struct OccP2G;
-template <> struct OccP2G<0> { static constexpr int v = 3; };
-template <> struct OccP2G<1> { static constexpr int v = 2; };
-template <> struct OccP2G<2> { static constexpr int v = 4; };
+template <int C, bool INELASTIC> struct OccP2G;
+template <> struct OccP2G<0, false> { static constexpr int v = 4; };
+template <> struct OccP2G<1, false> { static constexpr int v = 3; };
+template <> struct OccP2G<2, false> { static constexpr int v = 2; };
+template <> struct OccP2G<0, true> { static constexpr int v = 3; };  // the inelastic stress needs the registers
+template <> struct OccP2G<1, true> { static constexpr int v = 2; };
+template <> struct OccP2G<2, true> { static constexpr int v = 4; };
 template <int C> struct OccG2P;
 template <> struct OccG2P<0> { static constexpr int v = 5; };
 template <> struct OccG2P<1> { static constexpr int v = 4; };
@@ -2630,17 +2673,22 @@ template <> struct OccFupd<0> { static constexpr int v = 7; };
 template <> struct OccFupd<1> { static constexpr int v = 5; };
 template <> struct OccFupd<2> { static constexpr int v = 6; };
 
+// dynamic shared memory of the brick kernels, and the largest shared-memory
+// carveout, so that the CTAs per SM their launch bounds aim at fit
+template <class K>
+static cudaError_t brick_smem(K *kernel, int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
 template <int PPC, int C>
 static cudaError_t set_smem_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_p2g_brick<PPC, OccP2G<C>::v, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(K2S<PPC>));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_p2g_brick<PPC, OccP2G<C>::v, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(K2S<PPC>));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_g2p_musl<PPC, OccG2P<C>::v>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K4S<PPC>));
+  cudaError_t e = brick_smem(k_p2g_brick<PPC, OccP2G<C, false>::v, false>, (int)sizeof(K2S<PPC>));
+  if (e == cudaSuccess) e = brick_smem(k_p2g_brick<PPC, OccP2G<C, true>::v, true>, (int)sizeof(K2S<PPC>));
+  if (e == cudaSuccess) e = brick_smem(k_g2p_musl<PPC, OccG2P<C>::v>, (int)sizeof(K4S<PPC>));
+  return e;
 }
 
 cudaError_t bm_kernels_init() {
@@ -2664,9 +2712,9 @@ cudaError_t bm_kernels_init() {
 template <int PPC, int C>
 static void launch_p2g(const World &w, const LaunchSet &ls, cudaStream_t st) {
   if (ls.any_inelastic)
-    k_p2g_brick<PPC, OccP2G<C>::v, true><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+    k_p2g_brick<PPC, OccP2G<C, true>::v, true><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
   else
-    k_p2g_brick<PPC, OccP2G<C>::v, false><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
+    k_p2g_brick<PPC, OccP2G<C, false>::v, false><<<ls.n_btiles, BT, sizeof(K2S<PPC>), st>>>(w, ls);
 }
 
 template <int PPC, int C>
