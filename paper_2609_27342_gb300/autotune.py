@@ -47,6 +47,18 @@ def _time_shape(batch, stream, chunk: int, ntile: int, variant: int, substeps: i
     return best, chunk + rounds * n
 
 
+def pick(rows: List[dict], incumbent: Optional[dict], margin: float) -> dict:
+    """The fastest of ``rows`` by relative time, unless it beats the
+    ``incumbent`` (already timed) by less than ``margin``: short probes carry
+    a timing noise of about a percent, and a shape that wins by less is not
+    known to be faster."""
+    best = min(rows, key=lambda r: r["relative"])
+    if incumbent is not None and best is not incumbent and \
+            best["relative"] > incumbent["relative"] * (1.0 - margin):
+        return incumbent
+    return best
+
+
 def variant(p2g: int, g2p: int, fupd: int) -> int:
     """Brick variant of one occupancy choice per brick kernel."""
     return p2g + 3 * g2p + 9 * fupd
@@ -54,7 +66,8 @@ def variant(p2g: int, g2p: int, fupd: int) -> int:
 
 def autotune(batch, stream, key: Optional[tuple] = None, substeps: int = 16, rounds: int = 1,
              occ_choices: Iterable[int] = OCC_CHOICES, node_tiles: Iterable[int] = NODE_TILES,
-             graph_chunks: Iterable[int] = GRAPH_CHUNKS, baseline=(16, 128, 0)) -> dict:
+             graph_chunks: Iterable[int] = GRAPH_CHUNKS, baseline=(16, 128, 0),
+             margin: float = 0.01) -> dict:
     """Pick each brick kernel's occupancy in turn (the others held at their
     best so far) at a 16-substep graph, then the node tile, then the graph
     chunk; set the winner on ``batch`` and return
@@ -63,8 +76,9 @@ def autotune(batch, stream, key: Optional[tuple] = None, substeps: int = 16, rou
     The probes advance the scenes, and the cost of a substep drifts as cuts
     progress, so every candidate is timed between two timings of a fixed
     ``baseline`` shape (graph chunk, node tile, variant) and ranked by its
-    time relative to their mean.  ``stream`` is the torch stream the batch
-    launches on.  With ``key`` the result is cached for this process and a
+    time relative to their mean; a candidate replaces the shape it would
+    change only when it is faster by more than ``margin`` (see ``pick``).
+    ``stream`` is the torch stream the batch launches on.  With ``key`` the result is cached for this process and a
     later call with the same key only applies it."""
     if key is not None and key in _cache:
         b = _cache[key]["best"]
@@ -91,22 +105,26 @@ def autotune(batch, stream, key: Optional[tuple] = None, substeps: int = 16, rou
     trials.append({"brick_variant": baseline[2], "node_tile": baseline[1],
                    "graph_chunk": baseline[0], "ms": ref_ms, "relative": 1.0})
     seen.add(tuple(baseline))
+    def row(chunk, ntile, v):
+        return next((r for r in trials if (r["graph_chunk"], r["node_tile"], r["brick_variant"]) ==
+                     (chunk, ntile, v)), None)
+
     occ = [0, 0, 0]
     for k in range(3):          # P2G, G2P+MUSL, F update
         for c in occ_choices:
             o = list(occ)
             o[k] = c
             probe(16, baseline[1], variant(*o))
-        best = min((r for r in trials if r["graph_chunk"] == 16 and r["node_tile"] == baseline[1]),
-                   key=lambda r: r["relative"])
+        rows = [r for r in trials if r["graph_chunk"] == 16 and r["node_tile"] == baseline[1]]
+        best = pick(rows, row(16, baseline[1], variant(*occ)), margin)
         v = best["brick_variant"]
         occ = [v % 3, (v // 3) % 3, v // 9]
     for t in node_tiles:
         probe(16, t, variant(*occ))
-    best = min(trials, key=lambda r: r["relative"])
+    best = pick(trials, best, margin)
     for c in graph_chunks:
         probe(c, best["node_tile"], best["brick_variant"])
-    best = min(trials, key=lambda r: r["relative"])
+    best = pick(trials, best, margin)
     batch.set_tiles(best["graph_chunk"], best["node_tile"], best["brick_variant"])
     out = {"best": {"brick_variant": best["brick_variant"], "node_tile": best["node_tile"],
                     "graph_chunk": best["graph_chunk"], "ms_per_substep": best["ms"],

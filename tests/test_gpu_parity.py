@@ -243,7 +243,11 @@ def test_autotune_keeps_the_trajectory(pkg):
     assert len(shapes) == len(r["trials"])
     assert 6 <= len(shapes) <= 9, len(shapes)
     assert any(t["brick_variant"] not in (0, 1, 2) for t in r["trials"]), "mixed occupancy probed"
-    assert r["best"]["relative_to_baseline"] == min(t["relative"] for t in r["trials"])
+    rel = [t["relative"] for t in r["trials"]]
+    # the winner is the fastest shape, or within the switching margin (1%) of
+    # it at each of the three stages
+    assert r["best"]["relative_to_baseline"] in rel
+    assert min(rel) >= r["best"]["relative_to_baseline"] * (1.0 - 0.01) ** 3
     assert all(t["ms"] > 0 for t in r["trials"])
     b.step(3)
     n = r["substeps_advanced"] + 3
