@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import hashlib
+import re
 import json
 import math
 import os
@@ -145,9 +146,17 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def code_hash(text: str) -> str:
+    """Hash of a CUDA source's code: comments, trailing blanks and empty lines
+    removed, so that an edit of the comments keeps a capture's key."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", l).rstrip() for l in text.splitlines()]
+    return hashlib.sha256("\n".join(l for l in lines if l).encode()).hexdigest()[:16]
+
+
 def kernel_source_hash() -> str:
     src = os.path.join(ROOT, "paper_2609_27342_gb300", "csrc", "bm_kernels.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return code_hash(open(src).read())
 
 
 def ncu_traffic(kernel: str, units: dict):
@@ -157,7 +166,7 @@ def ncu_traffic(kernel: str, units: dict):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+    if d.get("kernel_code_sha256_16") != kernel_source_hash():
         return None
     k = d.get("kernels", {}).get(kernel)
     if not k:

@@ -14,6 +14,9 @@
 //   k_fupd       F update, commit of the new side labels
 //   k_tool       per scene: wrench, rigid tool step, next frame
 //   k_slot_*     compact logical-grid slots (Sec. III-G) after label changes
+//   k_pair_*     material-material contact (Eq. 10-13): the rebuild test,
+//                spatial hash and candidate lists, and the pair impulses,
+//                ahead of P2G
 // No atomics touch floating-point sums: every sum is taken in a fixed order,
 // so a scene gives bit-identical results alone or inside any batch.
 //
