@@ -2269,25 +2269,9 @@ __global__ void k_get_wrenches(World w, const int *ids, int n, double *out) {
   for (int k = 0; k < 6; ++k) out[(size_t)idx * 6 + k] = sc.lastW[k];
 }
 
-__global__ void k_tool(World w, LaunchSet ls) {
-  const int sid = ls.scene_ids[blockIdx.x];
-  DevScene &sc = w.scenes[sid];
-  if (sc.frozen) {  // a scene that has taken its substeps: nothing moves, nothing to rebuild
-    if (threadIdx.x == 0) sc.need_rebuild = 0;
-    return;
-  }
-  __shared__ double sm[32];
-  // reduce this substep's per-brick wrench partials in brick order
-  double W[6];
-  for (int k = 0; k < 6; ++k) {
-    double acc = 0.0;
-    if (sc.has_blade)
-      for (int j = threadIdx.x; j < sc.n_brick; j += blockDim.x)
-        acc += w.wpart[(size_t)(sc.brick_begin + j) * 6 + k];
-    W[k] = block_sum(acc, sm);
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+// the serial part of k_tool (one thread): wrench history, interval-averaged
+// rigid tool step, and the frame of the next substep
+__device__ __forceinline__ void tool_step(const World &w, DevScene &sc, const double W[6]) {
   // labels committed by k_fupd this substep -> rebuild the slot table
   sc.need_rebuild = sc.label_pending ? 1 : 0;
   sc.label_pending = 0;
@@ -2341,6 +2325,39 @@ __global__ void k_tool(World w, LaunchSet ls) {
   sc.step++;
   if (sc.stop_at >= 0 && sc.step >= sc.stop_at) sc.frozen = 1;
   prepare_substep(sc);
+}
+
+
+__global__ void k_tool(World w, LaunchSet ls) {
+  const int sid = ls.scene_ids[blockIdx.x];
+  DevScene &g = w.scenes[sid];
+  if (g.frozen) {  // a scene that has taken its substeps: nothing moves, nothing to rebuild
+    if (threadIdx.x == 0) g.need_rebuild = 0;
+    return;
+  }
+  __shared__ double sm[32];
+  // the scene record into shared memory (coalesced), so that the serial tool
+  // step and frame below read and write it at shared-memory latency
+  __shared__ DevScene sc;
+  static_assert(sizeof(DevScene) % sizeof(double) == 0, "the scene record copies as doubles");
+  constexpr int kWords = (int)(sizeof(DevScene) / sizeof(double));
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<double *>(&sc)[i] = reinterpret_cast<const double *>(&g)[i];
+  __syncthreads();
+  // reduce this substep's per-brick wrench partials in brick order
+  double W[6];
+  for (int k = 0; k < 6; ++k) {
+    double acc = 0.0;
+    if (sc.has_blade)
+      for (int j = threadIdx.x; j < sc.n_brick; j += blockDim.x)
+        acc += w.wpart[(size_t)(sc.brick_begin + j) * 6 + k];
+    W[k] = block_sum(acc, sm);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tool_step(w, sc, W);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<double *>(&g)[i] = reinterpret_cast<const double *>(&sc)[i];
 }
 
 // --------------------------------------------------------------------------
