@@ -2449,24 +2449,46 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
 
 // per brick: slot count and first tile slot of each tile node, and the
 // tile's slot total (after the per-node counts are final)
-__global__ void k_brick_tiles(World w, LaunchSet ls, int force) {
-  const int4 bt = ls.btiles[blockIdx.x];
+// (one warp per brick, BTILE_WARPS bricks per CTA: lane l takes the tile's
+// nodes 7l .. 7l + 6, an exclusive warp scan orders them)
+#define BTILE_WARPS 8
+__global__ void __launch_bounds__(32 * BTILE_WARPS) k_brick_tiles(World w, LaunchSet ls, int force) {
+  const int lane = threadIdx.x & 31;
+  const int bi = blockIdx.x * BTILE_WARPS + (threadIdx.x >> 5);
+  if (bi >= ls.n_btiles) return;
+  const int4 bt = ls.btiles[bi];
   const DevScene &sc = w.scenes[bt.x];
   if (!force && !sc.need_rebuild) return;
-  __shared__ int sm[33];
   int c0x, c0y, c0z;
   brick_coords(sc, bt.y - sc.brick_begin, c0x, c0y, c0z);
-  const int t = threadIdx.x;
-  int cnt = 0;
-  if (t < TN) {
-    const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
-    if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2])
-      cnt = w.N.slot_cnt[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
+  constexpr int PER = (TN + 31) / 32;  // 7
+  int cnt[PER];
+  int mine = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int t = lane * PER + j;
+    cnt[j] = 0;
+    if (t < TN) {
+      const int nx = c0x + t % TE, ny = c0y + (t / TE) % TE, nz = c0z + t / (TE * TE);
+      if (nx < sc.nn[0] && ny < sc.nn[1] && nz < sc.nn[2])
+        cnt[j] = w.N.slot_cnt[sc.node_begin + (nz * sc.nn[1] + ny) * sc.nn[0] + nx];
+    }
+    mine += cnt[j];
   }
-  int total;
-  const int ex = block_excl_scan(cnt, sm, total);
-  if (t < TN) w.B.tdesc[(size_t)bt.y * TN + t] = ex | (cnt << 16);
-  if (t == 0) w.B.ptot[bt.y] = total;
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int ex = incl - mine;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int t = lane * PER + j;
+    if (t < TN) w.B.tdesc[(size_t)bt.y * TN + t] = ex | (cnt[j] << 16);
+    ex += cnt[j];
+  }
+  if (lane == 31) w.B.ptot[bt.y] = incl;
 }
 
 // per scene: slot offsets of the node tiles, and partial-sum ranges of the bricks
@@ -2656,7 +2678,7 @@ static cudaError_t launch_rebuild(const World &w, const LaunchSet &ls, cudaStrea
   k_slot_count<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
   rec(ev, 6, 1, st);
   rec(ev, 9, 0, st);
-  k_brick_tiles<<<ls.n_btiles, 256, 0, st>>>(w, ls, force);
+  k_brick_tiles<<<(ls.n_btiles + BTILE_WARPS - 1) / BTILE_WARPS, 32 * BTILE_WARPS, 0, st>>>(w, ls, force);
   rec(ev, 9, 1, st);
   rec(ev, 7, 0, st);
   k_slot_scan<<<ls.n_scenes, 256, 0, st>>>(w, ls, force);
