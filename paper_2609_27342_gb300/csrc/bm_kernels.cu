@@ -2408,11 +2408,25 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
     bool over = false;
     unsigned long long last = 0;
     bool first = true;
+    // a cell of up to 8 particles keeps its keys in registers across the
+    // passes (the all-ones key is never a code: a cut has one side per particle)
+    constexpr int KR = 8;
+    const bool inreg = p1 - p0 <= KR;
+    unsigned long long kr[KR];
+#pragma unroll
+    for (int j = 0; j < KR; ++j)
+      kr[j] = (inreg && p0 + j < p1) ? ((unsigned long long)w.P.s2[p0 + j] << 32) | w.P.s1[p0 + j] : ~0ull;
     for (;;) {
       unsigned long long m = ~0ull;
-      for (int p = p0; p < p1; ++p) {
-        const unsigned long long k = ((unsigned long long)w.P.s2[p] << 32) | w.P.s1[p];
-        if ((first || k > last) && k < m) m = k;
+      if (inreg) {
+#pragma unroll
+        for (int j = 0; j < KR; ++j)
+          if ((first || kr[j] > last) && kr[j] < m) m = kr[j];
+      } else {
+        for (int p = p0; p < p1; ++p) {
+          const unsigned long long k = ((unsigned long long)w.P.s2[p] << 32) | w.P.s1[p];
+          if ((first || k > last) && k < m) m = k;
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
