@@ -52,12 +52,14 @@ FALLBACK_HBM_GBS = 6800.0
 # partials counted at 3.375 tiles per slot (6^3 tile nodes per 4^3 cells).
 KERNEL_MODEL = {
     # contact, labels and stress are computed in the P2G brick kernel's
-    # staging phase: it reads x, v, F, D, u_t, masks, the fractional offset
-    # and the base cell (100 B) and writes the pending label (D and u_t only
-    # where they change)
-    "k_p2g_brick": {"bytes": (101, 0, 108, 2000), "flops": (1470, 0, 0, 0)},
+    # staging phase: it reads x, v, F, masks, the fractional offset and the
+    # D/u_t flag (81 B) and writes the pending label; D and u_t (16 B) are
+    # read only for flagged particles and written only where they change, so
+    # they are not counted (the cell of a particle comes from the brick's
+    # cell ranges, not from memory)
+    "k_p2g_brick": {"bytes": (82, 0, 108, 2000), "flops": (1470, 0, 0, 0)},
     "k_p2g_node": {"bytes": (0, 12, 140, 0), "flops": (0, 0, 40, 0)},
-    "k_g2p_musl": {"bytes": (72, 0, 162, 1080), "flops": (570, 0, 0, 0)},
+    "k_g2p_musl": {"bytes": (68, 0, 162, 1080), "flops": (570, 0, 0, 0)},
     "k_musl_node": {"bytes": (0, 12, 86, 0), "flops": (0, 0, 20, 0)},
     "k_fupd": {"bytes": (97, 0, 54, 1080), "flops": (650, 0, 0, 0)},
 }

@@ -104,6 +104,8 @@ struct PPool {
   float *fx[3];
   uint32_t *base;           // packed local base cell: bx | by << 10 | bz << 20
   float *x[3], *v[3], *F[9], *D, *ut[3];
+  uint8_t *tflag;           // 0: D and u_t are both zero (P2G then skips their loads); set by
+                            // P2G when either becomes nonzero and by any write of either field
   float *Fpi[9];            // inverse plastic deformation Fp^-1 (identity without plasticity)
   float *Fdot[9];           // dF/dt of the last substep (viscosity)
   uint32_t *s1, *s2;        // bit k: digit k == 1 (s1) or == 2 (s2)

@@ -522,6 +522,17 @@ __device__ __forceinline__ int cell_index(const DevScene &sc, int bx, int by, in
   return b * BR3 + (((bz & 3) * BR + (by & 3)) * BR + (bx & 3));
 }
 
+// The cell (0..63) of the brick's particle i: particles are sorted by cell,
+// so it is the last cell whose range (cs: the brick's 65 cell starts,
+// relative to its first particle) starts at or before i.
+__device__ __forceinline__ int cell_of(const int *cs, int i) {
+  int c = 0;
+#pragma unroll
+  for (int step = 32; step > 0; step >>= 1)
+    if (cs[c + step] <= i) c += step;
+  return c;
+}
+
 __device__ __forceinline__ void particle_base(uint32_t b, int &bx, int &by, int &bz) {
   bx = (int)(b & 1023u);
   by = (int)((b >> 10) & 1023u);
@@ -648,15 +659,17 @@ __device__ __forceinline__ bool blade_out_of_reach(const DevScene &sc, const flo
 // INELASTIC: the launch set holds a scene with plasticity or viscosity (the
 // elastic instantiation carries no trace of those paths)
 template <bool INELASTIC>
-__device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P, int p, const float x[3],
+__device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P, int p, uint8_t tf, const float x[3],
                                              const float v[3], uint32_t s1, uint32_t s2, float A[9], float J[3],
                                              float wr[6], bool &clamped, bool &anyc) {
   const float dt = sc.dt, mp = sc.mp;
   const int cut = sc.cut;
   J[0] = J[1] = J[2] = 0.f;
-  const float D0 = P.D[p];
+  // most particles never touch the blade: D and u_t are read only where the
+  // flag says they may be nonzero (both are exactly zero where it is clear)
+  const float D0 = tf ? P.D[p] : 0.0f;
   float D = sc.reset_D ? 0.0f : D0;
-  const float u00 = P.ut[0][p], u01 = P.ut[1][p], u02 = P.ut[2][p];
+  const float u00 = tf ? P.ut[0][p] : 0.0f, u01 = tf ? P.ut[1][p] : 0.0f, u02 = tf ? P.ut[2][p] : 0.0f;
   float uh[3] = {u00, u01, u02};
   if (sc.has_blade && sc.tool_contact_on && blade_out_of_reach(sc, x, v)) {
     uh[0] = uh[1] = uh[2] = 0.0f;  // as on the no-contact branch below
@@ -763,6 +776,10 @@ __device__ __forceinline__ void pre_particle(const DevScene &sc, const PPool &P,
     P.ut[1][p] = uh[1];
     P.ut[2][p] = uh[2];
   }
+  // cleared only when the values in memory are zero: a value equal to zero
+  // (either sign) was either written above or already held as zero
+  const uint8_t nf = (D != 0.0f || uh[0] != 0.0f || uh[1] != 0.0f || uh[2] != 0.0f) ? 1 : 0;
+  if (nf != tf) P.tflag[p] = nf;
   P.pend[p] = pend;
 }
 
@@ -950,17 +967,20 @@ template <int PPC, bool INELASTIC>
 __device__ void stage_particles(const World &w, const DevScene &sc, const int4 &bt, int c0x, int c0y, int c0z,
                                 K2S<PPC> &S, float wr[6], bool &clamped, bool &anyc) {
   const PPool &P = w.P;
+  // each thread fetches its next particle's flag one iteration ahead, so the
+  // loads of D and u_t it gates do not wait on it
+  uint8_t tf_next = (int)threadIdx.x < bt.w ? P.tflag[bt.z + threadIdx.x] : 0;
   for (int i = threadIdx.x; i < bt.w; i += blockDim.x) {
     const int p = bt.z + i;
-    int bx, by, bz;
-    particle_base(P.base[p], bx, by, bz);
+    const uint8_t tf = tf_next;
+    if (i + (int)blockDim.x < bt.w) tf_next = P.tflag[p + blockDim.x];
     const float x[3] = {P.x[0][p], P.x[1][p], P.x[2][p]};
     const float v[3] = {P.v[0][p], P.v[1][p], P.v[2][p]};
     const uint32_t s1 = P.s1[p], s2 = P.s2[p];
     const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
     float A[9], J[3];
-    pre_particle<INELASTIC>(sc, P, p, x, v, s1, s2, A, J, wr, clamped, anyc);
-    const int c = ((bz - c0z) * BR + (by - c0y)) * BR + (bx - c0x);
+    pre_particle<INELASTIC>(sc, P, p, tf, x, v, s1, s2, A, J, wr, clamped, anyc);
+    const int c = cell_of(S.cs, i);
     const int si = pic(i - S.cs[c], c);
     S.part[0][si] = f0;
     S.part[1][si] = f1;
@@ -1387,10 +1407,8 @@ __global__ void __launch_bounds__(BT, MB) k_g2p_musl(World w, LaunchSet ls) {
   bool bad = false;
   for (int i = tid; i < bt.w; i += BT) {
     const int p = bt.z + i;
-    int bx, by, bz;
-    particle_base(P.base[p], bx, by, bz);
-    const int lx = bx - c0x, ly = by - c0y, lz = bz - c0z;
-    const int c = (lz * BR + ly) * BR + lx;
+    const int c = cell_of(S.cs, i);
+    const int lx = c & 3, ly = (c >> 2) & 3, lz = c >> 4;
     const int si = pic(i - S.cs[c], c);
     const uint32_t s1 = P.s1[p], s2 = P.s2[p];
     const float f0 = P.fx[0][p], f1 = P.fx[1][p], f2 = P.fx[2][p];
@@ -2612,14 +2630,19 @@ __global__ void k_io(World w, int scene_slot, int p_begin, int n, int field, voi
       }
       break;
     case 4:
-      if (to_pool) P.D[p] = fb[o];
-      else fb[o] = P.D[p];
+      if (to_pool) {
+        P.D[p] = fb[o];
+        P.tflag[p] = 1;  // may be nonzero: the next P2G reads it
+      } else {
+        fb[o] = P.D[p];
+      }
       break;
     case 5:
       for (int a = 0; a < 3; ++a) {
         if (to_pool) P.ut[a][p] = fb[3 * o + a];
         else fb[3 * o + a] = P.ut[a][p];
       }
+      if (to_pool) P.tflag[p] = 1;
       break;
     case 7:
       if (to_pool) P.s1[p] = ub[o];

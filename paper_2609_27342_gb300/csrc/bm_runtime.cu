@@ -214,6 +214,8 @@ int world_alloc(WorldH *W) {
     F(pp.Fdot[k], P);
   }
   F(pp.D, P);
+  pp.tflag = W->get<uint8_t>(P);
+  ok &= pp.tflag != nullptr;
   U(pp.base, P);
   U(pp.s1, P);
   U(pp.s2, P);
@@ -575,6 +577,7 @@ int place_fresh(WorldH *W, bm_scene_s *s) {
     CK(cudaMemsetAsync(P.Fdot[k] + pb, 0, sizeof(float) * n, st));
   }
   CK(cudaMemsetAsync(P.D + pb, 0, sizeof(float) * n, st));
+  CK(cudaMemsetAsync(P.tflag + pb, 0, n, st));
   CK(cudaMemsetAsync(P.pend + pb, 0, n, st));
   for (int a = 0; a < 3; ++a) CK(cudaMemsetAsync(P.J[a] + pb, 0, sizeof(float) * n, st));
   CK(cudaMemsetAsync(P.s1 + pb, 0, sizeof(uint32_t) * n, st));
@@ -654,6 +657,7 @@ int move_scene(bm_scene_s *s, WorldH *W) {
     CK(cp(B.Fdot[k] + pd, A.Fdot[k] + ps, sizeof(float) * n));
   }
   CK(cp(B.D + pd, A.D + ps, sizeof(float) * n));
+  CK(cp(B.tflag + pd, A.tflag + ps, n));
   CK(cp(B.base + pd, A.base + ps, sizeof(uint32_t) * n));
   CK(cp(B.s1 + pd, A.s1 + ps, sizeof(uint32_t) * n));
   CK(cp(B.s2 + pd, A.s2 + ps, sizeof(uint32_t) * n));
@@ -1155,6 +1159,7 @@ std::vector<CkSection> ck_layout(const bm_scene_s *s, size_t *total) {
   for (int k = 0; k < 9; ++k) add(P.Fdot[k] + pb, sizeof(float) * n);
   add(P.D + pb, sizeof(float) * n);
   for (int a = 0; a < 3; ++a) add(P.ut[a] + pb, sizeof(float) * n);
+  add(P.tflag + pb, n);
   add(P.s1 + pb, sizeof(uint32_t) * n);
   add(P.s2 + pb, sizeof(uint32_t) * n);
   if (s->desc.pair_contact) {
@@ -1496,9 +1501,10 @@ int bm_scene_footprint(const bm_scene_desc *desc, const float *X_ref, int64_t n,
   if (nodes) *nodes = s.n_node;
   if (bricks) *bricks = s.n_brick;
   // fx, x, v, u_t, J (3 each); F, Fp^-1, dF/dt (9 each); D; base, masks, perm; pending label;
+  // the D / u_t flag;
   // with pair contact: hash key, order, entries with their base cells and cell keys, the double-buffered history,
   // the candidate list and the positions at its build
-  const int64_t per_p = 4 * (3 * 5 + 9 * 3 + 1) + 4 * 4 + 1 +
+  const int64_t per_p = 4 * (3 * 5 + 9 * 3 + 1) + 4 * 4 + 1 + 1 +
                         (desc->pair_contact ? (4 + 4 + 16 + 4 + 16 + 2 * BM_HIST * 16 + 4 * BM_NBR + 1 + 12) : 0);
   const int64_t per_node = 4 + 1 + 8 * BM_MAXS + 4 * (3 * 16 + 8) + 6 * 32;
   const int64_t per_brick = 3 * BM_TILE_NODES + 48 + 16 + 8;
