@@ -133,6 +133,37 @@ def run100(pkg):
     return sc, o, g
 
 
+def test_written_cutting_progress_reaches_the_substep(pkg):
+    """D written through the state API mid-cut (Eq. 5: 0.875 for every
+    particle, after the cut has started, so no cut-start reset clears it)
+    drives the next substeps as in the oracle: the front-band particles
+    release early.  Most particles hold D = 0 up to the write, so the
+    substep skips their D loads until the write marks them; a write that
+    did not would leave the trajectory of the unwritten run, 3e-4 m away."""
+    sc = _touching_block()
+    o = O.OracleScene(sc)
+    g = pkg.Scene(sc, wrench_history=16)
+    o.step(3)
+    g.step(3)
+    D = np.full(sc.n, 0.875)
+    o.set("D", D)
+    g.write(D=D.astype(np.float32))
+    o.step(13)
+    g.step(13)
+    L = domain(sc)
+    r = g.read("x", "D")
+    assert np.max(np.abs(r["x"] - o.get("x"))) < 1e-6 * L
+    assert np.max(np.abs(r["D"] - o.get("D"))) < 1e-4
+    wo = o.wrench_history(0, 16)
+    wg = g.wrench_history(0, 16)
+    scale = np.max(np.abs(wo[:, :3]))
+    assert np.max(np.abs(wg[:, :3] - wo[:, :3])) < 1e-4 * scale
+    # the written D changed the run: the unwritten one ends elsewhere
+    h = pkg.Scene(sc)
+    h.step(16)
+    assert np.max(np.abs(h.read("x")["x"] - r["x"])) > 1e-5 * L
+
+
 def test_positions_after_100_substeps(run100):
     sc, o, g = run100
     r = g.read("x")
