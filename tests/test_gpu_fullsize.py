@@ -4,7 +4,7 @@ sampled scene by scene against the FP64 oracle, and the 252,800-particle
 cylinder program (two intersecting strokes and a push, 0.2 kg two-way tool,
 pair contact) compared phase by phase.
 
-Tolerances are those of the benchmark spec: positions within 1e-5 of the domain
+Tolerances: positions within 1e-5 of the domain
 size, tool position within 1e-6 of it, wrench within 1e-4 of its peak, label
 disagreement at most 1e-4 of the particles, each disagreeing particle within
 1e-5 dx of a band threshold (the label decision boundary) -- or, where the
