@@ -2390,6 +2390,9 @@ __global__ void k_tool(World w, LaunchSet ls) {
 // stencil, and the node's codes are found in ascending order of the key
 // (mask2 << 32 | mask1) as repeated warp-wide minima over the lanes' particles
 // of the keys above the last one found.
+// KR: particles per cell whose label keys a lane keeps in registers across
+// the passes (8 or 16, the launch set's largest cell)
+template <int KR>
 __global__ void k_slot_count(World w, LaunchSet ls, int force) {
   const int4 t = ls.ntiles[blockIdx.x];
   DevScene &sc = w.scenes[t.x];
@@ -2426,9 +2429,8 @@ __global__ void k_slot_count(World w, LaunchSet ls, int force) {
     bool over = false;
     unsigned long long last = 0;
     bool first = true;
-    // a cell of up to 8 particles keeps its keys in registers across the
+    // a cell of up to KR particles keeps its keys in registers across the
     // passes (the all-ones key is never a code: a cut has one side per particle)
-    constexpr int KR = 8;
     const bool inreg = p1 - p0 <= KR;
     unsigned long long kr[KR];
 #pragma unroll
@@ -2712,7 +2714,10 @@ static cudaError_t launch_rebuild(const World &w, const LaunchSet &ls, cudaStrea
                                   cudaEvent_t *ev) {
   if (ls.n_ntiles == 0) return cudaSuccess;
   rec(ev, 6, 0, st);
-  k_slot_count<<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
+  if (ls.ppc16)
+    k_slot_count<16><<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
+  else
+    k_slot_count<8><<<ls.n_ntiles, ls.ntile_size, 0, st>>>(w, ls, force);
   rec(ev, 6, 1, st);
   rec(ev, 9, 0, st);
   k_brick_tiles<<<(ls.n_btiles + BTILE_WARPS - 1) / BTILE_WARPS, 32 * BTILE_WARPS, 0, st>>>(w, ls, force);
