@@ -1,6 +1,7 @@
 """Pins of the oracle's building blocks against closed forms and textbook
 results (CPU only).  Each test names the passage of the paper it pins."""
 import itertools
+import os
 import math
 
 import numpy as np
@@ -139,6 +140,17 @@ def test_conflict_matches_bitmask_form_exhaustively():
                 assert O.conflict(a, b) == expect
     # unassigned (0) is compatible with both sides; 1 and 2 conflict
     assert not O.conflict(0, 1) and not O.conflict(0, 2) and O.conflict(1, 2)
+
+
+def test_conflict_matches_hand_written_two_cut_table():
+    """The oracle's conflict predicate against the 9 x 9 table of the
+    two-cut codes written out by hand from Sec. III-D (tests/golden)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "eq7_conflict_k2.txt")
+    rows = [l.strip() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 9 and all(len(r) == 9 for r in rows)
+    for a in range(9):
+        for b in range(9):
+            assert O.conflict(a, b) == (rows[a][b] == "1"), (a, b)
 
 
 # --------------------------------------------------------------------------
